@@ -1,0 +1,597 @@
+/*
+ * Plain CPU oracle for epsilon-cost-sharded VFunc / VFilter (arXiv 2503.18397).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product library. It shares no
+ * code, header or constant table with the CUDA path.
+ *
+ * The build follows the paper step by step, one key and one shard at a time:
+ *   hash -> shard on the top signature bits (Sec. 4, eq. logballsbins) ->
+ *   per-shard 3-hypergraph (fuse graph, Sec. 4.2) -> degree and XOR-of-edge
+ *   incidence (Sec. 4.3, XOR trick) -> stack-based peeling visit (Sec. 4.3) ->
+ *   [LGE regime: solve the 2-core over GF(2), here by plain Gaussian
+ *   elimination since any solution is acceptable, Sec. 3.3 / 4.2] ->
+ *   assignment in reverse peel order -> data array of cells.
+ *   Any failure restarts the whole construction with the next seed (Sec. 4).
+ *
+ * Parity status:
+ *   mix64              pinned (published SplitMix64 test vector)
+ *   signatures         pinned by uniformity / collision tests (repo-defined hash)
+ *   shard bits         pinned (Table 1 shard counts; eq. dupmwhc worked example)
+ *   geometry           pinned (space overhead of Sec. 5; closed forms)
+ *   peel               pinned (brute-force 2-core on tiny hypergraphs)
+ *   GF(2) solve        pinned (brute force over all assignments on tiny systems)
+ *   build / query      pinned (Problem 1: every key decodes to its value;
+ *                      Problem 2: no false negatives, FPR ~ 2^-b)
+ */
+#include "vf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Nothing-up-my-sleeve constants: hexadecimal digits of pi and the golden ratio. */
+#define ORC_K_HI    0x243F6A8885A308D3ULL
+#define ORC_K_LO    0x13198A2E03707344ULL
+#define ORC_C_EDGE  0xA4093822299F31D0ULL
+#define ORC_C_EDGE2 0x082EFA98EC4E6C89ULL
+#define ORC_C_FP    0x452821E638D01377ULL
+#define ORC_GOLDEN  0x9E3779B97F4A7C15ULL
+
+void orc_params_default(orc_params *p) {
+    memset(p, 0, sizeof *p);
+    p->kind = ORC_FUNC;
+    p->b = 8;
+    p->key_kind = ORC_KEYS_U64;
+    p->mode = ORC_MODE_AUTO;
+    p->max_retries = 16;
+    p->seed = 0;
+    p->eps = 0.001;            /* Sec. 5: VFunc/VFilter use epsilon = 0.001 */
+    p->eta = 0.1;              /* reading of eq. (logdupfuse) that reproduces Table 1 */
+    p->lge_threshold = 800000; /* Sec. 4.2: below 800,000 keys, LGE with c = 1.12 */
+    p->lge_target = 16384;
+    p->lge_max_shard = 24576;
+}
+
+/* ------------------------------------------------------------------ hashing */
+
+uint64_t orc_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_mulhi(uint64_t a, uint64_t b) {
+    return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+}
+
+/* Keys are hashed once to a signature and every later step uses the
+ * signature (Sec. 4.3, "All current constructions ... start by hashing"). */
+void orc_sig_u64(uint64_t key, uint64_t seed, uint64_t out[2]) {
+    uint64_t kh = orc_mix64(seed ^ ORC_K_HI);
+    uint64_t kl = orc_mix64(seed ^ ORC_K_LO);
+    out[0] = orc_mix64(key + kh);
+    out[1] = orc_mix64(key ^ kl);
+}
+
+void orc_sig_bytes(const uint8_t *p, uint64_t len, uint64_t seed, uint64_t out[2]) {
+    uint64_t kh = orc_mix64(seed ^ ORC_K_HI);
+    uint64_t kl = orc_mix64(seed ^ ORC_K_LO);
+    uint64_t a = kh ^ (len * ORC_GOLDEN);
+    uint64_t b = kl ^ len;
+    uint64_t nw = (len + 7) / 8;
+    for (uint64_t i = 0; i < nw; i++) {
+        /* i-th little-endian 8-byte word, zero-padded past the end */
+        uint64_t w = 0;
+        for (uint64_t j = 0; j < 8; j++) {
+            uint64_t pos = 8 * i + j;
+            if (pos < len) w |= (uint64_t)p[pos] << (8 * j);
+        }
+        a = orc_mix64(a ^ w);
+        b = orc_mix64(b + w);
+    }
+    out[0] = orc_mix64(a);
+    out[1] = orc_mix64(b);
+}
+
+/* ------------------------------------------------------------- parameters */
+
+/* Halley iteration on w e^w = x. */
+double orc_lambert_w0(double x) {
+    if (x == 0.0) return 0.0;
+    double w = log1p(x);
+    for (int it = 0; it < 200; it++) {
+        double ew = exp(w);
+        double f = w * ew - x;
+        double wp1 = w + 1.0;
+        double d = f / (ew * wp1 - (w + 2.0) * f / (2.0 * wp1));
+        w -= d;
+        if (fabs(d) <= 1e-15 * (1.0 + fabs(w))) break;
+    }
+    return w;
+}
+
+/* eq. (logballsbins): floor(lg x - lg ln x), x = n eps^2 / (2 alpha^2), alpha = 1.
+ * For x <= e the approximation is undefined or exceeds lg x: no sharding. */
+int orc_h_ballsbins(uint64_t n, double eps) {
+    double x = (double)n * eps * eps / 2.0;
+    if (!(x > exp(1.0))) return 0;
+    double h = floor(log2(x) - log2(log(x)));
+    return h < 0 ? 0 : (int)h;
+}
+
+/* eq. (logdupfuse): h <= lg n - t / (ln 2 W(t)),
+ * t = (lg(-n / (2 c ln(1 - eta))) - 2 beta) / (2 alpha), alpha = 0.41, beta = -3
+ * (the eq. (nln) coefficients substituted for lg s_c). */
+int orc_h_dupfuse(uint64_t n, double eta, double c) {
+    if (n == 0) return 0;
+    const double alpha = 0.41, beta = -3.0;
+    double t = (log2(-(double)n / (2.0 * c * log(1.0 - eta))) - 2.0 * beta) / (2.0 * alpha);
+    double h = floor(log2((double)n) - t / (log(2.0) * orc_lambert_w0(t)));
+    return h < 0 ? 0 : (int)h;
+}
+
+/* eq. (dupmwhc): S <= sqrt(-2 n (c/3)^3 ln(1 - eta)); returned as floor(lg S). */
+int orc_h_dupmwhc(uint64_t n, double eta, double c) {
+    double s = sqrt(-2.0 * (double)n * pow(c / 3.0, 3.0) * log(1.0 - eta));
+    if (s < 1.0) return 0;
+    return (int)floor(log2(s));
+}
+
+/* Sec. 4.1: probability that t uniform draws out of n have no repeat. */
+double orc_no_repeat_prob(double n, uint64_t t) {
+    double p = 1.0;
+    for (uint64_t i = 0; i < t; i++) p *= 1.0 - (double)i / n;
+    return p;
+}
+
+int orc_plan_h(const orc_params *p, uint64_t n, int *regime, int *h_bb, int *h_dup) {
+    int reg;
+    if (p->mode == ORC_MODE_LGE) reg = ORC_REGIME_LGE;
+    else if (p->mode == ORC_MODE_FUSE) reg = ORC_REGIME_FUSE;
+    else reg = n < p->lge_threshold ? ORC_REGIME_LGE : ORC_REGIME_FUSE;
+    int h;
+    if (reg == ORC_REGIME_FUSE) {
+        /* Sec. 4.2: the number of shards is the smaller of the two bounds. */
+        *h_bb = orc_h_ballsbins(n, p->eps);
+        *h_dup = orc_h_dupfuse(n, p->eta, 1.105);
+        h = *h_bb < *h_dup ? *h_bb : *h_dup;
+    } else {
+        /* LGE regime: as many shards as needed to bring the mean shard
+         * down to lge_target keys. */
+        *h_bb = -1;
+        *h_dup = -1;
+        h = 0;
+        while (h < 40 && n > (p->lge_target << h)) h++;
+    }
+    *regime = reg;
+    return h;
+}
+
+void orc_geometry(orc_info *in) {
+    double Mf = (double)(in->M > 0 ? in->M : 1);
+    if (in->regime == ORC_REGIME_LGE) {
+        in->c = 1.12;
+        in->lg_seg = 0;
+        in->seg = 0;
+        in->l = 0;
+        in->T = 0;
+        /* tiny shards get at least 32 cells so that distinct keys rarely
+         * share an edge (the expansion factor grows for small sizes, Sec. 4.2) */
+        uint64_t cells = (uint64_t)ceil(in->c * Mf);
+        in->cells = cells < 32 ? 32 : cells;
+    } else {
+        double lg;
+        if (in->h > 0 && in->M >= 10000000ULL) {
+            in->c = 1.105;                                   /* Sec. 4.2, sharded */
+            lg = floor(0.41 * log(Mf) * log(log(Mf)) - 3.0); /* eq. (nln) */
+        } else {
+            in->c = 1.12;
+            lg = floor(log(Mf) / log(3.33) + 2.25);          /* eq. (ln) */
+        }
+        if (lg < 0) lg = 0;
+        if (lg > 32) lg = 32;
+        in->lg_seg = (int)lg;
+        in->seg = 1ULL << in->lg_seg;
+        uint64_t T = (uint64_t)ceil(in->c * Mf / (double)in->seg);
+        in->T = T < 3 ? 3 : T;
+        in->l = in->T - 2;
+        in->cells = in->T * in->seg;
+    }
+    in->total_cells = in->shards * in->cells;
+    if (in->b == 8 || in->b == 16 || in->b == 32)
+        in->data_bytes = in->total_cells * (uint64_t)(in->b / 8);
+    else
+        in->data_bytes = ((in->total_cells * (uint64_t)in->b + 63) / 64 + 1) * 8;
+}
+
+/* ---------------------------------------------------- shard, edge, fingerprint */
+
+/* Shards are defined by the top h signature bits (Sec. 3.2 / Sec. 4). */
+uint64_t orc_shard(const uint64_t sig[2], int h) {
+    return h == 0 ? 0 : sig[0] >> (64 - h);
+}
+
+/* Subsigning (Sec. 4.4): the 64 signature bits that follow the shard bits. */
+uint64_t orc_local(const uint64_t sig[2], int h) {
+    return h == 0 ? sig[0] : (sig[0] << h) | (sig[1] >> (64 - h));
+}
+
+void orc_edge(const orc_info *in, uint64_t local, uint64_t v[3]) {
+    if (in->regime == ORC_REGIME_FUSE) {
+        /* Fuse graph (Sec. 4.2): a start segment s in [0, l) and one vertex in
+         * each of segments s, s+1, s+2. The first vertex (and with it the
+         * segment) comes from the top bits of the local signature by fixed-point
+         * inversion, so it is monotone in the signature (Sec. 4.5). */
+        uint64_t v0 = orc_mulhi(local, in->l * in->seg);
+        uint64_t s = v0 / in->seg;
+        uint64_t r = orc_mix64(local ^ ORC_C_EDGE);
+        v[0] = v0;
+        v[1] = (s + 1) * in->seg + (r % in->seg);
+        v[2] = (s + 2) * in->seg + ((r >> 32) % in->seg);
+    } else {
+        /* LGE regime: three distinct vertices drawn uniformly over the shard. */
+        uint64_t V = in->cells;
+        uint64_t r = orc_mix64(local ^ ORC_C_EDGE);
+        uint64_t q = orc_mix64(local ^ ORC_C_EDGE2);
+        uint64_t d1 = 1 + orc_mulhi(r, V - 1);
+        uint64_t t = 1 + orc_mulhi(q, V - 2);
+        uint64_t d2 = t >= d1 ? t + 1 : t;
+        v[0] = orc_mulhi(local, V);
+        v[1] = (v[0] + d1) % V;
+        v[2] = (v[0] + d2) % V;
+    }
+}
+
+/* Filters derive the b-bit hash from the signature (Sec. 4.5). */
+uint32_t orc_fingerprint(uint64_t local, int b) {
+    return (uint32_t)(orc_mix64(local ^ ORC_C_FP) >> (64 - b));
+}
+
+/* ------------------------------------------------------------------ cells */
+
+uint32_t orc_cell_get(const uint8_t *data, int b, uint64_t i) {
+    if (b == 8) return data[i];
+    if (b == 16) { uint16_t x; memcpy(&x, data + 2 * i, 2); return x; }
+    if (b == 32) { uint32_t x; memcpy(&x, data + 4 * i, 4); return x; }
+    uint64_t bit = i * (uint64_t)b;
+    uint32_t v = 0;
+    for (int j = 0; j < b; j++) {
+        uint64_t q = bit + (uint64_t)j;
+        v |= (uint32_t)((data[q / 8] >> (q % 8)) & 1u) << j;
+    }
+    return v;
+}
+
+static void cell_set(uint8_t *data, int b, uint64_t i, uint32_t v) {
+    if (b == 8) { data[i] = (uint8_t)v; return; }
+    if (b == 16) { uint16_t x = (uint16_t)v; memcpy(data + 2 * i, &x, 2); return; }
+    if (b == 32) { memcpy(data + 4 * i, &v, 4); return; }
+    uint64_t bit = i * (uint64_t)b;
+    for (int j = 0; j < b; j++) {
+        uint64_t q = bit + (uint64_t)j;
+        uint8_t m = (uint8_t)(1u << (q % 8));
+        if ((v >> j) & 1u) data[q / 8] |= m; else data[q / 8] &= (uint8_t)~m;
+    }
+}
+
+/* ---------------------------------------------------------------- peeling */
+
+/* Stack-based peeling visit of Sec. 4.3 with the XOR trick: each vertex keeps
+ * its degree and the XOR of the indices of its incident edges. Vertices are
+ * scanned in order; degree-one vertices go on the stack S; each popped vertex
+ * of degree one has its only edge removed and pushed (with the vertex's side)
+ * on E; popped vertices of degree zero are discarded. */
+uint64_t orc_peel(uint64_t V, uint64_t m, const uint32_t *edges, uint32_t *order, uint8_t *side) {
+    uint32_t *deg = calloc(V ? V : 1, sizeof *deg);
+    uint64_t *xr = calloc(V ? V : 1, sizeof *xr);
+    uint64_t *stack = malloc((V ? V : 1) * sizeof *stack);
+    for (uint64_t e = 0; e < m; e++)
+        for (int k = 0; k < 3; k++) {
+            deg[edges[3 * e + k]]++;
+            xr[edges[3 * e + k]] ^= e;
+        }
+    uint64_t sp = 0, ne = 0;
+    for (uint64_t v0 = 0; v0 < V; v0++) {
+        if (deg[v0] != 1) continue;
+        stack[sp++] = v0;
+        while (sp > 0) {
+            uint64_t v = stack[--sp];
+            if (deg[v] == 0) continue;
+            uint64_t e = xr[v];
+            int sd = 0;
+            for (int k = 0; k < 3; k++)
+                if (edges[3 * e + k] == v) sd = k;
+            if (order) order[ne] = (uint32_t)e;
+            if (side) side[ne] = (uint8_t)sd;
+            ne++;
+            for (int k = 0; k < 3; k++) {
+                uint32_t w = edges[3 * e + k];
+                deg[w]--;
+                xr[w] ^= e;
+                if (w != v && deg[w] == 1) stack[sp++] = w;
+            }
+        }
+    }
+    free(deg);
+    free(xr);
+    free(stack);
+    return ne;
+}
+
+/* Plain Gaussian elimination over GF(2) with b-bit right-hand sides. Rows are
+ * bit vectors over the V variables. Each row is reduced by the existing pivot
+ * rows (pivot = lowest set bit) until it becomes a new pivot row, or zero; a
+ * zero row with a non-zero right-hand side makes the system inconsistent.
+ * Back-substitution runs over pivot columns from the highest down; variables
+ * without a pivot are set to 0. */
+int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint32_t *rhs, uint32_t *w) {
+    uint64_t W = (V + 63) / 64;
+    if (W == 0) W = 1;
+    uint64_t *rows = calloc((m ? m : 1) * W, sizeof(uint64_t));
+    uint32_t *rr = calloc(m ? m : 1, sizeof(uint32_t));
+    int64_t *pivot = malloc((V ? V : 1) * sizeof(int64_t));
+    uint64_t *cur = malloc(W * sizeof(uint64_t));
+    int ok = 1;
+    uint64_t np = 0;
+    for (uint64_t c = 0; c < V; c++) pivot[c] = -1;
+    for (uint64_t e = 0; e < m && ok; e++) {
+        memset(cur, 0, W * sizeof(uint64_t));
+        for (int k = 0; k < 3; k++) {
+            uint32_t v = edges[3 * e + k];
+            cur[v / 64] ^= 1ULL << (v % 64);
+        }
+        uint32_t cr = rhs[e];
+        for (;;) {
+            uint64_t c = 0;
+            int found = 0;
+            for (uint64_t q = 0; q < W; q++)
+                if (cur[q]) { c = q * 64 + (uint64_t)__builtin_ctzll(cur[q]); found = 1; break; }
+            if (!found) { if (cr != 0) ok = 0; break; }
+            if (pivot[c] >= 0) {
+                const uint64_t *pr = rows + (uint64_t)pivot[c] * W;
+                for (uint64_t q = 0; q < W; q++) cur[q] ^= pr[q];
+                cr ^= rr[pivot[c]];
+            } else {
+                memcpy(rows + np * W, cur, W * sizeof(uint64_t));
+                rr[np] = cr;
+                pivot[c] = (int64_t)np;
+                np++;
+                break;
+            }
+        }
+    }
+    if (ok) {
+        for (uint64_t c = 0; c < V; c++) w[c] = 0;
+        for (uint64_t cc = V; cc-- > 0;) {
+            if (pivot[cc] < 0) continue;
+            const uint64_t *pr = rows + (uint64_t)pivot[cc] * W;
+            uint32_t val = rr[pivot[cc]];
+            for (uint64_t j = cc + 1; j < V; j++)
+                if ((pr[j / 64] >> (j % 64)) & 1ULL) val ^= w[j];
+            w[cc] = val;
+        }
+    }
+    free(rows);
+    free(rr);
+    free(pivot);
+    free(cur);
+    return ok;
+}
+
+/* ------------------------------------------------------------------- build */
+
+static int u64_cmp(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : x > y;
+}
+
+static uint32_t value_at(const void *values, int b, uint64_t i) {
+    uint32_t v;
+    if (b <= 8) v = ((const uint8_t *)values)[i];
+    else if (b <= 16) v = ((const uint16_t *)values)[i];
+    else v = ((const uint32_t *)values)[i];
+    return b == 32 ? v : (v & ((1u << b) - 1u));
+}
+
+/* Solve one shard: edges from local signatures, peel, optional GE on the
+ * 2-core, reverse assignment. Returns 1 on success. */
+static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, const uint32_t *val,
+                       uint8_t *data, uint64_t base, uint64_t *peeled_out) {
+    uint64_t V = in->cells;
+    uint32_t *edges = malloc((m ? m : 1) * 3 * sizeof(uint32_t));
+    uint32_t *order = malloc((m ? m : 1) * sizeof(uint32_t));
+    uint8_t *side = malloc(m ? m : 1);
+    for (uint64_t e = 0; e < m; e++) {
+        uint64_t v[3];
+        orc_edge(in, loc[e], v);
+        for (int k = 0; k < 3; k++) edges[3 * e + k] = (uint32_t)v[k];
+    }
+    uint64_t ne = orc_peel(V, m, edges, order, side);
+    *peeled_out = ne;
+    uint32_t *w = calloc(V, sizeof(uint32_t));
+    int ok = 1;
+    if (ne < m) {
+        if (in->regime != ORC_REGIME_LGE) {
+            ok = 0;
+        } else {
+            uint8_t *is_peeled = calloc(m, 1);
+            for (uint64_t i = 0; i < ne; i++) is_peeled[order[i]] = 1;
+            uint64_t nc = 0;
+            uint32_t *ce = malloc((m - ne) * 3 * sizeof(uint32_t));
+            uint32_t *cr = malloc((m - ne) * sizeof(uint32_t));
+            for (uint64_t e = 0; e < m; e++) {
+                if (is_peeled[e]) continue;
+                memcpy(ce + 3 * nc, edges + 3 * e, 3 * sizeof(uint32_t));
+                cr[nc++] = val[e];
+            }
+            ok = orc_gf2_solve(V, nc, ce, cr, w);
+            free(is_peeled);
+            free(ce);
+            free(cr);
+        }
+    }
+    if (ok) {
+        /* Reverse peel order: the peeled vertex takes the value that makes its
+         * equation hold; every other vertex of the edge is already final. */
+        for (uint64_t i = ne; i-- > 0;) {
+            uint32_t e = order[i];
+            int sd = side[i];
+            uint32_t x = val[e];
+            for (int k = 0; k < 3; k++)
+                if (k != sd) x ^= w[edges[3 * e + k]];
+            w[edges[3 * e + sd]] = x;
+        }
+        for (uint64_t v = 0; v < V; v++) cell_set(data, in->b, base + v, w[v]);
+    }
+    free(w);
+    free(edges);
+    free(order);
+    free(side);
+    return ok;
+}
+
+int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
+              const void *values, uint64_t n, orc_info *info, uint8_t **data_out) {
+    if (p->b < 1 || p->b > 32 || (p->kind != ORC_FUNC && p->kind != ORC_FILTER)) return ORC_EINVAL;
+    if (p->key_kind != ORC_KEYS_U64 && p->key_kind != ORC_KEYS_BYTES) return ORC_EINVAL;
+    if (n > 0 && keys == NULL) return ORC_EINVAL;
+    if (p->key_kind == ORC_KEYS_BYTES && offsets == NULL) return ORC_EINVAL;
+    if (p->kind == ORC_FUNC && n > 0 && values == NULL) return ORC_EINVAL;
+    *data_out = NULL;
+    uint64_t *sig = malloc((n ? n : 1) * 2 * sizeof(uint64_t));
+    uint64_t *loc = malloc((n ? n : 1) * sizeof(uint64_t));
+    uint32_t *val = malloc((n ? n : 1) * sizeof(uint32_t));
+    if (!sig || !loc || !val) return ORC_ENOMEM;
+
+    for (int attempt = 0; attempt <= p->max_retries; attempt++) {
+        orc_info in;
+        memset(&in, 0, sizeof in);
+        in.n = n;
+        in.kind = p->kind;
+        in.b = p->b;
+        in.seed = p->seed + (uint64_t)attempt;
+        in.retries = attempt;
+        for (uint64_t i = 0; i < n; i++) {
+            if (p->key_kind == ORC_KEYS_U64)
+                orc_sig_u64(((const uint64_t *)keys)[i], in.seed, sig + 2 * i);
+            else
+                orc_sig_bytes((const uint8_t *)keys + offsets[i], offsets[i + 1] - offsets[i], in.seed,
+                              sig + 2 * i);
+        }
+        in.h = orc_plan_h(p, n, &in.regime, &in.h_bb, &in.h_dup);
+        uint64_t *cnt = NULL;
+        for (;;) {
+            in.shards = 1ULL << in.h;
+            free(cnt);
+            cnt = calloc(in.shards, sizeof(uint64_t));
+            for (uint64_t i = 0; i < n; i++) cnt[orc_shard(sig + 2 * i, in.h)]++;
+            in.M = 0;
+            for (uint64_t s = 0; s < in.shards; s++)
+                if (cnt[s] > in.M) in.M = cnt[s];
+            if (in.regime == ORC_REGIME_LGE && in.M > p->lge_max_shard && in.h < 40) { in.h++; continue; }
+            break;
+        }
+        orc_geometry(&in);
+        /* Stable bucketing of (local signature, value) by shard. */
+        uint64_t *start = calloc(in.shards + 1, sizeof(uint64_t));
+        for (uint64_t s = 0; s < in.shards; s++) start[s + 1] = start[s] + cnt[s];
+        uint64_t *fill = malloc(in.shards * sizeof(uint64_t));
+        memcpy(fill, start, in.shards * sizeof(uint64_t));
+        for (uint64_t i = 0; i < n; i++) {
+            uint64_t s = orc_shard(sig + 2 * i, in.h);
+            uint64_t j = fill[s]++;
+            loc[j] = orc_local(sig + 2 * i, in.h);
+            val[j] = p->kind == ORC_FUNC ? value_at(values, p->b, i) : 0;
+        }
+        uint8_t *data = calloc(in.data_bytes ? in.data_bytes : 1, 1);
+        int ok = 1;
+        in.n_eff = 0;
+        for (uint64_t s = 0; s < in.shards && ok; s++) {
+            uint64_t m = cnt[s];
+            uint64_t *L = loc + start[s];
+            uint32_t *Vv = val + start[s];
+            if (p->kind == ORC_FILTER) {
+                /* Sec. 4.5: duplicate local signatures are dropped; the
+                 * fingerprint is a function of the local signature. */
+                qsort(L, m, sizeof(uint64_t), u64_cmp);
+                uint64_t u = 0;
+                for (uint64_t i = 0; i < m; i++)
+                    if (u == 0 || L[i] != L[u - 1]) L[u++] = L[i];
+                m = u;
+                for (uint64_t i = 0; i < m; i++) Vv[i] = orc_fingerprint(L[i], p->b);
+            }
+            in.n_eff += m;
+            uint64_t pe = 0;
+            ok = solve_shard(&in, m, L, Vv, data, s * in.cells, &pe);
+            in.peeled += pe;
+            in.core += m - pe;
+        }
+        free(cnt);
+        free(start);
+        free(fill);
+        *info = in;
+        if (ok) {
+            *data_out = data;
+            free(sig);
+            free(loc);
+            free(val);
+            return ORC_OK;
+        }
+        free(data);
+    }
+    free(sig);
+    free(loc);
+    free(val);
+    return ORC_EBUILD;
+}
+
+void orc_free(void *ptr) { free(ptr); }
+
+/* ------------------------------------------------------------------- query */
+
+/* Query (eq. MWHC with k = 3): XOR of the three cells of the key's edge in its
+ * shard, located at shard * cells with no offset array (Sec. 4); a filter
+ * compares the result with the key's fingerprint. */
+void orc_query(const orc_info *in, const uint8_t *data, int key_kind, const void *keys,
+               const uint64_t *offsets, uint64_t m, void *out) {
+    for (uint64_t i = 0; i < m; i++) {
+        uint64_t sig[2];
+        if (key_kind == ORC_KEYS_U64)
+            orc_sig_u64(((const uint64_t *)keys)[i], in->seed, sig);
+        else
+            orc_sig_bytes((const uint8_t *)keys + offsets[i], offsets[i + 1] - offsets[i], in->seed, sig);
+        uint64_t s = orc_shard(sig, in->h);
+        uint64_t local = orc_local(sig, in->h);
+        uint64_t v[3];
+        orc_edge(in, local, v);
+        uint64_t base = s * in->cells;
+        uint32_t x = orc_cell_get(data, in->b, base + v[0]) ^ orc_cell_get(data, in->b, base + v[1]) ^
+                     orc_cell_get(data, in->b, base + v[2]);
+        if (in->kind == ORC_FILTER) {
+            ((uint8_t *)out)[i] = x == orc_fingerprint(local, in->b);
+        } else if (in->b <= 8) {
+            ((uint8_t *)out)[i] = (uint8_t)x;
+        } else if (in->b <= 16) {
+            ((uint16_t *)out)[i] = (uint16_t)x;
+        } else {
+            ((uint32_t *)out)[i] = x;
+        }
+    }
+}
+
+/* --------------------------------------------------- batch helpers for tests */
+
+void orc_sigs(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t seed,
+              uint64_t *out) {
+    for (uint64_t i = 0; i < n; i++) {
+        if (key_kind == ORC_KEYS_U64)
+            orc_sig_u64(((const uint64_t *)keys)[i], seed, out + 2 * i);
+        else
+            orc_sig_bytes((const uint8_t *)keys + offsets[i], offsets[i + 1] - offsets[i], seed, out + 2 * i);
+    }
+}
+
+void orc_edges_of(const orc_info *in, const uint64_t *locals, uint64_t n, uint64_t *out) {
+    for (uint64_t i = 0; i < n; i++) orc_edge(in, locals[i], out + 3 * i);
+}
