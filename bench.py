@@ -1,0 +1,401 @@
+"""Benchmark: epsilon-cost-sharded VFilter/VFunc construction and 3-probe
+queries on GB300, through the C ABI (libvfunc.so).
+
+Default workload (one step = the whole hot path once): build a VFilter over
+n = 10^8 distinct uniform 64-bit keys with b = 8 fingerprint bits, then query
+the 10^8 members and 10^8 disjoint non-members (false-positive rate ~ 2^-8).
+`value` is the construction cost in ns per key (device-resident inputs,
+CUDA events on the launching stream); the query rate is reported next to it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                    [--workload c2|c1|c3]
+
+--impl reference times the plain CPU oracle (the paper's algorithm, one
+thread) on a bounded sample of the same workload. Under torchrun every rank
+builds its own replica (the structure is single-GPU; replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "build ns/key & Gqueries/s on 1 GB300 vs plain GPU path; p50/p99 request latency"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+WORKLOADS = {
+    # name: (kind, b, n, key kind, description)
+    "c2": ("filter", 8, 100_000_000, "u64",
+           "VFilter n=1e8 uniform 64-bit keys, b=8, fuse graphs (eps-cost sharding h=3); "
+           "query 1e8 members + 1e8 disjoint keys"),
+    "c1": ("func", 8, 1 << 20, "u64",
+           "VFunc n=2^20 uniform 64-bit keys, 8-bit values, unsharded fuse graph; "
+           "query 2^20 members + 2^20 disjoint keys"),
+    "c3": ("func", 16, 10_000_000, "bytes",
+           "VFunc n=1e7 byte strings (length 8..64), 16-bit values, LGE regime shards; "
+           "query 1e7 members + 1e7 disjoint strings"),
+}
+
+# Algorithmic DRAM bytes per unit for each phase kernel (unit: key, edge or query).
+# Random accesses count one 32-byte sector each.
+ALGO_BYTES = {
+    "hash_hist": lambda b, kind: 8.0,                                   # key read
+    "scatter": lambda b, kind: 8.0 + 8.0 + (0 if kind == "filter" else 1.0 + 4.0),  # key in, local sig out (+values)
+    "incidence": lambda b, kind: 8.0 + 3 * 32.0,                        # local sig + 3 vertex-word sectors
+    "peel": lambda b, kind: 4 + 32 + 32 + 32 + 2 * 32 + 4 + 8,          # frontier, own word, claim, sig, 2 RMW, order, pushes
+    "assign": lambda b, kind: 4 + 32 + (0 if kind == "filter" else 32) + 3 * 32,  # order, sig, value, 3 cells
+    "lge": lambda b, kind: 8.0 + 8.0 * 3,                               # per key, shard state on chip (lower bound)
+    "query": lambda b, kind: 8.0 + 3 * 32.0 + 1.0,                      # key, 3 cell sectors, output
+}
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_inputs(workload: str, seed: int):
+    from paper_2503_18397_gb300 import synth
+
+    kind, b, n, kk, _ = WORKLOADS[workload]
+    if kk == "u64":
+        keys = synth.u64_keys(0, n, seed)
+        other = synth.u64_keys(n, n, seed)
+        offs = ooffs = None
+    else:
+        keys, offs = synth.byte_strings(0, n, seed)
+        other, ooffs = synth.byte_strings(n, n, seed)
+    vals = synth.values(n, b, seed) if kind == "func" else None
+    return kind, b, n, keys, offs, vals, other, ooffs
+
+
+def to_dev(a, torch, pin=False):
+    if a is None:
+        return None
+    if a.dtype == np.uint64:
+        t = torch.from_numpy(a.view(np.int64))
+    elif a.dtype == np.uint16:
+        t = torch.from_numpy(a.view(np.int16))
+    elif a.dtype == np.uint32:
+        t = torch.from_numpy(a.view(np.int32))
+    else:
+        t = torch.from_numpy(a)
+    if pin:
+        return t.pin_memory()
+    return t.cuda()
+
+
+# ----------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+
+    import paper_2503_18397_gb300 as vf
+    from paper_2503_18397_gb300 import build as vbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world > 1:
+        vbuild.build()
+    vf.lib()
+
+    kind, b, n, keys, offs, vals, other, ooffs = make_inputs(args.workload, 0x5EED + rank)
+    p = vf.vf_params_default(kind=vf.FILTER if kind == "filter" else vf.FUNC, b=b,
+                             key_kind=vf.KEYS_BYTES if offs is not None else vf.KEYS_U64, seed=1 + rank)
+    kd, vd, od, xd, xo = (to_dev(a, torch) for a in (keys, vals, offs, other, ooffs))
+    stream = torch.cuda.current_stream()
+
+    def step(timing):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        s = vf.vf_build(kd, vd, offsets=od, params=p, stream=stream)
+        e1.record(stream)
+        o1 = s.query(kd, offsets=od, stream=stream)
+        o2 = s.query(xd, offsets=xo, stream=stream)
+        e2.record(stream)
+        return s, e0, e1, e2, o1, o2
+
+    for _ in range(args.warmup):
+        s, *_rest = step(False)
+        torch.cuda.synchronize()
+        info = s.info
+        s.free()
+    # correctness of the last warm-up step (outside the timed region)
+    s, e0, e1, e2, o1, o2 = step(False)
+    torch.cuda.synchronize()
+    info = s.info
+    if kind == "func":
+        ok = bool((o1.view(torch.int16 if b > 8 else torch.uint8) ==
+                   to_dev(vals, torch).view(torch.int16 if b > 8 else torch.uint8)).all().item())
+    else:
+        ok = bool(o1.bool().all().item())
+    fpr = float(o2.float().mean().item()) if kind == "filter" else None
+    s.free()
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    vf.vf_timing_read()
+    vf.vf_timing_enable(True)
+    build_ms, query_ms, step_ms = [], [], []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        s, e0, e1, e2, o1, o2 = step(True)
+        torch.cuda.synchronize()
+        build_ms.append(e0.elapsed_time(e1))
+        query_ms.append(e1.elapsed_time(e2))
+        step_ms.append(e0.elapsed_time(e2))
+        s.free()
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    vf.vf_timing_enable(False)
+    phases = vf.vf_timing_read()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([total_ms, statistics.mean(build_ms), statistics.mean(query_ms)], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, b_ms, q_ms = t.tolist()
+    else:
+        b_ms, q_ms = statistics.mean(build_ms), statistics.mean(query_ms)
+
+    # end to end: the same build and queries from pinned host buffers, host output
+    kh, vh, oh, xh, xoh = (None if a is None else to_dev(a, torch, pin=True) for a in (keys, vals, offs, other, ooffs))
+    outh = torch.empty(n, dtype=torch.uint8 if (kind == "filter" or b <= 8) else torch.int16).pin_memory()
+    e2e_b, e2e_q = [], []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = vf.vf_build(kh, vh, offsets=oh, params=p)
+        t1 = time.perf_counter()
+        vf.vf_query(s, kh, offsets=oh, out=outh)
+        vf.vf_query(s, xh, offsets=xoh, out=outh)
+        t2 = time.perf_counter()
+        e2e_b.append((t1 - t0) * 1e3)
+        e2e_q.append((t2 - t1) * 1e3)
+        s.free()
+    key_bytes = keys.nbytes + (offs.nbytes if offs is not None else 0)
+    other_bytes = other.nbytes + (ooffs.nbytes if ooffs is not None else 0)
+    h2d = key_bytes + (vals.nbytes if vals is not None else 0) + key_bytes + other_bytes
+    d2h = 2 * n * outh.element_size()
+
+    hbm, peak_kind = peaks()
+    nunits = {"hash_hist": n, "scatter": n, "incidence": n, "peel": n, "assign": n, "lge": n, "query": 2 * n}
+    per_phase = {}
+    for ph, (ms, cnt) in phases.items():
+        if cnt == 0:
+            continue
+        avg = ms / cnt
+        units_per_launch = nunits[ph] / (2 if ph == "query" else 1)
+        algo = ALGO_BYTES[ph](b, kind) * units_per_launch
+        per_phase[ph] = {"ms_per_launch": round(avg, 4), "launches": cnt,
+                         "share": round(ms / max(sum(v[0] for v in phases.values()), 1e-9), 4),
+                         "achieved_gbs": round(algo / (avg * 1e-3) / 1e9, 2)}
+    dom = max(per_phase, key=lambda k: per_phase[k]["share"]) if per_phase else None
+    launches = sum(v[1] for v in phases.values())
+    roof = None
+    if dom:
+        d = per_phase[dom]
+        traffic = TRAFFIC.get((args.workload, dom))
+        roof = {"bound": "hbm", "kernel": dom, "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": round(d["achieved_gbs"] / hbm, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_unit": ALGO_BYTES[dom](b, kind)}
+    build_ns = b_ms * 1e6 / n
+    qps = 2 * n / (q_ms * 1e-3)
+    out = {
+        "metric": METRIC,
+        "value": round(build_ns, 4),
+        "unit": "ns/key",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][4], "n": n, "b": b, "kind": kind,
+                   "l2": "inputs larger than L2 (no flush)" if 8 * n > 129e6 else "L2 flushed: none (small case)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "shards": int(info.shards), "cells_per_shard": int(info.cells), "lg_seg": int(info.lg_seg),
+                   "c": info.c, "space_overhead": round(info.total_cells / n - 1, 4)},
+        "build_ms": round(b_ms, 3),
+        "query": {"gqps": round(qps / 1e9, 3), "ms_per_2n": round(q_ms, 3)},
+        "e2e": {"value": round(statistics.mean(e2e_b) * 1e6 / n, 4), "unit": "ns/key",
+                "query_gqps": round(2 * n / (statistics.mean(e2e_q) * 1e-3) / 1e9, 3),
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "phases": per_phase,
+        "roofline": roof,
+        "clocks": clk,
+        "check": {"members_ok": ok, "fpr": fpr, "retries": int(info.retries)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, quick=True)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# Per-launch DRAM traffic (bytes) from ncu captures of the same kernels; None
+# until a capture of the current kernel exists.
+TRAFFIC = {}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def oracle_sample(workload: str, quick: bool):
+    """Bounded sample of the workload for the single-thread oracle."""
+    kind, b, n, kk, _ = WORKLOADS[workload]
+    ns = min(n, 4_000_000 if quick else 8_000_000)
+    return kind, b, ns, kk
+
+
+def cpu_baseline(workload: str, quick: bool = True):
+    from oracle import oracle as O
+    from paper_2503_18397_gb300 import synth
+
+    kind, b, ns, kk = oracle_sample(workload, quick)
+    if kk == "u64":
+        keys, offs = synth.u64_keys(0, ns, 3), None
+        other, ooffs = synth.u64_keys(ns, ns, 3), None
+    else:
+        keys, offs = synth.byte_strings(0, ns, 3)
+        other, ooffs = synth.byte_strings(ns, ns, 3)
+    vals = synth.values(ns, b, 3) if kind == "func" else None
+    p = O.default_params(kind=O.FILTER if kind == "filter" else O.FUNC, b=b,
+                         key_kind=O.KEYS_BYTES if offs is not None else O.KEYS_U64, seed=1)
+    t0 = time.perf_counter()
+    st, info, data = O.build(p, keys, vals, offsets=offs)
+    t1 = time.perf_counter()
+    O.query(info, data, keys, offsets=offs)
+    O.query(info, data, other, offsets=ooffs)
+    t2 = time.perf_counter()
+    return {"value": round((t1 - t0) * 1e9 / ns, 3), "unit": "ns/key", "cores": 1, "kind": "oracle",
+            "query_gqps": round(2 * ns / (t2 - t1) / 1e9, 6),
+            "sample": f"oracle build of {ns} keys ({kind}, b={b}, same parameters) + query of {2 * ns} keys "
+                      f"(members + disjoint), single thread"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    O.build_oracle()
+    kind, b, ns, kk = oracle_sample(args.workload, quick=True)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_baseline(args.workload, quick=True)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.workload, quick=True))
+    t1 = time.perf_counter()
+    v = statistics.mean(x["value"] for x in vals)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "ns/key", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round((t1 - t0) * 1e3 / args.steps, 3),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][4], "n": ns, "b": b, "kind": kind},
+           "cpu_baseline": {"value": round(v, 3), "unit": "ns/key", "cores": 1, "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": round(v, 3), "unit": "ns/key", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "query_gqps": statistics.mean(x["query_gqps"] for x in vals)}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

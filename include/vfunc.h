@@ -1,0 +1,148 @@
+/*
+ * vfunc.h -- C ABI of the GB300 (sm_103a) implementation of epsilon-cost-sharded
+ * hypergraph static functions (VFunc) and static filters (VFilter), after
+ * S. Vigna, "epsilon-Cost Sharding: Scaling Hypergraph-Based Static Functions
+ * and Filters to Trillions of Keys" (arXiv 2503.18397).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers to keys, values and outputs may be DEVICE pointers (any CUDA
+ *    allocation of the current device, e.g. a torch tensor's data_ptr()) or
+ *    HOST pointers (pageable or pinned). Host inputs are copied to the device
+ *    inside the call; a host output makes the call wait for its result.
+ *  - The caller owns every buffer it passes. The library owns a vf_struct and
+ *    its device memory until vf_free.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is ordered on it.
+ *  - Every call returns a vf_status and never throws or aborts; CUDA errors map
+ *    to VF_ECUDA and vf_last_error() gives the message of the calling thread.
+ *  - Keys are either 64-bit integers (VF_KEYS_U64, `keys` = uint64_t[n],
+ *    `offsets` = NULL) or byte strings (VF_KEYS_BYTES, `keys` = packed bytes,
+ *    `offsets` = uint64_t[n+1], string i = keys[offsets[i] .. offsets[i+1])).
+ *  - Values / outputs use the narrowest unsigned type that holds b bits:
+ *    uint8_t for b <= 8, uint16_t for b <= 16, uint32_t for b <= 32; only the
+ *    low b bits of a value are stored. Filter query outputs are uint8_t 0/1.
+ */
+#ifndef VFUNC_H
+#define VFUNC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vf_struct vf_struct;
+
+typedef enum {
+    VF_OK = 0,
+    VF_EINVAL = 1,    /* bad argument (b out of 1..32, NULL where data is needed, ...) */
+    VF_ENOMEM = 2,    /* device or host allocation failed */
+    VF_EBUILD = 3,    /* every attempt (seed, seed+1, ..., seed+max_retries) failed */
+    VF_EDUP = 4,      /* duplicate keys with different values make a function impossible */
+    VF_ETIMEOUT = 5,  /* a bounded device-side wait gave up; results are invalid */
+    VF_ECUDA = 6,     /* a CUDA runtime call failed */
+    VF_ECAPACITY = 7  /* a size exceeds a documented limit of this implementation */
+} vf_status;
+
+enum { VF_FUNC = 0, VF_FILTER = 1 };
+enum { VF_KEYS_U64 = 0, VF_KEYS_BYTES = 1 };
+enum { VF_MODE_AUTO = 0, VF_MODE_FUSE = 1, VF_MODE_LGE = 2 };
+enum { VF_REGIME_FUSE = 1, VF_REGIME_LGE = 2 };
+
+/* Build parameters. vf_params_default() fills the paper's defaults. */
+typedef struct {
+    int kind;                /* VF_FUNC (Problem 1) or VF_FILTER (Problem 2) */
+    int b;                   /* value bits (function) or fingerprint bits (filter), 1..32;
+                                a filter's false-positive rate is 2^-b (Sec. 3.1) */
+    int key_kind;            /* VF_KEYS_U64 or VF_KEYS_BYTES */
+    int mode;                /* VF_MODE_AUTO: LGE regime below lge_threshold keys, fuse
+                                regime above (Sec. 4.2); or force one regime */
+    int max_retries;         /* a failed attempt restarts everything with seed+1 (Sec. 4) */
+    uint64_t seed;           /* global seed; there is no per-shard seed (Sec. 4) */
+    double eps;              /* epsilon of epsilon-cost sharding, eq. (ballsbins); 0.001 */
+    double eta;              /* duplicate-edge budget of eq. (logdupfuse); 0.1 */
+    uint64_t lge_threshold;  /* 800000 keys (Sec. 4.2) */
+    uint64_t lge_target;     /* LGE regime: shard bits chosen so mean shard <= this (16384) */
+    uint64_t lge_max_shard;  /* LGE regime: shard bits grow until no shard exceeds this
+                                (24576, the per-CTA solver's capacity) */
+} vf_params;
+
+/* Geometry and outcome of a built structure. */
+typedef struct {
+    uint64_t n;              /* keys given */
+    uint64_t n_eff;          /* keys solved (a filter drops duplicate local signatures) */
+    int kind, b, regime;     /* regime: VF_REGIME_FUSE or VF_REGIME_LGE */
+    int h;                   /* shard bits: 2^h shards on the top signature bits (Sec. 4) */
+    int h_bb, h_dup;         /* eq. (logballsbins) and eq. (logdupfuse); -1 in LGE regime */
+    uint64_t shards;
+    uint64_t M;              /* keys in the largest shard; every shard gets cells for M */
+    double c;                /* expansion factor: 1.105 (large sharded fuse) or 1.12 */
+    int lg_seg;              /* fuse: log2 of the segment size (eq. nln or eq. ln) */
+    uint64_t seg, l, T;      /* fuse: segment size, start segments, segments (l = T - 2) */
+    uint64_t cells;          /* cells per shard; shard s owns cells [s*cells, (s+1)*cells) */
+    uint64_t total_cells;
+    uint64_t data_bytes;     /* size of the data array (b in {8,16,32}: native; else bits) */
+    uint64_t seed;           /* seed of the successful attempt */
+    int retries;             /* failed attempts before it */
+    uint64_t peeled, core;   /* edges peeled / edges solved by elimination (last attempt) */
+} vf_info;
+
+void vf_params_default(vf_params *p);
+
+/* Build a VFunc (values != NULL, kind VF_FUNC) or a VFilter (values == NULL,
+ * kind VF_FILTER) over n keys: hash to 128-bit signatures, shard on the top h
+ * bits (epsilon-cost sharding, Sec. 4), generate each shard's 3-hyperedges
+ * (fuse graph, Sec. 4.2), peel (Sec. 4.3), solve 2-cores by lazy Gaussian
+ * elimination in the LGE regime (Sec. 4.2), assign in reverse peel order.
+ * Waits for completion (the shard sizes and the outcome are read back).
+ * Errors: VF_EINVAL, VF_ENOMEM, VF_EBUILD, VF_ETIMEOUT, VF_ECUDA, VF_ECAPACITY
+ * (a fuse shard above 2^27 keys, or more than 2^32 keys in one call). */
+vf_status vf_build(const void *keys, const uint64_t *offsets, const void *values, uint64_t n,
+                   const vf_params *params, void *stream, vf_struct **out);
+
+/* Query m keys (eq. MWHC with k = 3): shard from the top signature bits, cell
+ * offset shard*cells with no offset array (Sec. 4), XOR of three cells; a
+ * filter compares with the key's fingerprint (Sec. 3.1). For a key outside
+ * the set a function returns an arbitrary but deterministic value (Problem 1).
+ * Asynchronous on `stream` unless a host pointer is involved. */
+vf_status vf_query(const vf_struct *s, const void *keys, const uint64_t *offsets, uint64_t m,
+                   void *out, void *stream);
+
+vf_status vf_get_info(const vf_struct *s, vf_info *info);
+
+/* Parameter planning without building: regime and shard bits for n keys
+ * (eq. logballsbins / logdupfuse, Sec. 4.2) and the geometry a largest shard of
+ * M keys would get. Pure host computation. */
+vf_status vf_plan(const vf_params *params, uint64_t n, uint64_t M, vf_info *out);
+
+/* Device address and size of the data array (read-only for the caller). */
+vf_status vf_data(const vf_struct *s, const void **dev_ptr, uint64_t *bytes);
+
+/* Copy the data array to host memory of at least vf_info.data_bytes bytes. */
+vf_status vf_export(const vf_struct *s, void *host_dst);
+
+/* 128-bit signatures of n keys under `seed` (out: uint64_t[2n], high word
+ * first) -- the first step of build and query, exposed for inspection. */
+vf_status vf_signatures(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n,
+                        uint64_t seed, uint64_t *out, void *stream);
+
+/* Per-phase device timing (CUDA events recorded on the launching stream
+ * around every kernel of build and query). Phases, in order: hash+histogram,
+ * scatter, incidence, peel, assign, LGE solver, query. vf_timing_read waits
+ * for the recorded events, adds their durations (milliseconds) and launch
+ * counts into ms[7] / launches[7], and clears the record. Off by default;
+ * timing serialises nothing but adds event records. Not thread-safe. */
+vf_status vf_timing_enable(int on);
+vf_status vf_timing_read(double *ms, uint64_t *launches);
+
+/* Release a structure (NULL is accepted). */
+vf_status vf_free(vf_struct *s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *vf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,253 @@
+"""ctypes binding of libvfunc (include/vfunc.h): same entry-point names,
+argument marshalling only. Accepts torch tensors (CUDA or CPU) and numpy
+arrays; CUDA tensors are passed as device pointers, everything else as host
+pointers (the library copies host data itself).
+
+There is no CPU fallback: if libvfunc.so has not been built, every call
+raises VFError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is part of the supported environment
+    torch = None
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(HERE, "libvfunc.so")
+
+FUNC, FILTER = 0, 1
+KEYS_U64, KEYS_BYTES = 0, 1
+MODE_AUTO, MODE_FUSE, MODE_LGE = 0, 1, 2
+REGIME_FUSE, REGIME_LGE = 1, 2
+STATUS = {0: "VF_OK", 1: "VF_EINVAL", 2: "VF_ENOMEM", 3: "VF_EBUILD", 4: "VF_EDUP", 5: "VF_ETIMEOUT",
+          6: "VF_ECUDA", 7: "VF_ECAPACITY"}
+
+
+class VFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class VfParams(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int), ("b", C.c_int), ("key_kind", C.c_int), ("mode", C.c_int),
+        ("max_retries", C.c_int), ("seed", C.c_uint64), ("eps", C.c_double), ("eta", C.c_double),
+        ("lge_threshold", C.c_uint64), ("lge_target", C.c_uint64), ("lge_max_shard", C.c_uint64),
+    ]
+
+
+class VfInfo(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint64), ("n_eff", C.c_uint64), ("kind", C.c_int), ("b", C.c_int),
+        ("regime", C.c_int), ("h", C.c_int), ("h_bb", C.c_int), ("h_dup", C.c_int),
+        ("shards", C.c_uint64), ("M", C.c_uint64), ("c", C.c_double), ("lg_seg", C.c_int),
+        ("seg", C.c_uint64), ("l", C.c_uint64), ("T", C.c_uint64), ("cells", C.c_uint64),
+        ("total_cells", C.c_uint64), ("data_bytes", C.c_uint64), ("seed", C.c_uint64),
+        ("retries", C.c_int), ("peeled", C.c_uint64), ("core", C.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+EXPORTS = ["vf_params_default", "vf_build", "vf_query", "vf_get_info", "vf_plan", "vf_data", "vf_export",
+           "vf_signatures", "vf_free", "vf_last_error"]
+
+_lib = None
+
+
+def lib():
+    """Load libvfunc.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(lib_path):
+            raise VFError(6, f"{lib_path} is missing: build it with paper_2503_18397_gb300.build.build()")
+        L = C.CDLL(lib_path)
+        vp, u64, i32 = C.c_void_p, C.c_uint64, C.c_int
+        L.vf_params_default.argtypes = [C.POINTER(VfParams)]
+        L.vf_params_default.restype = None
+        L.vf_build.argtypes = [vp, vp, vp, u64, C.POINTER(VfParams), vp, C.POINTER(vp)]
+        L.vf_query.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.vf_get_info.argtypes = [vp, C.POINTER(VfInfo)]
+        L.vf_plan.argtypes = [C.POINTER(VfParams), u64, u64, C.POINTER(VfInfo)]
+        L.vf_data.argtypes = [vp, C.POINTER(vp), C.POINTER(u64)]
+        L.vf_export.argtypes = [vp, vp]
+        L.vf_signatures.argtypes = [i32, vp, vp, u64, u64, vp, vp]
+        L.vf_free.argtypes = [vp]
+        L.vf_timing_enable.argtypes = [i32]
+        L.vf_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(u64)]
+        L.vf_last_error.argtypes = []
+        L.vf_last_error.restype = C.c_char_p
+        for name in ("vf_build", "vf_query", "vf_get_info", "vf_plan", "vf_data", "vf_export", "vf_signatures",
+                     "vf_free", "vf_timing_enable", "vf_timing_read"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise VFError(st, lib().vf_last_error().decode(errors="replace"))
+
+
+def _is_tensor(x):
+    return torch is not None and isinstance(x, torch.Tensor)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_tensor(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data_as(C.c_void_p)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream, *bufs):
+    if stream is not None:
+        return C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    if torch is not None and any(_is_tensor(b) and b.is_cuda for b in bufs if b is not None):
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return None
+
+
+def _len(keys, offsets):
+    return (len(offsets) - 1) if offsets is not None else len(keys)
+
+
+def vf_params_default(**overrides) -> VfParams:
+    p = VfParams()
+    lib().vf_params_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Structure:
+    """Owning handle of a built vf_struct (released by vf_free / garbage collection)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise VFError(1, "structure already freed")
+        return self._h
+
+    @property
+    def info(self) -> VfInfo:
+        return vf_get_info(self)
+
+    def query(self, keys, offsets=None, out=None, stream=None):
+        return vf_query(self, keys, offsets=offsets, out=out, stream=stream)
+
+    def free(self):
+        if self._h:
+            _check(lib().vf_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def vf_build(keys, values=None, *, offsets=None, params: VfParams | None = None, stream=None, **overrides):
+    """Build a VFunc (values given) or a VFilter (values None, kind=FILTER)."""
+    if params is None:
+        params = vf_params_default()
+        params.kind = FUNC if values is not None else FILTER
+        params.key_kind = KEYS_BYTES if offsets is not None else KEYS_U64
+    for k, v in overrides.items():
+        setattr(params, k, v)
+    n = _len(keys, offsets)
+    out = C.c_void_p()
+    _check(lib().vf_build(_ptr(keys), _ptr(offsets), _ptr(values), n, C.byref(params),
+                          _stream(stream, keys, values, offsets), C.byref(out)))
+    return Structure(out.value)
+
+
+def _out_dtype(info: VfInfo):
+    if info.kind == FILTER or info.b <= 8:
+        return np.uint8
+    return np.uint16 if info.b <= 16 else np.uint32
+
+
+def vf_query(s: Structure, keys, offsets=None, out=None, stream=None):
+    """Query keys; returns `out` (allocated like `keys`: CUDA tensor or numpy)."""
+    m = _len(keys, offsets)
+    if out is None:
+        dt = _out_dtype(vf_get_info(s))
+        if _is_tensor(keys):
+            tdt = {np.uint8: torch.uint8, np.uint16: torch.uint16, np.uint32: torch.uint32}[dt]
+            out = torch.empty(m, dtype=tdt, device=keys.device)
+        else:
+            out = np.empty(m, dtype=dt)
+    _check(lib().vf_query(s.handle, _ptr(keys), _ptr(offsets), m, _ptr(out), _stream(stream, keys, out)))
+    return out
+
+
+def vf_get_info(s: Structure) -> VfInfo:
+    info = VfInfo()
+    _check(lib().vf_get_info(s.handle, C.byref(info)))
+    return info
+
+
+def vf_plan(n: int, M: int, params: VfParams | None = None) -> VfInfo:
+    params = params or vf_params_default()
+    info = VfInfo()
+    _check(lib().vf_plan(C.byref(params), n, M, C.byref(info)))
+    return info
+
+
+def vf_export(s: Structure) -> np.ndarray:
+    info = vf_get_info(s)
+    buf = np.zeros(max(int(info.data_bytes), 1), dtype=np.uint8)
+    _check(lib().vf_export(s.handle, _ptr(buf)))
+    return buf[: info.data_bytes]
+
+
+def vf_signatures(keys, seed: int, offsets=None, out=None, stream=None):
+    """(n, 2) uint64 signatures (column 0 = high word)."""
+    n = _len(keys, offsets)
+    if out is None:
+        if _is_tensor(keys):
+            out = torch.empty((n, 2), dtype=torch.uint64, device=keys.device)
+        else:
+            out = np.empty((n, 2), dtype=np.uint64)
+    kind = KEYS_BYTES if offsets is not None else KEYS_U64
+    _check(lib().vf_signatures(kind, _ptr(keys), _ptr(offsets), n, seed, _ptr(out), _stream(stream, keys, out)))
+    return out
+
+
+def vf_free(s: Structure):
+    s.free()
+
+
+PHASES = ["hash_hist", "scatter", "incidence", "peel", "assign", "lge", "query"]
+
+
+def vf_timing_enable(on: bool = True):
+    _check(lib().vf_timing_enable(1 if on else 0))
+
+
+def vf_timing_read() -> dict:
+    """{phase: (milliseconds, launches)} accumulated since the last read."""
+    ms = (C.c_double * 7)()
+    n = (C.c_uint64 * 7)()
+    _check(lib().vf_timing_read(ms, n))
+    return {p: (ms[i], int(n[i])) for i, p in enumerate(PHASES)}

@@ -1,0 +1,623 @@
+// Host runtime and C ABI of libvfunc: parameter planning (epsilon-cost
+// sharding, fuse geometry), the build pipeline with its retry loop, queries,
+// and structure management. Declarations and contracts: include/vfunc.h.
+#include "vfunc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vf_internal.h"
+
+struct vf_struct {
+    vf_info info;
+    vf::Geom geom;
+    uint8_t* data;  // device, info.data_bytes (+ padding)
+    int device;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+vf_status fail(vf_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define VF_CK(call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(VF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+// Stream-ordered device allocation released on scope exit.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t n, cudaStream_t s) {
+        release();
+        st = s;
+        bytes = n;
+        return cudaMallocAsync(&p, n ? n : 16, s);
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+bool on_device(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------------ timing
+
+enum Phase { kPhHist = 0, kPhScatter, kPhAccum, kPhPeel, kPhAssign, kPhLge, kPhQuery, kNumPhases };
+
+struct TimedLaunch {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+bool g_timing = false;
+std::vector<TimedLaunch> g_timed;
+
+// Records an event before a launch and one after it, on the launch's stream.
+struct PhaseTimer {
+    int phase;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(int ph, cudaStream_t s) : phase(ph), st(s) {
+        if (g_timing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+    }
+    ~PhaseTimer() {
+        if (!a) return;
+        cudaEvent_t b = nullptr;
+        if (cudaEventCreate(&b) == cudaSuccess) {
+            cudaEventRecord(b, st);
+            g_timed.push_back({phase, a, b});
+        } else {
+            cudaEventDestroy(a);
+        }
+    }
+};
+
+// ----------------------------------------------------------------- planning
+
+// Lambert W (principal branch) by Newton's method on f(w) = w e^w - x.
+double lambert_w(double x) {
+    if (x <= 0.0) return 0.0;
+    double w = x < 3.0 ? 0.5 * std::log1p(2.0 * x) : std::log(x) - std::log(std::log(x));
+    for (int k = 0; k < 100; k++) {
+        double e = std::exp(w);
+        double step = (w * e - x) / (e * (w + 1.0));
+        w -= step;
+        if (std::fabs(step) <= 4e-16 * (1.0 + std::fabs(w))) break;
+    }
+    return w;
+}
+
+// eq. (logballsbins) with alpha = 1; no sharding while n eps^2 / 2 <= e.
+int h_ballsbins(uint64_t n, double eps) {
+    const double x = double(n) * eps * eps / 2.0;
+    if (!(x > std::exp(1.0))) return 0;
+    const double h = std::floor(std::log2(x) - std::log2(std::log(x)));
+    return h > 0 ? int(h) : 0;
+}
+
+// eq. (logdupfuse) with the segment-size law eq. (nln): alpha 0.41, beta -3.
+int h_dupfuse(uint64_t n, double eta, double c) {
+    if (n == 0) return 0;
+    const double a = 0.41, b = -3.0;
+    const double t = (std::log2(-double(n) / (2.0 * c * std::log(1.0 - eta))) - 2.0 * b) / (2.0 * a);
+    const double h = std::floor(std::log2(double(n)) - t / (std::log(2.0) * lambert_w(t)));
+    return h > 0 ? int(h) : 0;
+}
+
+void plan_h(const vf_params& p, uint64_t n, vf_info& in) {
+    const bool lge = p.mode == VF_MODE_LGE || (p.mode == VF_MODE_AUTO && n < p.lge_threshold);
+    in.regime = lge ? VF_REGIME_LGE : VF_REGIME_FUSE;
+    if (!lge) {
+        in.h_bb = h_ballsbins(n, p.eps);
+        in.h_dup = h_dupfuse(n, p.eta, 1.105);
+        in.h = std::min(in.h_bb, in.h_dup);
+    } else {
+        in.h_bb = in.h_dup = -1;
+        int h = 0;
+        while (h < 40 && n > (p.lge_target << h)) ++h;
+        in.h = h;
+    }
+}
+
+// Sec. 4.2: c = 1.105 with eq. (nln) segments for sharded shards of at least
+// 10^7 keys; otherwise c = 1.12 (eq. (ln) segments in the fuse regime).
+void geometry(vf_info& in) {
+    const double Mf = double(in.M > 0 ? in.M : 1);
+    if (in.regime == VF_REGIME_LGE) {
+        in.c = 1.12;
+        in.lg_seg = 0;
+        in.seg = in.l = in.T = 0;
+        uint64_t cells = uint64_t(std::ceil(in.c * Mf));
+        in.cells = std::max<uint64_t>(cells, 32);
+    } else {
+        double lg;
+        if (in.h > 0 && in.M >= 10000000ull) {
+            in.c = 1.105;
+            lg = std::floor(0.41 * std::log(Mf) * std::log(std::log(Mf)) - 3.0);
+        } else {
+            in.c = 1.12;
+            lg = std::floor(std::log(Mf) / std::log(3.33) + 2.25);
+        }
+        lg = std::min(32.0, std::max(0.0, lg));
+        in.lg_seg = int(lg);
+        in.seg = uint64_t(1) << in.lg_seg;
+        uint64_t T = uint64_t(std::ceil(in.c * Mf / double(in.seg)));
+        in.T = std::max<uint64_t>(T, 3);
+        in.l = in.T - 2;
+        in.cells = in.T * in.seg;
+    }
+    in.total_cells = in.shards * in.cells;
+    if (in.b == 8 || in.b == 16 || in.b == 32)
+        in.data_bytes = in.total_cells * uint64_t(in.b / 8);
+    else
+        in.data_bytes = ((in.total_cells * uint64_t(in.b) + 63) / 64 + 1) * 8;
+}
+
+vf::Geom make_geom(const vf_info& in) {
+    vf::Geom g;
+    std::memset(&g, 0, sizeof g);
+    g.kh = vf::mix64(in.seed ^ vf::kLaneHi);
+    g.kl = vf::mix64(in.seed ^ vf::kLaneLo);
+    g.cells = in.cells;
+    g.span = in.l * in.seg;
+    g.lg_seg = in.lg_seg;
+    g.h = in.h;
+    g.regime = in.regime;
+    g.b = in.b;
+    g.kind = in.kind;
+    return g;
+}
+
+size_t value_bytes(int b) { return b <= 8 ? 1 : b <= 16 ? 2 : 4; }
+
+// Input staged on the device (a copy when the caller passed host memory).
+struct Staged {
+    const void* keys = nullptr;
+    const uint64_t* offs = nullptr;
+    const void* values = nullptr;
+    uint64_t key_bytes = 0;
+    DevBuf kbuf, obuf, vbuf;
+};
+
+vf_status stage_keys(int key_kind, const void* keys, const uint64_t* offsets, uint64_t n, cudaStream_t st,
+                     Staged& s) {
+    if (key_kind == VF_KEYS_U64) {
+        s.key_bytes = n * 8;
+        if (on_device(keys) || n == 0) {
+            s.keys = keys;
+        } else {
+            VF_CK(s.kbuf.alloc(s.key_bytes, st));
+            VF_CK(cudaMemcpyAsync(s.kbuf.p, keys, s.key_bytes, cudaMemcpyHostToDevice, st));
+            s.keys = s.kbuf.p;
+        }
+        return VF_OK;
+    }
+    const bool offs_dev = on_device(offsets);
+    uint64_t total = 0;
+    if (offs_dev) {
+        VF_CK(cudaMemcpyAsync(&total, offsets + n, 8, cudaMemcpyDeviceToHost, st));
+        VF_CK(cudaStreamSynchronize(st));
+        s.offs = offsets;
+    } else {
+        total = offsets[n];
+        VF_CK(s.obuf.alloc((n + 1) * 8, st));
+        VF_CK(cudaMemcpyAsync(s.obuf.p, offsets, (n + 1) * 8, cudaMemcpyHostToDevice, st));
+        s.offs = s.obuf.as<uint64_t>();
+    }
+    s.key_bytes = total;
+    if (on_device(keys) || total == 0) {
+        s.keys = keys;
+        if (total == 0) {
+            VF_CK(s.kbuf.alloc(16, st));
+            s.keys = s.kbuf.p;
+        }
+    } else {
+        VF_CK(s.kbuf.alloc(total, st));
+        VF_CK(cudaMemcpyAsync(s.kbuf.p, keys, total, cudaMemcpyHostToDevice, st));
+        s.keys = s.kbuf.p;
+    }
+    return VF_OK;
+}
+
+template <class T>
+vf_status h2d(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+    VF_CK(b.alloc(v.size() * sizeof(T), st));
+    VF_CK(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return VF_OK;
+}
+
+// One attempt of the fuse-regime solver. Returns VF_OK, VF_EBUILD (peel
+// failed: the attempt must be retried), or an error.
+vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
+                     const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled) {
+    const uint64_t n = in.n_eff;
+    const uint64_t V = in.total_cells;
+    DevBuf W, claimed, f0, f1, order, roff, ctr;
+    VF_CK(W.alloc(V * 4, st));
+    VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
+    VF_CK(claimed.alloc(((n + 31) / 32) * 4, st));
+    VF_CK(cudaMemsetAsync(claimed.p, 0, ((n + 31) / 32) * 4, st));
+    VF_CK(f0.alloc(V * 4, st));
+    VF_CK(f1.alloc(V * 4, st));
+    VF_CK(order.alloc(std::max<uint64_t>(n, 1) * 4, st));
+    const uint32_t round_cap = uint32_t(std::min<uint64_t>(n + 1, uint64_t(1) << 22));
+    VF_CK(roff.alloc((uint64_t(round_cap) + 1) * 4, st));
+    VF_CK(cudaMemsetAsync(roff.p, 0, 4, st));
+    // counters: 4 x u32, barrier (2 x u32), error word
+    VF_CK(ctr.alloc(64, st));
+    VF_CK(cudaMemsetAsync(ctr.p, 0, 64, st));
+    uint32_t* c32 = ctr.as<uint32_t>();
+    vf::FusePeelBuffers b;
+    b.loc = loc;
+    b.start = start;
+    b.S = uint32_t(in.shards);
+    b.W = W.as<uint32_t>();
+    b.claimed = claimed.as<uint32_t>();
+    b.front0 = f0.as<uint32_t>();
+    b.front1 = f1.as<uint32_t>();
+    b.front_cap = V;
+    b.order = order.as<uint32_t>();
+    b.round_off = roff.as<uint32_t>();
+    b.round_cap = round_cap;
+    b.ctr = c32;
+    b.bar = reinterpret_cast<vf::GridBar*>(c32 + 4);
+    b.err = c32 + 6;
+    {
+        PhaseTimer t(kPhAccum, st);
+        VF_CK(vf::launch_accumulate(loc, n, start, b.S, g, b.W, b.err, st));
+    }
+    {
+        PhaseTimer t(kPhPeel, st);
+        VF_CK(vf::launch_peel(b, g, st));
+    }
+    uint32_t h[8];
+    VF_CK(cudaMemcpyAsync(h, c32, sizeof h, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaStreamSynchronize(st));
+    const uint32_t rounds = h[3], count = h[2], err = h[6];
+    *peeled = count;
+    if (err & vf::kErrTimeout) return fail(VF_ETIMEOUT, "peeling barrier timed out");
+    if (err & (vf::kErrDegOverflow | vf::kErrFrontier)) return VF_EBUILD;
+    if (count != n) return VF_EBUILD;  // non-empty 2-core
+    VF_CK(cudaMemsetAsync(b.bar, 0, 8, st));
+    {
+        PhaseTimer t(kPhAssign, st);
+        VF_CK(vf::launch_assign(b, val, g, rounds, data, st));
+    }
+    uint32_t e2 = 0;
+    VF_CK(cudaMemcpyAsync(&e2, b.err, 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaStreamSynchronize(st));
+    if (e2 & vf::kErrTimeout) return fail(VF_ETIMEOUT, "assignment barrier timed out");
+    return VF_OK;
+}
+
+vf_status solve_lge(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
+                    const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
+                    uint64_t* core) {
+    unsigned grid = vf::lge_grid();
+    grid = unsigned(std::min<uint64_t>(grid, std::max<uint64_t>(in.shards, 1)));
+    const uint32_t m_cap = uint32_t(std::max<uint64_t>(in.M, 1));
+    const uint32_t v_cap = uint32_t(in.cells);
+    const uint64_t per_cta = vf::lge_scratch_words_per_cta(m_cap, v_cap);
+    DevBuf scratch, misc;
+    VF_CK(scratch.alloc(per_cta * grid * 4, st));
+    VF_CK(misc.alloc(64, st));
+    VF_CK(cudaMemsetAsync(misc.p, 0, 64, st));
+    vf::LgeArgs a;
+    a.loc = loc;
+    a.val = val;
+    a.start = start;
+    a.S = uint32_t(in.shards);
+    a.g = g;
+    a.data = data;
+    a.scratch = scratch.as<uint32_t>();
+    a.scratch_words_per_cta = per_cta;
+    a.m_cap = m_cap;
+    a.v_cap = v_cap;
+    a.err = misc.as<uint32_t>();
+    a.stats = misc.as<uint32_t>() + 4;
+    {
+        PhaseTimer t(kPhLge, st);
+        VF_CK(vf::launch_lge(a, grid, st));
+    }
+    uint32_t h[8];
+    VF_CK(cudaMemcpyAsync(h, misc.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaStreamSynchronize(st));
+    *peeled = h[4];
+    *core = h[5];
+    if (h[0] & vf::kErrTimeout) return fail(VF_ETIMEOUT, "LGE solver wait timed out");
+    if (h[0] & vf::kErrCapacity) return fail(VF_ECAPACITY, "LGE shard exceeds the per-CTA solver capacity");
+    if (h[0] & (vf::kErrUnsolvable | vf::kErrDegOverflow | vf::kErrLgeSize)) return VF_EBUILD;
+    return VF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vf_params_default(vf_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->kind = VF_FUNC;
+    p->b = 8;
+    p->key_kind = VF_KEYS_U64;
+    p->mode = VF_MODE_AUTO;
+    p->max_retries = 16;
+    p->seed = 0;
+    p->eps = 0.001;
+    p->eta = 0.1;
+    p->lge_threshold = 800000;
+    p->lge_target = 16384;
+    p->lge_max_shard = 24576;
+}
+
+const char* vf_last_error(void) { return g_last_error.c_str(); }
+
+vf_status vf_plan(const vf_params* p, uint64_t n, uint64_t M, vf_info* out) {
+    if (!p || !out) return fail(VF_EINVAL, "vf_plan: NULL argument");
+    vf_info in;
+    std::memset(&in, 0, sizeof in);
+    in.n = in.n_eff = n;
+    in.kind = p->kind;
+    in.b = p->b;
+    in.seed = p->seed;
+    plan_h(*p, n, in);
+    in.shards = uint64_t(1) << in.h;
+    in.M = M;
+    geometry(in);
+    *out = in;
+    return VF_OK;
+}
+
+vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
+                   const vf_params* params, void* stream, vf_struct** out) {
+    g_last_error.clear();
+    if (!params || !out) return fail(VF_EINVAL, "vf_build: NULL params or out");
+    *out = nullptr;
+    const vf_params p = *params;
+    if (p.b < 1 || p.b > 32) return fail(VF_EINVAL, "b must be in 1..32");
+    if (p.kind != VF_FUNC && p.kind != VF_FILTER) return fail(VF_EINVAL, "bad kind");
+    if (p.key_kind != VF_KEYS_U64 && p.key_kind != VF_KEYS_BYTES) return fail(VF_EINVAL, "bad key_kind");
+    if (n > 0 && !keys) return fail(VF_EINVAL, "keys is NULL");
+    if (p.key_kind == VF_KEYS_BYTES && !offsets) return fail(VF_EINVAL, "offsets is NULL");
+    if (p.kind == VF_FUNC && n > 0 && !values) return fail(VF_EINVAL, "a function needs values");
+    if (!(p.eps > 0.0) || !(p.eta > 0.0 && p.eta < 1.0) || p.max_retries < 0 || p.lge_target == 0 ||
+        p.lge_max_shard < 2)
+        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes");
+    if (n > (uint64_t(1) << 30)) return fail(VF_ECAPACITY, "at most 2^30 keys per vf_build call");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    VF_CK(cudaGetDevice(&dev));
+
+    Staged in_keys;
+    vf_status rs = stage_keys(p.key_kind, keys, offsets, n, st, in_keys);
+    if (rs != VF_OK) return rs;
+    const void* vals_dev = nullptr;
+    if (p.kind == VF_FUNC && n > 0) {
+        if (on_device(values)) {
+            vals_dev = values;
+        } else {
+            VF_CK(in_keys.vbuf.alloc(n * value_bytes(p.b), st));
+            VF_CK(cudaMemcpyAsync(in_keys.vbuf.p, values, n * value_bytes(p.b), cudaMemcpyHostToDevice, st));
+            vals_dev = in_keys.vbuf.p;
+        }
+    }
+
+    DevBuf hist, sigs, loc, val, startb, cursor, data;
+    if (p.key_kind == VF_KEYS_BYTES) VF_CK(sigs.alloc(n * sizeof(vf::Sig), st));
+    VF_CK(loc.alloc(n * 8, st));
+    if (p.kind == VF_FUNC) VF_CK(val.alloc(n * 4, st));
+
+    vf_status last = VF_EBUILD;
+    for (int attempt = 0; attempt <= p.max_retries; attempt++) {
+        vf_info in;
+        std::memset(&in, 0, sizeof in);
+        in.n = in.n_eff = n;
+        in.kind = p.kind;
+        in.b = p.b;
+        in.seed = p.seed + uint64_t(attempt);
+        in.retries = attempt;
+        plan_h(p, n, in);
+        std::vector<uint32_t> counts;
+        for (;;) {
+            in.shards = uint64_t(1) << in.h;
+            vf::Geom g0 = make_geom(in);
+            VF_CK(hist.alloc(in.shards * 4, st));
+            VF_CK(cudaMemsetAsync(hist.p, 0, in.shards * 4, st));
+            {
+                PhaseTimer t(kPhHist, st);
+                VF_CK(vf::launch_hist(p.key_kind, in_keys.keys, in_keys.offs, n, g0, hist.as<uint32_t>(),
+                                      sigs.as<vf::Sig>(), st));
+            }
+            counts.assign(in.shards, 0);
+            VF_CK(cudaMemcpyAsync(counts.data(), hist.p, in.shards * 4, cudaMemcpyDeviceToHost, st));
+            VF_CK(cudaStreamSynchronize(st));
+            in.M = *std::max_element(counts.begin(), counts.end());
+            if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard && in.h < 40) {
+                in.h++;
+                continue;
+            }
+            break;
+        }
+        geometry(in);
+        if (in.regime == VF_REGIME_FUSE && in.M >= (uint64_t(1) << 27))
+            return fail(VF_ECAPACITY, "fuse shard above 2^27 keys");
+        if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard)
+            return fail(VF_ECAPACITY, "LGE shard above lge_max_shard");
+        if (in.total_cells >= (uint64_t(1) << 32)) return fail(VF_ECAPACITY, "more than 2^32 cells");
+        const vf::Geom g = make_geom(in);
+        std::vector<unsigned long long> start(in.shards + 1, 0);
+        for (uint64_t s = 0; s < in.shards; s++) start[s + 1] = start[s] + counts[s];
+        rs = h2d(startb, start, st);
+        if (rs != VF_OK) return rs;
+        VF_CK(cursor.alloc(in.shards * 8, st));
+        VF_CK(cudaMemcpyAsync(cursor.p, startb.p, in.shards * 8, cudaMemcpyDeviceToDevice, st));
+        {
+            PhaseTimer t(kPhScatter, st);
+            VF_CK(vf::launch_scatter(static_cast<const uint64_t*>(in_keys.keys), sigs.as<vf::Sig>(), vals_dev, n, g,
+                                     cursor.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(), st));
+        }
+        VF_CK(data.alloc(in.data_bytes + 16, st));
+        VF_CK(cudaMemsetAsync(data.p, 0, in.data_bytes + 16, st));
+        uint64_t peeled = 0, core = 0;
+        if (in.regime == VF_REGIME_FUSE)
+            rs = solve_fuse(in, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
+                            startb.as<unsigned long long>(), data.as<uint8_t>(), st, &peeled);
+        else
+            rs = solve_lge(in, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
+                           startb.as<unsigned long long>(), data.as<uint8_t>(), st, &peeled, &core);
+        in.peeled = peeled;
+        in.core = in.regime == VF_REGIME_FUSE ? 0 : core;
+        if (rs == VF_OK) {
+            VF_CK(cudaStreamSynchronize(st));
+            vf_struct* s = new vf_struct;
+            s->info = in;
+            s->geom = g;
+            s->data = data.as<uint8_t>();
+            s->device = dev;
+            data.p = nullptr;  // ownership moves to the structure
+            *out = s;
+            return VF_OK;
+        }
+        last = rs;
+        if (rs != VF_EBUILD) return rs;
+    }
+    return fail(last, "all attempts failed (seed .. seed+max_retries)");
+}
+
+vf_status vf_query(const vf_struct* s, const void* keys, const uint64_t* offsets, uint64_t m, void* out,
+                   void* stream) {
+    if (!s) return fail(VF_EINVAL, "vf_query: NULL structure");
+    if (m == 0) return VF_OK;
+    if (!keys || !out) return fail(VF_EINVAL, "vf_query: NULL keys or out");
+    const int key_kind = offsets ? VF_KEYS_BYTES : VF_KEYS_U64;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Staged in_keys;
+    vf_status rs = stage_keys(key_kind, keys, offsets, m, st, in_keys);
+    if (rs != VF_OK) return rs;
+    const size_t ob = s->info.kind == VF_FILTER ? 1 : value_bytes(s->info.b);
+    const bool out_dev = on_device(out);
+    DevBuf obuf;
+    void* dout = out;
+    if (!out_dev) {
+        VF_CK(obuf.alloc(m * ob, st));
+        dout = obuf.p;
+    }
+    {
+        PhaseTimer t(kPhQuery, st);
+        VF_CK(vf::launch_query(key_kind, in_keys.keys, in_keys.offs, m, s->geom, s->data, dout, st));
+    }
+    if (!out_dev) {
+        VF_CK(cudaMemcpyAsync(out, dout, m * ob, cudaMemcpyDeviceToHost, st));
+        VF_CK(cudaStreamSynchronize(st));
+    }
+    return VF_OK;
+}
+
+vf_status vf_get_info(const vf_struct* s, vf_info* info) {
+    if (!s || !info) return fail(VF_EINVAL, "vf_get_info: NULL argument");
+    *info = s->info;
+    return VF_OK;
+}
+
+vf_status vf_data(const vf_struct* s, const void** dev_ptr, uint64_t* bytes) {
+    if (!s || !dev_ptr || !bytes) return fail(VF_EINVAL, "vf_data: NULL argument");
+    *dev_ptr = s->data;
+    *bytes = s->info.data_bytes;
+    return VF_OK;
+}
+
+vf_status vf_export(const vf_struct* s, void* host_dst) {
+    if (!s || !host_dst) return fail(VF_EINVAL, "vf_export: NULL argument");
+    VF_CK(cudaMemcpy(host_dst, s->data, s->info.data_bytes, cudaMemcpyDeviceToHost));
+    return VF_OK;
+}
+
+vf_status vf_signatures(int key_kind, const void* keys, const uint64_t* offsets, uint64_t n, uint64_t seed,
+                        uint64_t* out, void* stream) {
+    if (n == 0) return VF_OK;
+    if (!keys || !out || (key_kind == VF_KEYS_BYTES && !offsets)) return fail(VF_EINVAL, "vf_signatures: NULL");
+    if (key_kind != VF_KEYS_U64 && key_kind != VF_KEYS_BYTES) return fail(VF_EINVAL, "bad key_kind");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Staged in_keys;
+    vf_status rs = stage_keys(key_kind, keys, offsets, n, st, in_keys);
+    if (rs != VF_OK) return rs;
+    const bool out_dev = on_device(out);
+    DevBuf obuf;
+    void* dout = out;
+    if (!out_dev) {
+        VF_CK(obuf.alloc(n * 16, st));
+        dout = obuf.p;
+    }
+    VF_CK(vf::launch_sigs(key_kind, in_keys.keys, in_keys.offs, n, vf::mix64(seed ^ vf::kLaneHi),
+                          vf::mix64(seed ^ vf::kLaneLo), static_cast<vf::Sig*>(dout), st));
+    if (!out_dev) {
+        VF_CK(cudaMemcpyAsync(out, dout, n * 16, cudaMemcpyDeviceToHost, st));
+        VF_CK(cudaStreamSynchronize(st));
+    }
+    return VF_OK;
+}
+
+vf_status vf_timing_enable(int on) {
+    g_timing = on != 0;
+    return VF_OK;
+}
+
+vf_status vf_timing_read(double* ms, uint64_t* launches) {
+    if (!ms || !launches) return fail(VF_EINVAL, "vf_timing_read: NULL argument");
+    vf_status rs = VF_OK;
+    for (auto& t : g_timed) {
+        float x = 0.f;
+        cudaError_t e = cudaEventSynchronize(t.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&x, t.a, t.b);
+        if (e != cudaSuccess) rs = fail(VF_ECUDA, std::string("timing: ") + cudaGetErrorString(e));
+        ms[t.phase] += x;
+        launches[t.phase] += 1;
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    g_timed.clear();
+    return rs;
+}
+
+vf_status vf_free(vf_struct* s) {
+    if (!s) return VF_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != s->device) cudaSetDevice(s->device);
+    cudaError_t e = cudaFree(s->data);
+    if (cur != s->device) cudaSetDevice(cur);
+    delete s;
+    if (e != cudaSuccess) return fail(VF_ECUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
+    return VF_OK;
+}
+
+}  // extern "C"

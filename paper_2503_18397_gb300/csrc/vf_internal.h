@@ -1,0 +1,65 @@
+// Internal declarations shared by the translation units of libvfunc.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vf_device.cuh"
+
+namespace vf {
+
+int num_sms();
+
+// Buffers of the fuse-regime (global-memory) solver for one attempt.
+struct FusePeelBuffers {
+    const uint64_t* loc;              // bucketed local signatures
+    const unsigned long long* start;  // S+1 shard starts
+    uint32_t S;
+    uint32_t* W;                      // S*cells vertex words
+    uint32_t* claimed;                // (n+31)/32 words
+    uint32_t* front0;
+    uint32_t* front1;
+    uint64_t front_cap;
+    uint32_t* order;                  // n entries
+    uint32_t* round_off;              // round_cap+1 entries
+    uint32_t round_cap;
+    uint32_t* ctr;                    // 4 counters
+    GridBar* bar;
+    uint32_t* err;
+};
+
+cudaError_t launch_hist(int key_kind, const void* keys, const uint64_t* offs, uint64_t n, const Geom& g,
+                        uint32_t* hist, Sig* sig_out, cudaStream_t st);
+cudaError_t launch_scatter(const uint64_t* keys_u64, const Sig* sig_in, const void* values, uint64_t n,
+                           const Geom& g, unsigned long long* cursor, uint64_t* loc_out, uint32_t* val_out,
+                           cudaStream_t st);
+cudaError_t launch_sigs(int key_kind, const void* keys, const uint64_t* offs, uint64_t n, uint64_t kh,
+                        uint64_t kl, Sig* out, cudaStream_t st);
+cudaError_t launch_accumulate(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
+                              const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st);
+cudaError_t launch_peel(const FusePeelBuffers& b, const Geom& g, cudaStream_t st);
+cudaError_t launch_assign(const FusePeelBuffers& b, const uint32_t* val, const Geom& g, uint32_t rounds,
+                          uint8_t* data, cudaStream_t st);
+
+// LGE regime: one CTA per shard (peel + lazy Gaussian elimination + assign).
+struct LgeArgs {
+    const uint64_t* loc;
+    const uint32_t* val;              // NULL for a filter
+    const unsigned long long* start;  // S+1
+    uint32_t S;
+    Geom g;
+    uint8_t* data;
+    uint32_t* scratch;                // per-CTA global scratch
+    uint64_t scratch_words_per_cta;
+    uint32_t m_cap, v_cap;            // largest shard / cell count the scratch layout holds
+    uint32_t* err;
+    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] shard counter
+};
+cudaError_t launch_lge(const LgeArgs& a, unsigned grid, cudaStream_t st);
+unsigned lge_grid();
+uint64_t lge_scratch_words_per_cta(uint32_t m_cap, uint32_t v_cap);
+
+cudaError_t launch_query(int key_kind, const void* keys, const uint64_t* offs, uint64_t m, const Geom& g,
+                         const uint8_t* data, void* out, cudaStream_t st);
+
+}  // namespace vf

@@ -1,0 +1,556 @@
+// LGE-regime solver of libvfunc (sm_103a): one CTA per shard, shards taken
+// from a global counter so uneven shards balance across SMs.
+//
+// Per shard, all synchronisation is __syncthreads (no spin-waits):
+//  1. incidence: degree (8-bit lanes) and XOR of shard-local edge indices
+//     (16-bit lanes) per vertex, in shared memory (Sec. 4.3, XOR trick);
+//  2. peeling in synchronous rounds; each round first reads every frontier
+//     vertex's (degree, XOR) and only then removes edges, so a vertex's only
+//     edge is read consistently; edges are claimed with a bit per edge;
+//  3. lazy Gaussian elimination of the 2-core (Sec. 3.3, GOV): variables start
+//     idle; an equation with one idle variable is solved for it and the
+//     variable is eliminated from the other equations; when none is left, the
+//     heaviest idle variables are made active (a batch of ~1% of the open
+//     equations at a time); equations left with no idle variable form the
+//     dense system over the active variables;
+//  4. every solved variable is an affine function of the active ones; the
+//     bit-packed coefficient rows (32 active variables per word) are built
+//     round by round, the dense rows are reduced by Gauss-Jordan elimination
+//     in shared memory (free variables = 0), solved variables are evaluated
+//     forward, and peeled edges are assigned in reverse peel order.
+#include "vf_internal.h"
+
+namespace vf {
+
+constexpr int kLT = 512;
+constexpr uint32_t kMaxActive = 2048;      // active variables per shard
+constexpr uint32_t kLPoolPerKey = 40;      // words of coefficient rows per shard key
+constexpr uint32_t kMaxBatch = 256;
+constexpr uint32_t kLgeSmemWords = 50 * 1024;  // 200 KB dynamic shared memory
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+struct LgeOffsets {
+    uint64_t cev, porder, proff, f0, f1, cand, core, eqst, eqdone, inc_off, inc_cur, inc_list, vstate, act, actv,
+        solves, soff, dense, lc, L, lpool, total;
+};
+
+__host__ __device__ inline uint64_t lge_take(uint64_t& p, uint64_t words) {
+    uint64_t r = p;
+    p += (words + 3) & ~uint64_t(3);
+    return r;
+}
+
+__host__ __device__ inline LgeOffsets lge_offsets(uint32_t m, uint32_t V) {
+    LgeOffsets o;
+    uint64_t p = 0;
+    o.cev = lge_take(p, 3ull * m);
+    o.porder = lge_take(p, m);
+    o.proff = lge_take(p, V + 2ull);
+    o.f0 = lge_take(p, V);
+    o.f1 = lge_take(p, V);
+    o.cand = lge_take(p, V);
+    o.core = lge_take(p, m);
+    o.eqst = lge_take(p, m);
+    o.eqdone = lge_take(p, m);
+    o.inc_off = lge_take(p, V + 1ull);
+    o.inc_cur = lge_take(p, V);
+    o.inc_list = lge_take(p, 3ull * m);
+    o.vstate = lge_take(p, V);
+    o.act = lge_take(p, V);
+    o.actv = lge_take(p, kMaxActive);
+    o.solves = lge_take(p, m);
+    o.soff = lge_take(p, uint64_t(m) + V + 4);
+    o.dense = lge_take(p, m);
+    o.lc = lge_take(p, m);
+    o.lpool = uint64_t(m) * kLPoolPerKey + 4096;
+    o.L = lge_take(p, o.lpool);
+    o.total = p;
+    return o;
+}
+
+uint64_t lge_scratch_words_per_cta(uint32_t m_cap, uint32_t v_cap) { return lge_offsets(m_cap, v_cap).total; }
+
+__device__ __forceinline__ uint32_t rhs_of(const LgeArgs& a, uint64_t ge) {
+    return a.val ? __ldg(a.val + ge) : fingerprint(__ldg(a.loc + ge), a.g.b);
+}
+
+__device__ __forceinline__ uint32_t deg_of(const uint32_t* degw, uint32_t v) {
+    return (degw[v >> 2] >> ((v & 3u) * 8u)) & 255u;
+}
+__device__ __forceinline__ uint32_t xr_of(const uint32_t* xrw, uint32_t v) {
+    return (xrw[v >> 1] >> ((v & 1u) * 16u)) & 0xFFFFu;
+}
+
+// Inclusive-to-exclusive scan of arr[0..len) in global memory by one CTA.
+__device__ void cta_exclusive_scan(uint32_t* arr, uint32_t len, uint32_t* s_part) {
+    const uint32_t T = blockDim.x, tid = threadIdx.x;
+    const uint32_t chunk = (len + T - 1) / T;
+    const uint32_t lo = min(len, tid * chunk), hi = min(len, lo + chunk);
+    uint32_t sum = 0;
+    for (uint32_t i = lo; i < hi; i++) sum += arr[i];
+    s_part[tid] = sum;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (uint32_t t = 0; t < T; t++) {
+            uint32_t x = s_part[t];
+            s_part[t] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    uint32_t run = s_part[tid];
+    for (uint32_t i = lo; i < hi; i++) {
+        uint32_t x = arr[i];
+        arr[i] = run;
+        run += x;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t s_shard, s_fail;
+    __shared__ uint32_t s_cnt[4];
+    __shared__ uint32_t s_C, s_rem, s_A, s_S, s_D, s_r, s_apos, s_nact, s_nbatch, s_piv;
+    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_batch[kMaxBatch];
+    __shared__ uint32_t s_part[kLT];
+
+    const uint32_t tid = threadIdx.x, T = blockDim.x;
+    const LgeOffsets o = lge_offsets(a.m_cap, a.v_cap);
+    uint32_t* scr = a.scratch + uint64_t(blockIdx.x) * a.scratch_words_per_cta;
+    uint32_t* cev = scr + o.cev;
+    uint32_t* porder = scr + o.porder;
+    uint32_t* proff = scr + o.proff;
+    uint32_t* fr[2] = {scr + o.f0, scr + o.f1};
+    uint32_t* cand = scr + o.cand;
+    uint32_t* core = scr + o.core;
+    uint32_t* eqst = scr + o.eqst;
+    uint32_t* eqdone = scr + o.eqdone;
+    uint32_t* inc_off = scr + o.inc_off;
+    uint32_t* inc_cur = scr + o.inc_cur;
+    uint32_t* inc_list = scr + o.inc_list;
+    uint32_t* vstate = scr + o.vstate;
+    uint32_t* act = scr + o.act;
+    uint32_t* actv = scr + o.actv;
+    uint32_t* solves = scr + o.solves;
+    uint32_t* soff = scr + o.soff;
+    uint32_t* dense = scr + o.dense;
+    uint32_t* lc = scr + o.lc;
+    uint32_t* L = scr + o.L;
+    const int b = a.g.b;
+
+    for (;;) {
+        if (tid == 0) {
+            uint32_t bad = *reinterpret_cast<volatile uint32_t*>(a.err) & (kErrUnsolvable | kErrCapacity | kErrLgeSize |
+                                                                         kErrDegOverflow);
+            s_shard = bad ? kNone : atomicAdd(&a.stats[2], 1u);
+            s_fail = 0;
+        }
+        __syncthreads();
+        const uint32_t s = s_shard;
+        if (s >= a.S) break;
+        const uint64_t e0 = a.start[s];
+        const uint32_t m = uint32_t(a.start[s + 1] - e0);
+        const uint32_t V = uint32_t(a.g.cells);
+        const uint64_t cbase = uint64_t(s) * a.g.cells;
+        if (m > a.m_cap || V > a.v_cap || V > 65535u) {
+            if (tid == 0) atomicOr(a.err, kErrCapacity);
+            __syncthreads();
+            continue;
+        }
+
+        // ---------------------------------------------------------------- 1. incidence
+        uint32_t* degw = sm;
+        uint32_t* xrw = degw + (V + 3) / 4;
+        uint32_t* clm = xrw + (V + 1) / 2;
+        const uint32_t pw = (V + 3) / 4 + (V + 1) / 2 + (m + 31) / 32;
+        for (uint32_t i = tid; i < pw; i += T) sm[i] = 0;
+        __syncthreads();
+        for (uint32_t e = tid; e < m; e += T) {
+            uint64_t v[3];
+            edge_of(a.g, __ldg(a.loc + e0 + e), v);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                uint32_t vk = uint32_t(v[k]);
+                cev[3 * e + k] = vk;
+                uint32_t sh8 = (vk & 3u) * 8u;
+                uint32_t old = atomicAdd(&degw[vk >> 2], 1u << sh8);
+                if (((old >> sh8) & 255u) == 255u) s_fail = 1;
+                atomicXor(&xrw[vk >> 1], e << ((vk & 1u) * 16u));
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            if (tid == 0) atomicOr(a.err, kErrDegOverflow);
+            __syncthreads();
+            continue;
+        }
+
+        // -------------------------------------------------------------------- 2. peel
+        if (tid == 0) {
+            s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
+            proff[0] = 0;
+        }
+        __syncthreads();
+        for (uint32_t v = tid; v < V; v += T)
+            if (deg_of(degw, v) == 1u) fr[0][atomicAdd(&s_cnt[0], 1u)] = v;
+        __syncthreads();
+        uint32_t fi = 0;
+        for (;;) {
+            const uint32_t nF = s_cnt[fi];
+            if (nF == 0) break;
+            const uint32_t* F = fr[fi];
+            uint32_t* G = fr[fi ^ 1];
+            for (uint32_t i = tid; i < nF; i += T) {
+                uint32_t v = F[i];
+                cand[i] = deg_of(degw, v) == 1u ? xr_of(xrw, v) : kNone;
+            }
+            __syncthreads();
+            for (uint32_t i = tid; i < nF; i += T) {
+                uint32_t e = cand[i];
+                if (e == kNone) continue;
+                uint32_t bit = 1u << (e & 31u);
+                if (atomicOr(&clm[e >> 5], bit) & bit) continue;
+                uint32_t v = F[i];
+                uint32_t side = cev[3 * e] == v ? 0u : cev[3 * e + 1] == v ? 1u : 2u;
+                porder[atomicAdd(&s_cnt[2], 1u)] = (e << 2) | side;
+#pragma unroll
+                for (uint32_t k = 0; k < 3; k++) {
+                    if (k == side) continue;
+                    uint32_t u = cev[3 * e + k];
+                    uint32_t sh8 = (u & 3u) * 8u;
+                    uint32_t old = atomicSub(&degw[u >> 2], 1u << sh8);
+                    atomicXor(&xrw[u >> 1], e << ((u & 1u) * 16u));
+                    if (((old >> sh8) & 255u) == 2u) G[atomicAdd(&s_cnt[fi ^ 1], 1u)] = u;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_cnt[3]++;
+                proff[s_cnt[3]] = s_cnt[2];
+                s_cnt[fi] = 0;
+            }
+            fi ^= 1;
+            __syncthreads();
+        }
+        const uint32_t peeled = s_cnt[2];
+        const uint32_t prounds = s_cnt[3];
+
+        // ---------------------------------------------------- 3. lazy Gaussian elimination
+        uint32_t C = 0;
+        if (peeled < m) {
+            if (tid == 0) s_C = 0;
+            __syncthreads();
+            for (uint32_t e = tid; e < m; e += T)
+                if (!((clm[e >> 5] >> (e & 31u)) & 1u)) core[atomicAdd(&s_C, 1u)] = e;
+            for (uint32_t v = tid; v <= V; v += T) inc_off[v] = 0;
+            __syncthreads();
+            C = s_C;
+            for (uint32_t j = tid; j < C; j += T) {
+                const uint32_t* ev = cev + 3 * core[j];
+                atomicAdd(&inc_off[ev[0]], 1u);
+                atomicAdd(&inc_off[ev[1]], 1u);
+                atomicAdd(&inc_off[ev[2]], 1u);
+                eqst[j] = ((ev[0] ^ ev[1] ^ ev[2]) << 2) | 3u;
+                eqdone[j] = 0;
+            }
+            for (uint32_t i = tid; i < 256; i += T) s_hist[i] = 0;
+            __syncthreads();
+            // activation order: core degree, heaviest first (counting sort)
+            for (uint32_t v = tid; v < V; v += T) {
+                uint32_t d = inc_off[v];
+                vstate[v] = 0;
+                if (d) atomicAdd(&s_hist[min(d, 255u)], 1u);
+            }
+            cta_exclusive_scan(inc_off, V + 1, s_part);
+            for (uint32_t v = tid; v < V; v += T) inc_cur[v] = inc_off[v];
+            if (tid == 0) {
+                uint32_t run = 0;
+                for (int d = 255; d >= 1; d--) {
+                    uint32_t x = s_hist[d];
+                    s_hist[d] = run;
+                    run += x;
+                }
+                s_nact = run;
+            }
+            __syncthreads();
+            for (uint32_t v = tid; v < V; v += T) {
+                uint32_t d = inc_off[v + 1] - inc_off[v];
+                if (d) act[atomicAdd(&s_hist[min(d, 255u)], 1u)] = v;
+            }
+            for (uint32_t j = tid; j < C; j += T) {
+                const uint32_t* ev = cev + 3 * core[j];
+                inc_list[atomicAdd(&inc_cur[ev[0]], 1u)] = j;
+                inc_list[atomicAdd(&inc_cur[ev[1]], 1u)] = j;
+                inc_list[atomicAdd(&inc_cur[ev[2]], 1u)] = j;
+            }
+            if (tid == 0) {
+                s_rem = C;
+                s_A = s_S = s_D = s_r = s_apos = 0;
+                s_cnt[0] = s_cnt[1] = 0;
+                soff[0] = 0;
+            }
+            fi = 0;
+            const uint32_t max_rounds = m + V + 2;
+            __syncthreads();
+            for (;;) {
+                if (s_rem == 0 || s_fail) break;
+                if (s_r >= max_rounds) {
+                    if (tid == 0) s_fail = 2;
+                    __syncthreads();
+                    break;
+                }
+                const uint32_t nF = s_cnt[fi];
+                uint32_t* G = fr[fi ^ 1];
+                if (nF == 0) {
+                    // activate the next heaviest idle variables that still occur in open equations
+                    if (tid == 0) {
+                        uint32_t K = max(1u, min(kMaxBatch, s_rem / 100u));
+                        uint32_t nb = 0;
+                        while (nb < K && s_apos < s_nact) {
+                            uint32_t v = act[s_apos++];
+                            if (vstate[v] != 0) continue;
+                            bool live = false;
+                            for (uint32_t q = inc_off[v]; q < inc_off[v + 1] && !live; q++)
+                                live = eqdone[inc_list[q]] == 0;
+                            if (live) s_batch[nb++] = v;
+                        }
+                        s_nbatch = nb;
+                        if (nb == 0 || s_A + nb > kMaxActive) s_fail = 2;
+                    }
+                    __syncthreads();
+                    if (s_fail) break;
+                    const uint32_t nb = s_nbatch, abase = s_A;
+                    for (uint32_t i = tid; i < nb; i += T) {
+                        uint32_t v = s_batch[i];
+                        vstate[v] = 1u | ((abase + i) << 2);
+                        actv[abase + i] = v;
+                        for (uint32_t q = inc_off[v]; q < inc_off[v + 1]; q++) {
+                            uint32_t k = inc_list[q];
+                            if (eqdone[k]) continue;
+                            uint32_t old = atomicSub(&eqst[k], 1u);
+                            atomicXor(&eqst[k], v << 2);
+                            uint32_t c = (old & 3u) - 1u;
+                            if (c == 1u) {
+                                G[atomicAdd(&s_cnt[fi ^ 1], 1u)] = k;
+                            } else if (c == 0u) {
+                                eqdone[k] = 1;
+                                dense[atomicAdd(&s_D, 1u)] = k;
+                                atomicSub(&s_rem, 1u);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    if (tid == 0) s_A += nb;
+                } else {
+                    const uint32_t* F = fr[fi];
+                    const uint32_t lo = s_S;
+                    for (uint32_t i = tid; i < nF; i += T) {
+                        uint32_t j = F[i];
+                        if (eqdone[j]) continue;
+                        uint32_t w = eqst[j];
+                        if ((w & 3u) != 1u) continue;
+                        uint32_t x = w >> 2;
+                        if (atomicCAS(&vstate[x], 0u, 3u) != 0u) continue;
+                        uint32_t si = atomicAdd(&s_S, 1u);
+                        vstate[x] = 2u | (si << 2);
+                        solves[si] = (j << 16) | x;
+                        eqdone[j] = 1;
+                        atomicSub(&s_rem, 1u);
+                    }
+                    __syncthreads();
+                    const uint32_t hi = s_S;
+                    for (uint32_t si = lo + tid; si < hi; si += T) {
+                        uint32_t j = solves[si] >> 16, x = solves[si] & 0xFFFFu;
+                        for (uint32_t q = inc_off[x]; q < inc_off[x + 1]; q++) {
+                            uint32_t k = inc_list[q];
+                            if (k == j || eqdone[k]) continue;
+                            uint32_t old = atomicSub(&eqst[k], 1u);
+                            atomicXor(&eqst[k], x << 2);
+                            uint32_t c = (old & 3u) - 1u;
+                            if (c == 1u) {
+                                G[atomicAdd(&s_cnt[fi ^ 1], 1u)] = k;
+                            } else if (c == 0u) {
+                                eqdone[k] = 1;
+                                dense[atomicAdd(&s_D, 1u)] = k;
+                                atomicSub(&s_rem, 1u);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (tid == 0) {
+                    s_r++;
+                    soff[s_r] = s_S;
+                    s_cnt[fi] = 0;
+                }
+                fi ^= 1;
+                __syncthreads();
+            }
+            if (s_fail) {
+                if (tid == 0) atomicOr(a.err, kErrLgeSize);
+                __syncthreads();
+                continue;
+            }
+            const uint32_t A = s_A, S = s_S, D = s_D, R = s_r;
+            const uint32_t AW = (A + 31) / 32;
+            const uint32_t RS = AW | 1u;  // odd row stride: conflict-free shared-memory rows
+            if (uint64_t(S) * AW > o.lpool || uint64_t(D) * RS + 2ull * D + A > kLgeSmemWords) {
+                if (tid == 0) atomicOr(a.err, kErrLgeSize);
+                __syncthreads();
+                continue;
+            }
+            // solved variables as affine functions of the active ones, round by round
+            for (uint32_t r = 0; r < R; r++) {
+                const uint32_t lo = soff[r], hi = soff[r + 1];
+                if (hi == lo) continue;
+                const uint32_t items = (hi - lo) * AW;
+                for (uint32_t it = tid; it < items; it += T) {
+                    const uint32_t si = lo + it / AW, w = it % AW;
+                    const uint32_t j = solves[si] >> 16, x = solves[si] & 0xFFFFu;
+                    const uint32_t e = core[j];
+                    uint32_t acc = 0, c = 0;
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        uint32_t u = cev[3 * e + k];
+                        if (u == x) continue;
+                        uint32_t st = vstate[u];
+                        if ((st & 3u) == 1u) {
+                            uint32_t ai = st >> 2;
+                            if ((ai >> 5) == w) acc |= 1u << (ai & 31u);
+                        } else {
+                            acc ^= L[uint64_t(st >> 2) * AW + w];
+                            c ^= lc[st >> 2];
+                        }
+                    }
+                    L[uint64_t(si) * AW + w] = acc;
+                    if (w == 0) lc[si] = c ^ rhs_of(a, e0 + e);
+                }
+                __syncthreads();
+            }
+            // dense rows in shared memory
+            uint32_t* rows = sm;
+            uint32_t* rhs = rows + uint64_t(D) * RS;
+            uint32_t* pivf = rhs + D;
+            uint32_t* colrow = pivf + D;
+            for (uint32_t it = tid; it < D * AW; it += T) {
+                const uint32_t d = it / AW, w = it % AW;
+                const uint32_t e = core[dense[d]];
+                uint32_t acc = 0, c = 0;
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    uint32_t st = vstate[cev[3 * e + k]];
+                    if ((st & 3u) == 1u) {
+                        uint32_t ai = st >> 2;
+                        if ((ai >> 5) == w) acc |= 1u << (ai & 31u);
+                    } else {
+                        acc ^= L[uint64_t(st >> 2) * AW + w];
+                        c ^= lc[st >> 2];
+                    }
+                }
+                rows[d * RS + w] = acc;
+                if (w == 0) {
+                    rhs[d] = c ^ rhs_of(a, e0 + e);
+                    pivf[d] = 0;
+                }
+            }
+            for (uint32_t c = tid; c < A; c += T) colrow[c] = kNone;
+            __syncthreads();
+            // Gauss-Jordan over GF(2): pivot = lowest unused row with the column bit
+            for (uint32_t col = 0; col < A; col++) {
+                const uint32_t cw = col >> 5, cb = 1u << (col & 31u);
+                if (tid == 0) s_piv = kNone;
+                __syncthreads();
+                for (uint32_t d = tid; d < D; d += T)
+                    if (!pivf[d] && (rows[d * RS + cw] & cb)) atomicMin(&s_piv, d);
+                __syncthreads();
+                const uint32_t p = s_piv;
+                if (p == kNone) {
+                    __syncthreads();
+                    continue;
+                }
+                for (uint32_t d = tid; d < D; d += T) {
+                    if (d == p || !(rows[d * RS + cw] & cb)) continue;
+                    for (uint32_t w = cw; w < AW; w++) rows[d * RS + w] ^= rows[p * RS + w];
+                    rhs[d] ^= rhs[p];
+                }
+                if (tid == 0) {
+                    pivf[p] = 1;
+                    colrow[col] = p;
+                }
+                __syncthreads();
+            }
+            for (uint32_t d = tid; d < D; d += T)
+                if (!pivf[d] && rhs[d] != 0) s_fail = 1;
+            __syncthreads();
+            if (s_fail) {
+                if (tid == 0) atomicOr(a.err, kErrUnsolvable);
+                __syncthreads();
+                continue;
+            }
+            for (uint32_t c = tid; c < A; c += T)
+                cell_put_zero(a.data, b, cbase + actv[c], colrow[c] != kNone ? rhs[colrow[c]] : 0u);
+            __syncthreads();
+            // solved variables, in solve order (their equations as generated)
+            for (uint32_t r = 0; r < R; r++) {
+                const uint32_t lo = soff[r], hi = soff[r + 1];
+                if (hi == lo) continue;
+                for (uint32_t si = lo + tid; si < hi; si += T) {
+                    const uint32_t j = solves[si] >> 16, x = solves[si] & 0xFFFFu;
+                    const uint32_t e = core[j];
+                    uint32_t val = rhs_of(a, e0 + e);
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        uint32_t u = cev[3 * e + k];
+                        if (u != x) val ^= cell_get_cg(a.data, b, cbase + u);
+                    }
+                    cell_put_zero(a.data, b, cbase + x, val);
+                }
+                __syncthreads();
+            }
+        }
+
+        // -------------------------------------------- 4. reverse peel-order assignment
+        for (uint32_t r = prounds; r-- > 0;) {
+            const uint32_t lo = proff[r], hi = proff[r + 1];
+            for (uint32_t i = lo + tid; i < hi; i += T) {
+                const uint32_t ent = porder[i];
+                const uint32_t e = ent >> 2, side = ent & 3u;
+                uint32_t val = rhs_of(a, e0 + e);
+#pragma unroll
+                for (uint32_t k = 0; k < 3; k++)
+                    if (k != side) val ^= cell_get_cg(a.data, b, cbase + cev[3 * e + k]);
+                cell_put_zero(a.data, b, cbase + cev[3 * e + side], val);
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            atomicAdd(&a.stats[0], peeled);
+            atomicAdd(&a.stats[1], C);
+        }
+        __syncthreads();
+    }
+}
+
+unsigned lge_grid() {
+    static unsigned g = 0;
+    if (g == 0) {
+        cudaFuncSetAttribute(k_lge, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLgeSmemWords * 4));
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lge, kLT, kLgeSmemWords * 4);
+        if (per_sm < 1) per_sm = 1;
+        g = unsigned(per_sm) * unsigned(num_sms());
+    }
+    return g;
+}
+
+cudaError_t launch_lge(const LgeArgs& a, unsigned grid, cudaStream_t st) {
+    if (a.S == 0) return cudaSuccess;
+    lge_grid();
+    k_lge<<<grid, kLT, kLgeSmemWords * 4, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace vf

@@ -1,0 +1,106 @@
+// Query kernel of libvfunc (sm_103a): signature -> shard (top h bits) ->
+// cell offset shard*cells (no offset array, Sec. 4) -> three cells -> XOR
+// (eq. MWHC, k = 3) -> [filter: compare with the fingerprint].
+//
+// Each thread takes kQ keys spaced one grid-stride apart (coalesced key loads)
+// and issues all 3*kQ cell loads before using any, so every warp keeps 96
+// independent random 32-byte sector reads in flight.
+#include "vf_internal.h"
+
+namespace vf {
+
+constexpr int kQThreads = 256;
+constexpr int kQ = 4;
+
+template <int WIDTH>
+__device__ __forceinline__ uint32_t cell_q(const uint8_t* data, int b, uint64_t i) {
+    if constexpr (WIDTH == 8) return __ldg(data + i);
+    else if constexpr (WIDTH == 16) return __ldg(reinterpret_cast<const uint16_t*>(data) + i);
+    else if constexpr (WIDTH == 32) return __ldg(reinterpret_cast<const uint32_t*>(data) + i);
+    else return cell_get_nc(data, b, i);
+}
+
+template <int WIDTH, bool FILTER, bool BYTES>
+__global__ void __launch_bounds__(kQThreads) k_query(const void* __restrict__ keys, const uint64_t* __restrict__ offs,
+                                                     uint64_t m, Geom g, const uint8_t* __restrict__ data,
+                                                     void* __restrict__ out) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint64_t total = BYTES ? __ldg(offs + m) : 0;
+    for (uint64_t i0 = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i0 < m; i0 += stride * kQ) {
+        uint64_t idx[kQ], loc[kQ], cell[kQ][3];
+        bool ok[kQ];
+#pragma unroll
+        for (int k = 0; k < kQ; k++) {
+            idx[k] = i0 + uint64_t(k) * stride;
+            ok[k] = idx[k] < m;
+            Sig s{0, 0};
+            if (ok[k]) {
+                if constexpr (BYTES) {
+                    uint64_t o0 = __ldg(offs + idx[k]), o1 = __ldg(offs + idx[k] + 1);
+                    s = sig_bytes(static_cast<const uint8_t*>(keys), total, o0, o1 - o0, g.kh, g.kl);
+                } else {
+                    s = sig_u64(__ldg(static_cast<const uint64_t*>(keys) + idx[k]), g.kh, g.kl);
+                }
+            }
+            uint64_t base = shard_of(s, g.h) * g.cells;
+            loc[k] = local_of(s, g.h);
+            uint64_t v[3];
+            edge_of(g, loc[k], v);
+            cell[k][0] = base + v[0];
+            cell[k][1] = base + v[1];
+            cell[k][2] = base + v[2];
+        }
+        uint32_t x[kQ][3];
+#pragma unroll
+        for (int k = 0; k < kQ; k++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) x[k][j] = ok[k] ? cell_q<WIDTH>(data, g.b, cell[k][j]) : 0u;
+#pragma unroll
+        for (int k = 0; k < kQ; k++) {
+            if (!ok[k]) continue;
+            uint32_t r = x[k][0] ^ x[k][1] ^ x[k][2];
+            if constexpr (FILTER) {
+                static_cast<uint8_t*>(out)[idx[k]] = uint8_t(r == fingerprint(loc[k], g.b));
+            } else {
+                if (g.b <= 8) static_cast<uint8_t*>(out)[idx[k]] = uint8_t(r);
+                else if (g.b <= 16) static_cast<uint16_t*>(out)[idx[k]] = uint16_t(r);
+                else static_cast<uint32_t*>(out)[idx[k]] = r;
+            }
+        }
+    }
+}
+
+template <int WIDTH, bool FILTER>
+static void launch_q(bool bytes, const void* keys, const uint64_t* offs, uint64_t m, const Geom& g,
+                     const uint8_t* data, void* out, cudaStream_t st) {
+    uint64_t blocks = (m + uint64_t(kQThreads) * kQ - 1) / (uint64_t(kQThreads) * kQ);
+    uint64_t cap = uint64_t(num_sms()) * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (bytes)
+        k_query<WIDTH, FILTER, true><<<unsigned(blocks), kQThreads, 0, st>>>(keys, offs, m, g, data, out);
+    else
+        k_query<WIDTH, FILTER, false><<<unsigned(blocks), kQThreads, 0, st>>>(keys, offs, m, g, data, out);
+}
+
+template <bool FILTER>
+static void launch_w(bool bytes, const void* keys, const uint64_t* offs, uint64_t m, const Geom& g,
+                     const uint8_t* data, void* out, cudaStream_t st) {
+    switch (g.b) {
+        case 8: launch_q<8, FILTER>(bytes, keys, offs, m, g, data, out, st); break;
+        case 16: launch_q<16, FILTER>(bytes, keys, offs, m, g, data, out, st); break;
+        case 32: launch_q<32, FILTER>(bytes, keys, offs, m, g, data, out, st); break;
+        default: launch_q<0, FILTER>(bytes, keys, offs, m, g, data, out, st); break;
+    }
+}
+
+cudaError_t launch_query(int key_kind, const void* keys, const uint64_t* offs, uint64_t m, const Geom& g,
+                         const uint8_t* data, void* out, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    bool bytes = key_kind != 0;
+    if (g.kind == 1) launch_w<true>(bytes, keys, offs, m, g, data, out, st);
+    else launch_w<false>(bytes, keys, offs, m, g, data, out, st);
+    return cudaGetLastError();
+}
+
+}  // namespace vf

@@ -1,0 +1,84 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads,
+exports every entry point include/vfunc.h declares, and its parameter
+planning (pure host code) agrees with the oracle's."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def vf():
+    from paper_2503_18397_gb300 import build
+
+    build.build()
+    import paper_2503_18397_gb300 as vf
+
+    vf.lib()
+    return vf
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(vf_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(vf):
+    names = declared_functions()
+    assert "vf_build" in names and "vf_query" in names
+    for name in names:
+        assert hasattr(vf.lib(), name), name
+
+
+def test_params_default_match_paper(vf, orc):
+    p = vf.vf_params_default()
+    o = orc.default_params()
+    for f, _ in vf.VfParams._fields_:
+        assert getattr(p, f) == getattr(o, f), f
+    assert p.eps == 0.001 and p.lge_threshold == 800000
+
+
+def _plan_pair(vf, orc, n, M, **kw):
+    p = vf.vf_params_default(**kw)
+    info = vf.vf_plan(n, M, p)
+    op = orc.default_params(**kw)
+    h, regime, h_bb, h_dup = orc.plan_h(op, n)
+    g = orc.geometry(regime, h, M, b=kw.get("b", 8))
+    return info, (h, regime, h_bb, h_dup), g
+
+
+FIELDS = ["shards", "c", "lg_seg", "seg", "l", "T", "cells", "total_cells", "data_bytes"]
+
+
+def test_plan_matches_oracle_over_many_sizes(vf, orc):
+    rng = np.random.default_rng(0)
+    ns = sorted(set([0, 1, 2, 1000, 799_999, 800_000, 2**20, 10**7, 10**8, 5 * 10**9, 10**10, 10**11, 10**12]
+                    + [int(10 ** x) for x in rng.uniform(0, 13, 400)]))
+    for n in ns:
+        for b in (1, 8, 13, 32):
+            mean = n / (1 << max(0, 0))
+            info, (h, regime, h_bb, h_dup), _ = _plan_pair(vf, orc, n, 1, b=b)
+            assert (info.h, info.regime, info.h_bb, info.h_dup) == (h, regime, h_bb, h_dup), n
+            M = int(n / (1 << h) + math.sqrt(max(n / (1 << h), 1)) * 3)
+            info, _, g = _plan_pair(vf, orc, n, M, b=b)
+            for f in FIELDS:
+                assert getattr(info, f) == getattr(g, f), (n, b, f)
+
+
+def test_plan_forced_regimes(vf, orc):
+    for mode in (1, 2):
+        for n in (10, 5000, 123_456, 10**7):
+            info, (h, regime, _, _), g = _plan_pair(vf, orc, n, max(n // 3, 1), mode=mode)
+            assert info.h == h and info.regime == regime
+            for f in FIELDS:
+                assert getattr(info, f) == getattr(g, f)

@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact: signatures; shard bits, largest shard, geometry, seed and retries of
+every build; every member key decodes to its value (function) or is accepted
+(filter); and for arbitrary keys the GPU query equals the oracle's query on the
+same (GPU-built) data array byte for byte. The data array itself may differ
+from the oracle's where the peel order differs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_18397_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+_NP2T = {np.uint8: torch.uint8, np.int64: torch.int64}
+
+
+@pytest.fixture(scope="module")
+def vf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_18397_gb300 import build
+
+    build.build()
+    import paper_2503_18397_gb300 as vf
+
+    vf.lib()
+    return vf
+
+
+def dev(a: np.ndarray):
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).cuda()
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.view(np.int16)).cuda().view(torch.uint16)
+    if a.dtype == np.uint32:
+        return torch.from_numpy(a.view(np.int32)).cuda().view(torch.uint32)
+    return torch.from_numpy(a).cuda()
+
+
+def host(t) -> np.ndarray:
+    m = {torch.uint16: (torch.int16, np.uint16), torch.uint32: (torch.int32, np.uint32),
+         torch.uint64: (torch.int64, np.uint64)}
+    if t.dtype in m:
+        sd, nd = m[t.dtype]
+        return t.view(sd).cpu().numpy().view(nd)
+    return t.cpu().numpy()
+
+
+def oracle_info(orc, info):
+    oi = orc.Info()
+    for f, _ in orc.Info._fields_:
+        setattr(oi, f, getattr(info, f))
+    return oi
+
+
+def check_build(vf, orc, keys, vals, offsets=None, n_other=20_000, **kw):
+    """Build on GPU and with the oracle; compare geometry, decode and query parity."""
+    kind = vf.FUNC if vals is not None else vf.FILTER
+    key_kind = vf.KEYS_BYTES if offsets is not None else vf.KEYS_U64
+    p = vf.vf_params_default(kind=kind, key_kind=key_kind, **kw)
+    n = len(offsets) - 1 if offsets is not None else len(keys)
+    s = vf.vf_build(dev(keys), None if vals is None else dev(vals), offsets=None if offsets is None else dev(offsets),
+                    params=p)
+    info = s.info
+    op = orc.default_params(kind=kind, key_kind=key_kind, **kw)
+    st, oi, odata = orc.build(op, keys, vals, offsets=offsets)
+    assert st == orc.OK
+    for f in ("regime", "h", "h_bb", "h_dup", "shards", "M", "c", "lg_seg", "seg", "l", "T", "cells",
+              "total_cells", "data_bytes", "seed", "retries"):
+        assert getattr(info, f) == getattr(oi, f), f
+    if info.regime == vf.REGIME_FUSE:
+        assert info.peeled == oi.peeled == n
+    out = host(s.query(dev(keys), offsets=None if offsets is None else dev(offsets)))
+    if kind == vf.FUNC:
+        assert (out == vals).all()
+    else:
+        assert out.all()
+    data = vf.vf_export(s)
+    assert len(data) == info.data_bytes
+    # oracle query on the GPU-built array decodes members too
+    ref = orc.query(oracle_info(orc, info), data, keys, offsets=offsets)
+    assert (ref == out).all()
+    if n_other:
+        if offsets is None:
+            other = synth.u64_keys(n + 7, n_other, 99)
+            gq = host(s.query(dev(other)))
+            oq = orc.query(oracle_info(orc, info), data, other)
+        else:
+            ob, oo = synth.byte_strings(n + 7, n_other, 99)
+            gq = host(s.query(dev(ob), offsets=dev(oo)))
+            oq = orc.query(oracle_info(orc, info), data, ob, offsets=oo)
+        assert gq.dtype == oq.dtype and (gq == oq).all()
+    return s, info, oi
+
+
+# ---------------------------------------------------------------- signatures
+
+@pytest.mark.parametrize("seed", [0, 1, 0xDEADBEEF, 2**64 - 1])
+@pytest.mark.parametrize("n", [1, 31, 100_003])
+def test_signatures_u64(vf, orc, seed, n):
+    keys = synth.u64_keys(5, n, seed & 0xFFFF)
+    g = host(vf.vf_signatures(dev(keys), seed))
+    assert (g == orc.sigs(keys, seed)).all()
+
+
+def test_signatures_bytes_unaligned(vf, orc):
+    data, offs = synth.byte_strings(0, 50_001, 3, lmin=8, lmax=64)
+    # shift the buffer so strings start at every alignment, include empty and short strings
+    extra = [b"", b"x", b"abcdefg", b"abcdefgh", b"abcdefghi", bytes(range(200))]
+    tail = np.frombuffer(b"".join(extra), dtype=np.uint8)
+    buf = np.concatenate([np.zeros(3, np.uint8), data, tail])
+    offs = np.concatenate([offs + np.uint64(3),
+                           offs[-1] + np.uint64(3) + np.cumsum([len(x) for x in extra]).astype(np.uint64)])
+    for seed in (0, 77):
+        g = host(vf.vf_signatures(dev(buf), seed, offsets=dev(offs)))
+        assert (g == orc.sigs(buf, seed, offsets=offs)).all()
+
+
+def test_signatures_host_buffers(vf, orc):
+    keys = synth.u64_keys(0, 4096, 1)
+    g = vf.vf_signatures(keys, 5)  # numpy in, numpy out: staged through the device
+    assert (g == orc.sigs(keys, 5)).all()
+
+
+# -------------------------------------------------------------------- builds
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 97, 1000, 30_011])
+@pytest.mark.parametrize("b", [1, 8, 13, 16, 32])
+def test_function_lge_regime(vf, orc, n, b):
+    keys = synth.u64_keys(0, n, 21 + n)
+    vals = synth.values(n, b, 21 + n)
+    check_build(vf, orc, keys, vals, seed=4, n_other=5000)
+
+
+@pytest.mark.parametrize("b", [1, 8, 16, 32])
+def test_filter_lge_regime(vf, orc, b):
+    n = 50_000
+    keys = synth.u64_keys(0, n, 2)
+    s, info, _ = check_build(vf, orc, keys, None, b=b, seed=9)
+    assert info.h >= 2 and info.core > 0
+
+
+def test_lge_sharded_byte_strings(vf, orc):
+    n = 60_000
+    data, offs = synth.byte_strings(0, n, 5)
+    vals = synth.values(n, 16, 5)
+    s, info, oi = check_build(vf, orc, data, vals, offsets=offs, b=16, mode=vf.MODE_LGE, lge_target=4096, seed=3)
+    assert info.regime == vf.REGIME_LGE and info.shards >= 8 and info.core > 0
+
+
+def test_lge_host_inputs(vf, orc):
+    n = 20_000
+    keys = synth.u64_keys(0, n, 8)
+    vals = synth.values(n, 8, 8)
+    s = vf.vf_build(keys, vals, params=vf.vf_params_default(seed=2))
+    out = s.query(keys)  # numpy in, numpy out
+    assert isinstance(out, np.ndarray) and (out == vals).all()
+
+
+def test_function_fuse_unsharded_2pow20(vf, orc):
+    n = 1 << 20
+    keys = synth.u64_keys(0, n, 1)
+    vals = synth.values(n, 8, 1)
+    s, info, _ = check_build(vf, orc, keys, vals, seed=1, n_other=1 << 18)
+    assert info.regime == vf.REGIME_FUSE and info.h == 0 and info.lg_seg == 13
+
+
+@pytest.mark.parametrize("b", [1, 7, 8, 16, 32])
+def test_filter_fuse_regime(vf, orc, b):
+    n = 1_000_003
+    keys = synth.u64_keys(0, n, 3)
+    s, info, _ = check_build(vf, orc, keys, None, b=b, seed=5, n_other=200_000)
+    other = synth.u64_keys(n, 400_000, 3)
+    fpr = host(s.query(dev(other))).mean()
+    p = 2.0 ** -b
+    assert abs(fpr - p) < 5 * math.sqrt(p * (1 - p) / len(other)) + 1e-9
+
+
+def test_fuse_sharded_byte_strings(vf, orc):
+    # epsilon forced up so that 2M keys shard (h > 0) in the fuse regime
+    n = 2_000_000
+    data, offs = synth.byte_strings(0, n, 6)
+    vals = synth.values(n, 16, 6)
+    s, info, _ = check_build(vf, orc, data, vals, offsets=offs, b=16, mode=vf.MODE_FUSE, eps=0.01, seed=2,
+                             n_other=50_000)
+    assert info.h >= 1
+
+
+def test_retries_match_oracle(vf, orc):
+    # small forced fuse graphs often fail to peel: the GPU must fail exactly when
+    # the oracle does (the 2-core is unique) and succeed with the same seed
+    keys = synth.u64_keys(0, 600_000, 4)
+    vals = synth.values(600_000, 8, 4)
+    retried = 0
+    for seed in range(8):
+        s, info, oi = check_build(vf, orc, keys, vals, mode=vf.MODE_FUSE, seed=seed, max_retries=20, n_other=0)
+        retried += info.retries > 0
+    assert retried > 0
+
+
+def test_query_stream_async_and_reuse(vf, orc):
+    n = 100_000
+    keys = synth.u64_keys(0, n, 12)
+    vals = synth.values(n, 16, 12)
+    s = vf.vf_build(dev(keys), dev(vals), params=vf.vf_params_default(b=16, seed=1))
+    st = torch.cuda.Stream()
+    kd = dev(keys)
+    with torch.cuda.stream(st):
+        outs = [s.query(kd, stream=st) for _ in range(3)]
+    st.synchronize()
+    for o in outs:
+        assert (host(o) == vals).all()
+
+
+def test_invalid_arguments(vf):
+    keys = dev(synth.u64_keys(0, 10, 1))
+    with pytest.raises(vf.VFError) as e:
+        vf.vf_build(keys, None, params=vf.vf_params_default(kind=vf.FILTER, b=0))
+    assert e.value.status == 1
+    with pytest.raises(vf.VFError) as e:
+        vf.vf_build(keys, None, params=vf.vf_params_default(kind=vf.FUNC))
+    assert e.value.status == 1
