@@ -204,22 +204,22 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             const uint32_t* F = fr[fi];
             uint32_t* G = fr[fi ^ 1];
             for (uint32_t i = tid; i < nF; i += T) {
-                uint32_t v = F[i];
+                uint32_t v = __ldcg(&F[i]);
                 cand[i] = deg_of(degw, v) == 1u ? xr_of(xrw, v) : kNone;
             }
             __syncthreads();
             for (uint32_t i = tid; i < nF; i += T) {
-                uint32_t e = cand[i];
+                uint32_t e = __ldcg(&cand[i]);
                 if (e == kNone) continue;
                 uint32_t bit = 1u << (e & 31u);
                 if (atomicOr(&clm[e >> 5], bit) & bit) continue;
-                uint32_t v = F[i];
-                uint32_t side = cev[3 * e] == v ? 0u : cev[3 * e + 1] == v ? 1u : 2u;
+                uint32_t v = __ldcg(&F[i]);
+                uint32_t side = __ldcg(&cev[3 * e]) == v ? 0u : __ldcg(&cev[3 * e + 1]) == v ? 1u : 2u;
                 porder[atomicAdd(&s_cnt[2], 1u)] = (e << 2) | side;
 #pragma unroll
                 for (uint32_t k = 0; k < 3; k++) {
                     if (k == side) continue;
-                    uint32_t u = cev[3 * e + k];
+                    uint32_t u = __ldcg(&cev[3 * e + k]);
                     uint32_t sh8 = (u & 3u) * 8u;
                     uint32_t old = atomicSub(&degw[u >> 2], 1u << sh8);
                     atomicXor(&xrw[u >> 1], e << ((u & 1u) * 16u));
@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             __syncthreads();
             C = s_C;
             for (uint32_t j = tid; j < C; j += T) {
-                const uint32_t* ev = cev + 3 * core[j];
+                const uint32_t* evp = cev + 3 * __ldcg(&core[j]);
+                const uint32_t ev[3] = {__ldcg(evp), __ldcg(evp + 1), __ldcg(evp + 2)};
                 atomicAdd(&inc_off[ev[0]], 1u);
                 atomicAdd(&inc_off[ev[1]], 1u);
                 atomicAdd(&inc_off[ev[2]], 1u);
@@ -260,12 +261,12 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             __syncthreads();
             // activation order: core degree, heaviest first (counting sort)
             for (uint32_t v = tid; v < V; v += T) {
-                uint32_t d = inc_off[v];
+                uint32_t d = __ldcg(&inc_off[v]);
                 vstate[v] = 0;
                 if (d) atomicAdd(&s_hist[min(d, 255u)], 1u);
             }
             cta_exclusive_scan(inc_off, V + 1, s_part);
-            for (uint32_t v = tid; v < V; v += T) inc_cur[v] = inc_off[v];
+            for (uint32_t v = tid; v < V; v += T) inc_cur[v] = __ldcg(&inc_off[v]);
             if (tid == 0) {
                 uint32_t run = 0;
                 for (int d = 255; d >= 1; d--) {
@@ -277,11 +278,12 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             }
             __syncthreads();
             for (uint32_t v = tid; v < V; v += T) {
-                uint32_t d = inc_off[v + 1] - inc_off[v];
+                uint32_t d = __ldcg(&inc_off[v + 1]) - __ldcg(&inc_off[v]);
                 if (d) act[atomicAdd(&s_hist[min(d, 255u)], 1u)] = v;
             }
             for (uint32_t j = tid; j < C; j += T) {
-                const uint32_t* ev = cev + 3 * core[j];
+                const uint32_t* evp = cev + 3 * __ldcg(&core[j]);
+                const uint32_t ev[3] = {__ldcg(evp), __ldcg(evp + 1), __ldcg(evp + 2)};
                 inc_list[atomicAdd(&inc_cur[ev[0]], 1u)] = j;
                 inc_list[atomicAdd(&inc_cur[ev[1]], 1u)] = j;
                 inc_list[atomicAdd(&inc_cur[ev[2]], 1u)] = j;
@@ -310,11 +312,11 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                         uint32_t K = max(1u, min(kMaxBatch, s_rem / 100u));
                         uint32_t nb = 0;
                         while (nb < K && s_apos < s_nact) {
-                            uint32_t v = act[s_apos++];
-                            if (vstate[v] != 0) continue;
+                            uint32_t v = __ldcg(&act[s_apos++]);
+                            if (__ldcg(&vstate[v]) != 0) continue;
                             bool live = false;
-                            for (uint32_t q = inc_off[v]; q < inc_off[v + 1] && !live; q++)
-                                live = eqdone[inc_list[q]] == 0;
+                            for (uint32_t q = __ldcg(&inc_off[v]); q < __ldcg(&inc_off[v + 1]) && !live; q++)
+                                live = __ldcg(&eqdone[__ldcg(&inc_list[q])]) == 0;
                             if (live) s_batch[nb++] = v;
                         }
                         s_nbatch = nb;
@@ -325,11 +327,11 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                     const uint32_t nb = s_nbatch, abase = s_A;
                     for (uint32_t i = tid; i < nb; i += T) {
                         uint32_t v = s_batch[i];
-                        vstate[v] = 1u | ((abase + i) << 2);
+                        atomicExch(&vstate[v], 1u | ((abase + i) << 2));
                         actv[abase + i] = v;
-                        for (uint32_t q = inc_off[v]; q < inc_off[v + 1]; q++) {
-                            uint32_t k = inc_list[q];
-                            if (eqdone[k]) continue;
+                        for (uint32_t q = __ldcg(&inc_off[v]); q < __ldcg(&inc_off[v + 1]); q++) {
+                            uint32_t k = __ldcg(&inc_list[q]);
+                            if (__ldcg(&eqdone[k])) continue;
                             uint32_t old = atomicSub(&eqst[k], 1u);
                             atomicXor(&eqst[k], v << 2);
                             uint32_t c = (old & 3u) - 1u;
@@ -346,16 +348,16 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                     if (tid == 0) s_A += nb;
                 } else {
                     const uint32_t* F = fr[fi];
-                    const uint32_t lo = s_S;
+                    const uint32_t lo = __ldcg(&soff[s_r]);  // solves of earlier rounds; s_S moves below
                     for (uint32_t i = tid; i < nF; i += T) {
-                        uint32_t j = F[i];
-                        if (eqdone[j]) continue;
-                        uint32_t w = eqst[j];
+                        uint32_t j = __ldcg(&F[i]);
+                        if (__ldcg(&eqdone[j])) continue;
+                        uint32_t w = __ldcg(&eqst[j]);
                         if ((w & 3u) != 1u) continue;
                         uint32_t x = w >> 2;
                         if (atomicCAS(&vstate[x], 0u, 3u) != 0u) continue;
                         uint32_t si = atomicAdd(&s_S, 1u);
-                        vstate[x] = 2u | (si << 2);
+                        atomicExch(&vstate[x], 2u | (si << 2));
                         solves[si] = (j << 16) | x;
                         eqdone[j] = 1;
                         atomicSub(&s_rem, 1u);
@@ -363,10 +365,10 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                     __syncthreads();
                     const uint32_t hi = s_S;
                     for (uint32_t si = lo + tid; si < hi; si += T) {
-                        uint32_t j = solves[si] >> 16, x = solves[si] & 0xFFFFu;
-                        for (uint32_t q = inc_off[x]; q < inc_off[x + 1]; q++) {
-                            uint32_t k = inc_list[q];
-                            if (k == j || eqdone[k]) continue;
+                        uint32_t j = __ldcg(&solves[si]) >> 16, x = __ldcg(&solves[si]) & 0xFFFFu;
+                        for (uint32_t q = __ldcg(&inc_off[x]); q < __ldcg(&inc_off[x + 1]); q++) {
+                            uint32_t k = __ldcg(&inc_list[q]);
+                            if (k == j || __ldcg(&eqdone[k])) continue;
                             uint32_t old = atomicSub(&eqst[k], 1u);
                             atomicXor(&eqst[k], x << 2);
                             uint32_t c = (old & 3u) - 1u;
@@ -404,25 +406,25 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             }
             // solved variables as affine functions of the active ones, round by round
             for (uint32_t r = 0; r < R; r++) {
-                const uint32_t lo = soff[r], hi = soff[r + 1];
+                const uint32_t lo = __ldcg(&soff[r]), hi = __ldcg(&soff[r + 1]);
                 if (hi == lo) continue;
                 const uint32_t items = (hi - lo) * AW;
                 for (uint32_t it = tid; it < items; it += T) {
                     const uint32_t si = lo + it / AW, w = it % AW;
-                    const uint32_t j = solves[si] >> 16, x = solves[si] & 0xFFFFu;
-                    const uint32_t e = core[j];
+                    const uint32_t j = __ldcg(&solves[si]) >> 16, x = __ldcg(&solves[si]) & 0xFFFFu;
+                    const uint32_t e = __ldcg(&core[j]);
                     uint32_t acc = 0, c = 0;
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
-                        uint32_t u = cev[3 * e + k];
+                        uint32_t u = __ldcg(&cev[3 * e + k]);
                         if (u == x) continue;
-                        uint32_t st = vstate[u];
+                        uint32_t st = __ldcg(&vstate[u]);
                         if ((st & 3u) == 1u) {
                             uint32_t ai = st >> 2;
-                            if ((ai >> 5) == w) acc |= 1u << (ai & 31u);
+                            if ((ai >> 5) == w) acc ^= 1u << (ai & 31u);
                         } else {
-                            acc ^= L[uint64_t(st >> 2) * AW + w];
-                            c ^= lc[st >> 2];
+                            acc ^= __ldcg(&L[uint64_t(st >> 2) * AW + w]);
+                            c ^= __ldcg(&lc[st >> 2]);
                         }
                     }
                     L[uint64_t(si) * AW + w] = acc;
@@ -437,17 +439,17 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             uint32_t* colrow = pivf + D;
             for (uint32_t it = tid; it < D * AW; it += T) {
                 const uint32_t d = it / AW, w = it % AW;
-                const uint32_t e = core[dense[d]];
+                const uint32_t e = __ldcg(&core[__ldcg(&dense[d])]);
                 uint32_t acc = 0, c = 0;
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
-                    uint32_t st = vstate[cev[3 * e + k]];
+                    uint32_t st = __ldcg(&vstate[__ldcg(&cev[3 * e + k])]);
                     if ((st & 3u) == 1u) {
                         uint32_t ai = st >> 2;
-                        if ((ai >> 5) == w) acc |= 1u << (ai & 31u);
+                        if ((ai >> 5) == w) acc ^= 1u << (ai & 31u);
                     } else {
-                        acc ^= L[uint64_t(st >> 2) * AW + w];
-                        c ^= lc[st >> 2];
+                        acc ^= __ldcg(&L[uint64_t(st >> 2) * AW + w]);
+                        c ^= __ldcg(&lc[st >> 2]);
                     }
                 }
                 rows[d * RS + w] = acc;
@@ -491,19 +493,19 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 continue;
             }
             for (uint32_t c = tid; c < A; c += T)
-                cell_put_zero(a.data, b, cbase + actv[c], colrow[c] != kNone ? rhs[colrow[c]] : 0u);
+                cell_put_zero(a.data, b, cbase + __ldcg(&actv[c]), colrow[c] != kNone ? rhs[colrow[c]] : 0u);
             __syncthreads();
             // solved variables, in solve order (their equations as generated)
             for (uint32_t r = 0; r < R; r++) {
-                const uint32_t lo = soff[r], hi = soff[r + 1];
+                const uint32_t lo = __ldcg(&soff[r]), hi = __ldcg(&soff[r + 1]);
                 if (hi == lo) continue;
                 for (uint32_t si = lo + tid; si < hi; si += T) {
-                    const uint32_t j = solves[si] >> 16, x = solves[si] & 0xFFFFu;
-                    const uint32_t e = core[j];
+                    const uint32_t j = __ldcg(&solves[si]) >> 16, x = __ldcg(&solves[si]) & 0xFFFFu;
+                    const uint32_t e = __ldcg(&core[j]);
                     uint32_t val = rhs_of(a, e0 + e);
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
-                        uint32_t u = cev[3 * e + k];
+                        uint32_t u = __ldcg(&cev[3 * e + k]);
                         if (u != x) val ^= cell_get_cg(a.data, b, cbase + u);
                     }
                     cell_put_zero(a.data, b, cbase + x, val);
@@ -514,15 +516,15 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
 
         // -------------------------------------------- 4. reverse peel-order assignment
         for (uint32_t r = prounds; r-- > 0;) {
-            const uint32_t lo = proff[r], hi = proff[r + 1];
+            const uint32_t lo = __ldcg(&proff[r]), hi = __ldcg(&proff[r + 1]);
             for (uint32_t i = lo + tid; i < hi; i += T) {
-                const uint32_t ent = porder[i];
+                const uint32_t ent = __ldcg(&porder[i]);
                 const uint32_t e = ent >> 2, side = ent & 3u;
                 uint32_t val = rhs_of(a, e0 + e);
 #pragma unroll
                 for (uint32_t k = 0; k < 3; k++)
-                    if (k != side) val ^= cell_get_cg(a.data, b, cbase + cev[3 * e + k]);
-                cell_put_zero(a.data, b, cbase + cev[3 * e + side], val);
+                    if (k != side) val ^= cell_get_cg(a.data, b, cbase + __ldcg(&cev[3 * e + k]));
+                cell_put_zero(a.data, b, cbase + __ldcg(&cev[3 * e + side]), val);
             }
             __syncthreads();
         }

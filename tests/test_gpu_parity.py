@@ -135,7 +135,7 @@ def test_signatures_host_buffers(vf, orc):
 def test_function_lge_regime(vf, orc, n, b):
     keys = synth.u64_keys(0, n, 21 + n)
     vals = synth.values(n, b, 21 + n)
-    check_build(vf, orc, keys, vals, seed=4, n_other=5000)
+    check_build(vf, orc, keys, vals, b=b, seed=4, n_other=5000)
 
 
 @pytest.mark.parametrize("b", [1, 8, 16, 32])
