@@ -86,6 +86,7 @@ typedef struct {
     uint64_t seed;           /* seed of the successful attempt */
     int retries;             /* failed attempts before it */
     uint64_t peeled, core;   /* edges peeled / edges solved by elimination (last attempt) */
+    uint64_t rounds;         /* fuse regime: synchronous peeling rounds (last attempt) */
 } vf_info;
 
 void vf_params_default(vf_params *p);

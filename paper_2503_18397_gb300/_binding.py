@@ -50,7 +50,7 @@ class VfInfo(C.Structure):
         ("shards", C.c_uint64), ("M", C.c_uint64), ("c", C.c_double), ("lg_seg", C.c_int),
         ("seg", C.c_uint64), ("l", C.c_uint64), ("T", C.c_uint64), ("cells", C.c_uint64),
         ("total_cells", C.c_uint64), ("data_bytes", C.c_uint64), ("seed", C.c_uint64),
-        ("retries", C.c_int), ("peeled", C.c_uint64), ("core", C.c_uint64),
+        ("retries", C.c_int), ("peeled", C.c_uint64), ("core", C.c_uint64), ("rounds", C.c_uint64),
     ]
 
     def as_dict(self):

@@ -258,62 +258,70 @@ vf_status h2d(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
 // One attempt of the fuse-regime solver. Returns VF_OK, VF_EBUILD (peel
 // failed: the attempt must be retried), or an error.
 vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
-                     const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled) {
+                     const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
+                     uint64_t* rounds_out) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
-    DevBuf W, claimed, f0, f1, order, roff, ctr;
+    DevBuf W, claimed, f0, f1, rec, roff, ctr;
     VF_CK(W.alloc(V * 4, st));
     VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
     VF_CK(claimed.alloc(((n + 31) / 32) * 4, st));
     VF_CK(cudaMemsetAsync(claimed.p, 0, ((n + 31) / 32) * 4, st));
-    VF_CK(f0.alloc(V * 4, st));
-    VF_CK(f1.alloc(V * 4, st));
-    VF_CK(order.alloc(std::max<uint64_t>(n, 1) * 4, st));
+    VF_CK(f0.alloc(V * 8, st));
+    VF_CK(f1.alloc(V * 8, st));
+    VF_CK(rec.alloc(std::max<uint64_t>(n, 1) * 16, st));
     const uint32_t round_cap = uint32_t(std::min<uint64_t>(n + 1, uint64_t(1) << 22));
     VF_CK(roff.alloc((uint64_t(round_cap) + 1) * 4, st));
     VF_CK(cudaMemsetAsync(roff.p, 0, 4, st));
-    // counters: 4 x u32, barrier (2 x u32), error word
-    VF_CK(ctr.alloc(64, st));
-    VF_CK(cudaMemsetAsync(ctr.p, 0, 64, st));
+    // counters (4 x u32), error word, barrier
+    const size_t ctr_bytes = 64 + sizeof(vf::Bar2);
+    VF_CK(ctr.alloc(ctr_bytes, st));
+    VF_CK(cudaMemsetAsync(ctr.p, 0, ctr_bytes, st));
     uint32_t* c32 = ctr.as<uint32_t>();
-    vf::FusePeelBuffers b;
-    b.loc = loc;
-    b.start = start;
-    b.S = uint32_t(in.shards);
-    b.W = W.as<uint32_t>();
-    b.claimed = claimed.as<uint32_t>();
-    b.front0 = f0.as<uint32_t>();
-    b.front1 = f1.as<uint32_t>();
-    b.front_cap = V;
-    b.order = order.as<uint32_t>();
-    b.round_off = roff.as<uint32_t>();
-    b.round_cap = round_cap;
-    b.ctr = c32;
-    b.bar = reinterpret_cast<vf::GridBar*>(c32 + 4);
-    b.err = c32 + 6;
+    vf::FuseSolveArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.loc = loc;
+    a.val = val;
+    a.start = start;
+    a.S = uint32_t(in.shards);
+    a.g = g;
+    a.W = W.as<uint32_t>();
+    a.claimed = claimed.as<uint32_t>();
+    a.front[0] = f0.as<uint2>();
+    a.front[1] = f1.as<uint2>();
+    a.front_cap = V;
+    a.rec = rec.as<uint4>();
+    a.round_off = roff.as<uint32_t>();
+    a.round_cap = round_cap;
+    a.ctr = c32;
+    a.err = c32 + 6;
+    a.bar = reinterpret_cast<vf::Bar2*>(c32 + 16);
+    a.data = data;
     {
         PhaseTimer t(kPhAccum, st);
-        VF_CK(vf::launch_accumulate(loc, n, start, b.S, g, b.W, b.err, st));
+        VF_CK(vf::launch_accumulate(loc, n, start, a.S, g, a.W, a.err, st));
     }
     {
         PhaseTimer t(kPhPeel, st);
-        VF_CK(vf::launch_peel(b, g, st));
+        VF_CK(vf::launch_peel(a, st));
     }
     uint32_t h[8];
     VF_CK(cudaMemcpyAsync(h, c32, sizeof h, cudaMemcpyDeviceToHost, st));
     VF_CK(cudaStreamSynchronize(st));
     const uint32_t rounds = h[3], count = h[2], err = h[6];
     *peeled = count;
+    *rounds_out = rounds;
     if (err & vf::kErrTimeout) return fail(VF_ETIMEOUT, "peeling barrier timed out");
     if (err & (vf::kErrDegOverflow | vf::kErrFrontier)) return VF_EBUILD;
     if (count != n) return VF_EBUILD;  // non-empty 2-core
-    VF_CK(cudaMemsetAsync(b.bar, 0, 8, st));
+    VF_CK(cudaMemsetAsync(a.bar, 0, sizeof(vf::Bar2), st));
+    a.rounds = rounds;
     {
         PhaseTimer t(kPhAssign, st);
-        VF_CK(vf::launch_assign(b, val, g, rounds, data, st));
+        VF_CK(vf::launch_assign(a, st));
     }
     uint32_t e2 = 0;
-    VF_CK(cudaMemcpyAsync(&e2, b.err, 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaMemcpyAsync(&e2, a.err, 4, cudaMemcpyDeviceToHost, st));
     VF_CK(cudaStreamSynchronize(st));
     if (e2 & vf::kErrTimeout) return fail(VF_ETIMEOUT, "assignment barrier timed out");
     return VF_OK;
@@ -487,15 +495,16 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
         }
         VF_CK(data.alloc(in.data_bytes + 16, st));
         VF_CK(cudaMemsetAsync(data.p, 0, in.data_bytes + 16, st));
-        uint64_t peeled = 0, core = 0;
+        uint64_t peeled = 0, core = 0, rounds = 0;
         if (in.regime == VF_REGIME_FUSE)
             rs = solve_fuse(in, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
-                            startb.as<unsigned long long>(), data.as<uint8_t>(), st, &peeled);
+                            startb.as<unsigned long long>(), data.as<uint8_t>(), st, &peeled, &rounds);
         else
             rs = solve_lge(in, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
                            startb.as<unsigned long long>(), data.as<uint8_t>(), st, &peeled, &core);
         in.peeled = peeled;
         in.core = in.regime == VF_REGIME_FUSE ? 0 : core;
+        in.rounds = rounds;
         if (rs == VF_OK) {
             VF_CK(cudaStreamSynchronize(st));
             vf_struct* s = new vf_struct;

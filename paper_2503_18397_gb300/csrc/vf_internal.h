@@ -10,22 +10,32 @@ namespace vf {
 
 int num_sms();
 
-// Buffers of the fuse-regime (global-memory) solver for one attempt.
-struct FusePeelBuffers {
+// Two-level grid barrier state (zeroed before each cooperative launch).
+struct Bar2 {
+    unsigned int count;
+    unsigned int gen;
+    unsigned int grp[64];
+};
+
+// Fuse-regime (global-memory) solver of one attempt: peeling and assignment.
+struct FuseSolveArgs {
     const uint64_t* loc;              // bucketed local signatures
+    const uint32_t* val;              // bucketed values, NULL for a filter
     const unsigned long long* start;  // S+1 shard starts
     uint32_t S;
+    Geom g;
     uint32_t* W;                      // S*cells vertex words
-    uint32_t* claimed;                // (n+31)/32 words
-    uint32_t* front0;
-    uint32_t* front1;
+    uint32_t* claimed;                // one bit per edge
+    uint2* front[2];                  // frontier entries (vertex, edge)
     uint64_t front_cap;
-    uint32_t* order;                  // n entries
-    uint32_t* round_off;              // round_cap+1 entries
+    uint4* rec;                       // assignment records, one per peeled edge
+    uint32_t* round_off;              // round r's records: rec[round_off[r] .. round_off[r+1])
     uint32_t round_cap;
-    uint32_t* ctr;                    // 4 counters
-    GridBar* bar;
+    uint32_t* ctr;                    // [0],[1] frontier sizes, [2] records, [3] rounds
+    Bar2* bar;
     uint32_t* err;
+    uint8_t* data;                    // assignment target
+    uint32_t rounds;                  // assignment: rounds recorded by the peel
 };
 
 cudaError_t launch_hist(int key_kind, const void* keys, const uint64_t* offs, uint64_t n, const Geom& g,
@@ -37,9 +47,8 @@ cudaError_t launch_sigs(int key_kind, const void* keys, const uint64_t* offs, ui
                         uint64_t kl, Sig* out, cudaStream_t st);
 cudaError_t launch_accumulate(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
                               const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st);
-cudaError_t launch_peel(const FusePeelBuffers& b, const Geom& g, cudaStream_t st);
-cudaError_t launch_assign(const FusePeelBuffers& b, const uint32_t* val, const Geom& g, uint32_t rounds,
-                          uint8_t* data, cudaStream_t st);
+cudaError_t launch_peel(FuseSolveArgs a, cudaStream_t st);
+cudaError_t launch_assign(FuseSolveArgs a, cudaStream_t st);
 
 // LGE regime: one CTA per shard (peel + lazy Gaussian elimination + assign).
 struct LgeArgs {
