@@ -137,6 +137,30 @@ vf_status vf_signatures(int key_kind, const void *keys, const uint64_t *offsets,
 vf_status vf_timing_enable(int on);
 vf_status vf_timing_read(double *ms, uint64_t *launches);
 
+/* Allocation-free build of a small structure. The paper has no counterpart;
+ * this entry point exists for callers that must not allocate device memory
+ * during a build: code whose device memory is owned by its own pool or
+ * arena, and latency-sensitive paths where a cudaMalloc/cudaFree could
+ * synchronise the device or fail under memory pressure. It builds the same
+ * structure vf_build builds for n <= 16384 64-bit keys with default shard
+ * parameters: one shard, lazy-Gaussian-elimination regime (params->mode and
+ * the LGE sizes are ignored), same hash, seed, retries and geometry.
+ *  keys    device uint64_t[n]; values: device array of the value type of b
+ *          (function) or NULL (filter); data: device buffer of at least
+ *          data_capacity >= vf_info.data_bytes bytes (get it from vf_plan with
+ *          M = n), written with the structure's cells; info: host, receives
+ *          the geometry, seed and retries, as vf_get_info would.
+ *  All scratch lives in one static device array of about 4.2 MB that every
+ *  GPU loading the library keeps until the process exits; no call allocates
+ *  or frees memory. The first call on a device looks up that array's device
+ *  address; make it before any stream capture. All calls share the array,
+ *  so calls that overlap on the GPU (other streams, other host threads) race
+ *  and must be serialised by the caller. Waits for completion.
+ *  Errors: VF_ECAPACITY (n > 16384), VF_EINVAL (host pointers, data buffer too
+ *  small, byte-string keys, bad b/kind), VF_EBUILD, VF_ECUDA. */
+vf_status vf_build_static(const uint64_t *keys, const void *values, uint64_t n, const vf_params *params,
+                          void *data, uint64_t data_capacity, vf_info *info, void *stream);
+
 /* Release a structure (NULL is accepted). */
 vf_status vf_free(vf_struct *s);
 

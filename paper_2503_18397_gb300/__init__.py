@@ -21,6 +21,7 @@ from ._binding import (  # noqa: F401
     lib,
     lib_path,
     vf_build,
+    vf_build_static,
     vf_export,
     vf_free,
     vf_get_info,

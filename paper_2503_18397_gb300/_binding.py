@@ -81,6 +81,8 @@ def lib():
         L.vf_export.argtypes = [vp, vp]
         L.vf_signatures.argtypes = [i32, vp, vp, u64, u64, vp, vp]
         L.vf_free.argtypes = [vp]
+        L.vf_build_static.argtypes = [vp, vp, u64, C.POINTER(VfParams), vp, u64, C.POINTER(VfInfo), vp]
+        L.vf_build_static.restype = C.c_int
         L.vf_timing_enable.argtypes = [i32]
         L.vf_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(u64)]
         L.vf_last_error.argtypes = []
@@ -232,6 +234,18 @@ def vf_signatures(keys, seed: int, offsets=None, out=None, stream=None):
     kind = KEYS_BYTES if offsets is not None else KEYS_U64
     _check(lib().vf_signatures(kind, _ptr(keys), _ptr(offsets), n, seed, _ptr(out), _stream(stream, keys, out)))
     return out
+
+
+def vf_build_static(keys, values, data, *, params: VfParams | None = None, stream=None) -> VfInfo:
+    """Allocation-free build of <= 16384 u64 keys into the caller's device buffer `data`."""
+    if params is None:
+        params = vf_params_default()
+        params.kind = FUNC if values is not None else FILTER
+    info = VfInfo()
+    nbytes = data.numel() * data.element_size() if _is_tensor(data) else data.nbytes
+    _check(lib().vf_build_static(_ptr(keys), _ptr(values), len(keys), C.byref(params), _ptr(data), nbytes,
+                                 C.byref(info), _stream(stream, keys, values, data)))
+    return info
 
 
 def vf_free(s: Structure):

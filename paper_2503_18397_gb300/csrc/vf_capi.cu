@@ -369,6 +369,8 @@ vf_status solve_lge(const vf_info& in, const vf::Geom& g, const uint64_t* loc, c
 
 }  // namespace
 
+void vf::set_last_error(const char* msg) { g_last_error = msg; }
+
 extern "C" {
 
 void vf_params_default(vf_params* p) {

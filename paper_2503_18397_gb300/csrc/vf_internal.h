@@ -10,6 +10,9 @@ namespace vf {
 
 int num_sms();
 
+// Message returned by vf_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // Two-level grid barrier state (zeroed before each cooperative launch).
 struct Bar2 {
     unsigned int count;
@@ -64,6 +67,49 @@ struct LgeArgs {
     uint32_t* err;
     uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] shard counter
 };
+// Layout (in 32-bit words) of one CTA's LGE scratch slab for shards of at most
+// m keys and V cells.
+constexpr uint32_t kMaxActive = 2048;  // active variables per shard
+constexpr uint32_t kLPoolPerKey = 40;  // words of coefficient rows per shard key
+struct LgeOffsets {
+    uint64_t cev, porder, proff, f0, f1, cand, core, eqst, eqdone, inc_off, inc_cur, inc_list, vstate, act, actv,
+        solves, soff, dense, lc, L, lpool, total;
+};
+
+__host__ __device__ constexpr uint64_t lge_take(uint64_t& p, uint64_t words) {
+    uint64_t r = p;
+    p += (words + 3) & ~uint64_t(3);
+    return r;
+}
+
+__host__ __device__ constexpr LgeOffsets lge_offsets(uint32_t m, uint32_t V) {
+    LgeOffsets o{};
+    uint64_t p = 0;
+    o.cev = lge_take(p, 3ull * m);
+    o.porder = lge_take(p, m);
+    o.proff = lge_take(p, V + 2ull);
+    o.f0 = lge_take(p, V);
+    o.f1 = lge_take(p, V);
+    o.cand = lge_take(p, V);
+    o.core = lge_take(p, m);
+    o.eqst = lge_take(p, m);
+    o.eqdone = lge_take(p, m);
+    o.inc_off = lge_take(p, V + 1ull);
+    o.inc_cur = lge_take(p, V);
+    o.inc_list = lge_take(p, 3ull * m);
+    o.vstate = lge_take(p, V);
+    o.act = lge_take(p, V);
+    o.actv = lge_take(p, kMaxActive);
+    o.solves = lge_take(p, m);
+    o.soff = lge_take(p, uint64_t(m) + V + 4);
+    o.dense = lge_take(p, m);
+    o.lc = lge_take(p, m);
+    o.lpool = uint64_t(m) * kLPoolPerKey + 4096;
+    o.L = lge_take(p, o.lpool);
+    o.total = p;
+    return o;
+}
+
 cudaError_t launch_lge(const LgeArgs& a, unsigned grid, cudaStream_t st);
 unsigned lge_grid();
 uint64_t lge_scratch_words_per_cta(uint32_t m_cap, uint32_t v_cap);
