@@ -35,7 +35,7 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 
 WORKLOADS = {
-    # name: (kind, b, n, key kind, description)
+    # name: (kind, b, n, key kind, description[, forced mode])
     "c2": ("filter", 8, 100_000_000, "u64",
            "VFilter n=1e8 uniform 64-bit keys, b=8, fuse graphs (eps-cost sharding h=3); "
            "query 1e8 members + 1e8 disjoint keys"),
@@ -44,7 +44,7 @@ WORKLOADS = {
            "query 2^20 members + 2^20 disjoint keys"),
     "c3": ("func", 16, 10_000_000, "bytes",
            "VFunc n=1e7 byte strings (length 8..64), 16-bit values, LGE regime shards; "
-           "query 1e7 members + 1e7 disjoint strings"),
+           "query 1e7 members + 1e7 disjoint strings", "lge"),
 }
 
 # Algorithmic DRAM bytes per unit for each phase kernel (unit: key, edge or query).
@@ -115,10 +115,11 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def make_inputs(workload: str, seed: int):
+def make_inputs(workload: str, seed: int, n_override: int = 0):
     from paper_2503_18397_gb300 import synth
 
-    kind, b, n, kk, _ = WORKLOADS[workload]
+    kind, b, n, kk = WORKLOADS[workload][:4]
+    n = n_override or n
     if kk == "u64":
         keys = synth.u64_keys(0, n, seed)
         other = synth.u64_keys(n, n, seed)
@@ -169,9 +170,11 @@ def run_gpu(args):
         vbuild.build()
     vf.lib()
 
-    kind, b, n, keys, offs, vals, other, ooffs = make_inputs(args.workload, 0x5EED + rank)
+    kind, b, n, keys, offs, vals, other, ooffs = make_inputs(args.workload, 0x5EED + rank, args.n)
     p = vf.vf_params_default(kind=vf.FILTER if kind == "filter" else vf.FUNC, b=b,
                              key_kind=vf.KEYS_BYTES if offs is not None else vf.KEYS_U64, seed=1 + rank)
+    if len(WORKLOADS[args.workload]) > 5:
+        p.mode = vf.MODE_LGE
     kd, vd, od, xd, xo = (to_dev(a, torch) for a in (keys, vals, offs, other, ooffs))
     stream = torch.cuda.current_stream()
 
@@ -289,7 +292,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][4], "n": n, "b": b, "kind": kind,
+        "config": {"workload": WORKLOADS[args.workload][4] if not args.n else f"{args.workload} with n={n}", "n": n, "b": b, "kind": kind,
                    "l2": "inputs larger than L2 (no flush)" if 8 * n > 129e6 else "L2 flushed: none (small case)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "shards": int(info.shards), "cells_per_shard": int(info.cells), "lg_seg": int(info.lg_seg),
@@ -314,16 +317,17 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-# Per-launch DRAM traffic (bytes) from ncu captures of the same kernels; None
-# until a capture of the current kernel exists.
-TRAFFIC = {}
+# Per-launch DRAM traffic (bytes) from ncu captures of the same kernels, scaled
+# from the captured case by units processed; absent until a capture of the
+# current kernel exists (profiles/ holds the summaries).
+TRAFFIC = {("c2", "peel"): round(2.792688e9 / 2e7 * 1e8), ("c2", "query"): round(198.56e6 / 2e7 * 1e8)}
 
 
 # ---------------------------------------------------------------- reference arm
 
 def oracle_sample(workload: str, quick: bool):
     """Bounded sample of the workload for the single-thread oracle."""
-    kind, b, n, kk, _ = WORKLOADS[workload]
+    kind, b, n, kk = WORKLOADS[workload][:4]
     ns = min(n, 4_000_000 if quick else 8_000_000)
     return kind, b, ns, kk
 
@@ -342,6 +346,8 @@ def cpu_baseline(workload: str, quick: bool = True):
     vals = synth.values(ns, b, 3) if kind == "func" else None
     p = O.default_params(kind=O.FILTER if kind == "filter" else O.FUNC, b=b,
                          key_kind=O.KEYS_BYTES if offs is not None else O.KEYS_U64, seed=1)
+    if len(WORKLOADS[workload]) > 5:
+        p.mode = O.MODE_LGE
     t0 = time.perf_counter()
     st, info, data = O.build(p, keys, vals, offsets=offs)
     t1 = time.perf_counter()
@@ -390,6 +396,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="override the workload's key count (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
