@@ -328,6 +328,9 @@ TRAFFIC = {("c2", "peel"): round(2.792688e9 / 2e7 * 1e8), ("c2", "query"): round
 def oracle_sample(workload: str, quick: bool):
     """Bounded sample of the workload for the single-thread oracle."""
     kind, b, n, kk = WORKLOADS[workload][:4]
+    if len(WORKLOADS[workload]) > 5:
+        # plain Gaussian elimination of every 2-core is cubic: a few shards only
+        return kind, b, min(n, 40_000), kk
     ns = min(n, 4_000_000 if quick else 8_000_000)
     return kind, b, ns, kk
 
