@@ -128,6 +128,47 @@ vf_status vf_export(const vf_struct *s, void *host_dst);
 vf_status vf_signatures(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n,
                         uint64_t seed, uint64_t *out, void *stream);
 
+/* Batched construction of many independent structures (the batching
+ * pattern: thousands of structures of uneven sizes built together). All
+ * structures' keys are hashed, histogrammed and bucketed by two batched
+ * kernels; every LGE-regime shard of every structure is then one task of a
+ * single persistent solver launch (tasks largest first when `lpt`), the
+ * scatter and that launch captured in one CUDA graph when `use_graph`.
+ * Structures at or above `lge_threshold` keys take the fuse regime, one
+ * solver each. A structure whose attempt fails is retried alone with its
+ * next seed (Sec. 4), up to common->max_retries times. Keys are 64-bit
+ * integers (device or host pointers). */
+typedef struct {
+    const uint64_t *keys;
+    const void *values;      /* function: values of the type of b; filter: NULL */
+    uint64_t n;
+    int kind, b;
+    uint64_t seed;
+} vf_batch_item;
+
+typedef struct {
+    uint64_t lge_threshold;  /* structures with fewer keys use the LGE regime (paper: 800000) */
+    uint64_t lge_target;     /* LGE regime: mean keys per shard */
+    int lpt;                 /* solve shards largest first */
+    int use_graph;           /* scatter + solver as one CUDA graph */
+} vf_batch_opts;
+
+vf_status vf_batch_opts_default(vf_batch_opts *opts);
+
+/* out: count structure pointers (all NULL on failure). common: eps, eta,
+ * lge_max_shard, max_retries (kind, b, seed and the LGE sizes come from the
+ * items and opts). Errors as vf_build. */
+vf_status vf_build_batch(const vf_batch_item *items, uint32_t count, const vf_params *common,
+                         const vf_batch_opts *opts, void *stream, vf_struct **out);
+
+/* Autotuner: times candidate opts (fuse/LGE threshold at the given one or
+ * none, mean LGE shard 8192 or 16384 keys, largest-first or natural task
+ * order) on a sample of the batch (every k-th structure, ~5% of the keys)
+ * and returns the fastest; results are cached per batch shape (count, total
+ * keys, largest structure). best_ms: the sample's build time (-1 if cached). */
+vf_status vf_tune_batch(const vf_batch_item *items, uint32_t count, const vf_params *common, void *stream,
+                        vf_batch_opts *best, double *best_ms);
+
 /* Per-phase device timing (CUDA events recorded on the launching stream
  * around every kernel of build and query). Phases, in order: hash+histogram,
  * scatter, incidence, peel, assign, LGE solver, query. vf_timing_read waits

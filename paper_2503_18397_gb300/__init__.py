@@ -20,7 +20,12 @@ from ._binding import (  # noqa: F401
     Structure,
     lib,
     lib_path,
+    VfBatchItem,
+    VfBatchOpts,
+    vf_batch_opts_default,
     vf_build,
+    vf_build_batch,
+    vf_tune_batch,
     vf_build_static,
     vf_export,
     vf_free,

@@ -57,6 +57,19 @@ class VfInfo(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class VfBatchItem(C.Structure):
+    _fields_ = [("keys", C.c_void_p), ("values", C.c_void_p), ("n", C.c_uint64), ("kind", C.c_int),
+                ("b", C.c_int), ("seed", C.c_uint64)]
+
+
+class VfBatchOpts(C.Structure):
+    _fields_ = [("lge_threshold", C.c_uint64), ("lge_target", C.c_uint64), ("lpt", C.c_int),
+                ("use_graph", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 EXPORTS = ["vf_params_default", "vf_build", "vf_query", "vf_get_info", "vf_plan", "vf_data", "vf_export",
            "vf_signatures", "vf_free", "vf_last_error"]
 
@@ -83,6 +96,13 @@ def lib():
         L.vf_free.argtypes = [vp]
         L.vf_build_static.argtypes = [vp, vp, u64, C.POINTER(VfParams), vp, u64, C.POINTER(VfInfo), vp]
         L.vf_build_static.restype = C.c_int
+        L.vf_batch_opts_default.argtypes = [C.POINTER(VfBatchOpts)]
+        L.vf_build_batch.argtypes = [C.POINTER(VfBatchItem), C.c_uint32, C.POINTER(VfParams),
+                                     C.POINTER(VfBatchOpts), vp, C.POINTER(vp)]
+        L.vf_tune_batch.argtypes = [C.POINTER(VfBatchItem), C.c_uint32, C.POINTER(VfParams), vp,
+                                    C.POINTER(VfBatchOpts), C.POINTER(C.c_double)]
+        for name in ("vf_batch_opts_default", "vf_build_batch", "vf_tune_batch"):
+            getattr(L, name).restype = C.c_int
         L.vf_timing_enable.argtypes = [i32]
         L.vf_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(u64)]
         L.vf_last_error.argtypes = []
@@ -246,6 +266,49 @@ def vf_build_static(keys, values, data, *, params: VfParams | None = None, strea
     _check(lib().vf_build_static(_ptr(keys), _ptr(values), len(keys), C.byref(params), _ptr(data), nbytes,
                                  C.byref(info), _stream(stream, keys, values, data)))
     return info
+
+
+def vf_batch_opts_default(**overrides) -> VfBatchOpts:
+    o = VfBatchOpts()
+    _check(lib().vf_batch_opts_default(C.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _batch_items(items):
+    """items: sequence of (keys, values_or_None, kind, b, seed) with u64 keys."""
+    arr = (VfBatchItem * max(len(items), 1))()
+    for i, (keys, values, kind, b, seed) in enumerate(items):
+        arr[i].keys = _ptr(keys)
+        arr[i].values = _ptr(values)
+        arr[i].n = len(keys)
+        arr[i].kind = kind
+        arr[i].b = b
+        arr[i].seed = seed
+    return arr
+
+
+def vf_build_batch(items, *, params: VfParams | None = None, opts: VfBatchOpts | None = None, stream=None):
+    """Build many structures at once; returns a list of Structure."""
+    params = params or vf_params_default()
+    arr = _batch_items(items)
+    out = (C.c_void_p * max(len(items), 1))()
+    bufs = [x for it in items for x in it[:2] if x is not None]
+    _check(lib().vf_build_batch(arr, len(items), C.byref(params), None if opts is None else C.byref(opts),
+                                _stream(stream, *bufs), out))
+    return [Structure(out[i]) for i in range(len(items))]
+
+
+def vf_tune_batch(items, *, params: VfParams | None = None, stream=None):
+    """Autotuned batch options for this batch shape and the sample build time (ms, -1 if cached)."""
+    params = params or vf_params_default()
+    arr = _batch_items(items)
+    best = VfBatchOpts()
+    ms = C.c_double()
+    bufs = [x for it in items for x in it[:2] if x is not None]
+    _check(lib().vf_tune_batch(arr, len(items), C.byref(params), _stream(stream, *bufs), C.byref(best), C.byref(ms)))
+    return best, ms.value
 
 
 def vf_free(s: Structure):

@@ -4,6 +4,8 @@
 #include "vfunc.h"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -327,25 +329,56 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     return VF_OK;
 }
 
-vf_status solve_lge(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
-                    const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
-                    uint64_t* core) {
+// Tasks of the LGE solver for the shards of one or more structures, largest
+// shard first when `lpt` (longest-processing-time order balances the CTAs).
+void add_lge_tasks(std::vector<vf::LgeTask>& tasks, const std::vector<unsigned long long>& start, uint64_t base_key,
+                   const vf_info& in, uint8_t* data, uint32_t item) {
+    for (uint64_t s = 0; s < in.shards; s++) {
+        vf::LgeTask t;
+        std::memset(&t, 0, sizeof t);
+        t.loc_off = base_key + start[s];
+        t.cell_base = s * in.cells;
+        t.data = data;
+        t.m = uint32_t(start[s + 1] - start[s]);
+        t.cells = uint32_t(in.cells);
+        t.b = in.b;
+        t.kind = in.kind;
+        t.item = item;
+        if (t.m > 0) tasks.push_back(t);
+    }
+}
+
+// Runs the LGE solver over `tasks`; item_fail (device, one word per
+// structure) receives each structure's failure bits.
+vf_status run_lge_tasks(std::vector<vf::LgeTask>& tasks, bool lpt, const uint64_t* loc, const uint32_t* val,
+                        uint32_t* item_fail, cudaStream_t st, uint64_t* peeled, uint64_t* core, uint32_t* err_out) {
+    *peeled = *core = 0;
+    *err_out = 0;
+    if (tasks.empty()) return VF_OK;
+    if (lpt)
+        std::stable_sort(tasks.begin(), tasks.end(),
+                         [](const vf::LgeTask& x, const vf::LgeTask& y) { return x.m > y.m; });
+    uint32_t m_cap = 1, v_cap = 32;
+    for (auto& t : tasks) {
+        m_cap = std::max(m_cap, t.m);
+        v_cap = std::max(v_cap, t.cells);
+    }
     unsigned grid = vf::lge_grid();
-    grid = unsigned(std::min<uint64_t>(grid, std::max<uint64_t>(in.shards, 1)));
-    const uint32_t m_cap = uint32_t(std::max<uint64_t>(in.M, 1));
-    const uint32_t v_cap = uint32_t(in.cells);
+    grid = unsigned(std::min<uint64_t>(grid, tasks.size()));
     const uint64_t per_cta = vf::lge_scratch_words_per_cta(m_cap, v_cap);
-    DevBuf scratch, misc;
+    DevBuf scratch, misc, tbuf;
     VF_CK(scratch.alloc(per_cta * grid * 4, st));
     VF_CK(misc.alloc(64, st));
     VF_CK(cudaMemsetAsync(misc.p, 0, 64, st));
+    vf_status rs = h2d(tbuf, tasks, st);
+    if (rs != VF_OK) return rs;
     vf::LgeArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.tasks = tbuf.as<vf::LgeTask>();
+    a.ntasks = uint32_t(tasks.size());
     a.loc = loc;
     a.val = val;
-    a.start = start;
-    a.S = uint32_t(in.shards);
-    a.g = g;
-    a.data = data;
+    a.item_fail = item_fail ? item_fail : misc.as<uint32_t>();
     a.scratch = scratch.as<uint32_t>();
     a.scratch_words_per_cta = per_cta;
     a.m_cap = m_cap;
@@ -361,11 +394,263 @@ vf_status solve_lge(const vf_info& in, const vf::Geom& g, const uint64_t* loc, c
     VF_CK(cudaStreamSynchronize(st));
     *peeled = h[4];
     *core = h[5];
+    *err_out = h[0];
     if (h[0] & vf::kErrTimeout) return fail(VF_ETIMEOUT, "LGE solver wait timed out");
-    if (h[0] & vf::kErrCapacity) return fail(VF_ECAPACITY, "LGE shard exceeds the per-CTA solver capacity");
-    if (h[0] & (vf::kErrUnsolvable | vf::kErrDegOverflow | vf::kErrLgeSize)) return VF_EBUILD;
     return VF_OK;
 }
+
+vf_status solve_lge(const vf_info& in, const std::vector<unsigned long long>& start, const uint64_t* loc,
+                    const uint32_t* val, uint8_t* data, cudaStream_t st, uint64_t* peeled, uint64_t* core) {
+    std::vector<vf::LgeTask> tasks;
+    add_lge_tasks(tasks, start, 0, in, data, 0);
+    uint32_t err = 0;
+    vf_status rs = run_lge_tasks(tasks, true, loc, val, nullptr, st, peeled, core, &err);
+    if (rs != VF_OK) return rs;
+    if (err & vf::kErrCapacity) return fail(VF_ECAPACITY, "LGE shard exceeds the per-CTA solver capacity");
+    if (err & (vf::kErrUnsolvable | vf::kErrDegOverflow | vf::kErrLgeSize)) return VF_EBUILD;
+    return VF_OK;
+}
+
+
+// ------------------------------------------------------------ batched builds
+
+struct BatchState {
+    std::vector<uint32_t> attempt;  // per item
+};
+
+// One attempt of every pending item: plan, histogram, scatter, solve.
+// Built items go to out[]; failed ones to `failed`.
+vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_t>& pending,
+                           const std::vector<uint32_t>& attempt, const vf_params& common, const vf_batch_opts& opts,
+                           const std::vector<const uint64_t*>& kdev, const std::vector<const void*>& vdev,
+                           cudaStream_t st, int dev, vf_struct** out, std::vector<uint32_t>& failed) {
+    const uint32_t P = uint32_t(pending.size());
+    std::vector<vf_info> info(P);
+    std::vector<uint64_t> key_off(P + 1, 0);
+    for (uint32_t j = 0; j < P; j++) {
+        const vf_batch_item& it = items[pending[j]];
+        vf_params pi = common;
+        pi.kind = it.kind;
+        pi.b = it.b;
+        pi.key_kind = VF_KEYS_U64;
+        pi.lge_threshold = opts.lge_threshold;
+        pi.lge_target = opts.lge_target;
+        vf_info& in = info[j];
+        std::memset(&in, 0, sizeof in);
+        in.n = in.n_eff = it.n;
+        in.kind = it.kind;
+        in.b = it.b;
+        in.seed = it.seed + attempt[pending[j]];
+        in.retries = int(attempt[pending[j]]);
+        plan_h(pi, it.n, in);
+        key_off[j + 1] = key_off[j] + it.n;
+    }
+    const uint64_t total = key_off[P];
+    // histograms; LGE structures whose largest shard is too big get more shard bits
+    std::vector<vf::BatchItem> desc(P);
+    std::vector<uint32_t> hist_off(P + 1, 0), counts;
+    DevBuf ddesc, doff, dhist;
+    VF_CK(doff.alloc(std::max<uint64_t>(P, 1) * 8, st));
+    VF_CK(cudaMemcpyAsync(doff.p, key_off.data(), P * 8, cudaMemcpyHostToDevice, st));
+    for (;;) {
+        for (uint32_t j = 0; j < P; j++) {
+            info[j].shards = uint64_t(1) << info[j].h;
+            hist_off[j + 1] = hist_off[j] + uint32_t(info[j].shards);
+            vf::BatchItem& d = desc[j];
+            d.keys = kdev[pending[j]];
+            d.vals = info[j].kind == VF_FUNC ? vdev[pending[j]] : nullptr;
+            d.key_off = key_off[j];
+            d.kh = vf::mix64(info[j].seed ^ vf::kLaneHi);
+            d.kl = vf::mix64(info[j].seed ^ vf::kLaneLo);
+            d.n = uint32_t(info[j].n);
+            d.h = info[j].h;
+            d.hist_off = hist_off[j];
+            d.b = info[j].b;
+        }
+        vf_status rs = h2d(ddesc, desc, st);
+        if (rs != VF_OK) return rs;
+        VF_CK(dhist.alloc(std::max<uint64_t>(hist_off[P], 1) * 4, st));
+        VF_CK(cudaMemsetAsync(dhist.p, 0, hist_off[P] * 4, st));
+        {
+            PhaseTimer t(kPhHist, st);
+            VF_CK(vf::launch_batch_hist(ddesc.as<vf::BatchItem>(), doff.as<uint64_t>(), P, total, dhist.as<uint32_t>(),
+                                        st));
+        }
+        counts.assign(hist_off[P], 0);
+        VF_CK(cudaMemcpyAsync(counts.data(), dhist.p, hist_off[P] * 4, cudaMemcpyDeviceToHost, st));
+        VF_CK(cudaStreamSynchronize(st));
+        bool again = false;
+        for (uint32_t j = 0; j < P; j++) {
+            uint64_t M = 0;
+            for (uint32_t k = hist_off[j]; k < hist_off[j + 1]; k++) M = std::max<uint64_t>(M, counts[k]);
+            info[j].M = M;
+            if (info[j].regime == VF_REGIME_LGE && M > common.lge_max_shard && info[j].h < 30) {
+                info[j].h++;
+                again = true;
+            }
+        }
+        if (!again) break;
+    }
+    // geometry, data arrays, scatter cursors
+    std::vector<uint8_t*> data(P, nullptr);
+    auto free_data = [&]() {
+        for (auto* d : data)
+            if (d) cudaFreeAsync(d, st);
+    };
+    std::vector<unsigned long long> cursor(hist_off[P]);
+    for (uint32_t j = 0; j < P; j++) {
+        vf_info& in = info[j];
+        geometry(in);
+        if ((in.regime == VF_REGIME_FUSE && in.M >= (uint64_t(1) << 27)) || in.total_cells >= (uint64_t(1) << 32)) {
+            free_data();
+            return fail(VF_ECAPACITY, "batched structure exceeds a size limit");
+        }
+        if (cudaMallocAsync(reinterpret_cast<void**>(&data[j]), in.data_bytes + 16, st) != cudaSuccess) {
+            free_data();
+            return fail(VF_ENOMEM, "batched data allocation failed");
+        }
+        VF_CK(cudaMemsetAsync(data[j], 0, in.data_bytes + 16, st));
+        unsigned long long run = key_off[j];
+        for (uint32_t k = hist_off[j]; k < hist_off[j + 1]; k++) {
+            cursor[k] = run;
+            run += counts[k];
+        }
+    }
+    DevBuf dcur, loc, val, fails;
+    vf_status rs = h2d(dcur, cursor, st);
+    if (rs != VF_OK) return free_data(), rs;
+    VF_CK(loc.alloc(std::max<uint64_t>(total, 1) * 8, st));
+    VF_CK(val.alloc(std::max<uint64_t>(total, 1) * 4, st));
+    VF_CK(fails.alloc(std::max<uint64_t>(P, 1) * 4, st));
+    // LGE tasks of every LGE structure, one solver launch for all of them
+    std::vector<vf::LgeTask> tasks;
+    for (uint32_t j = 0; j < P; j++) {
+        if (info[j].regime != VF_REGIME_LGE) continue;
+        std::vector<unsigned long long> start(info[j].shards + 1, 0);
+        for (uint64_t s2 = 0; s2 < info[j].shards; s2++) start[s2 + 1] = start[s2] + counts[hist_off[j] + s2];
+        add_lge_tasks(tasks, start, key_off[j], info[j], data[j], j);
+    }
+    if (opts.lpt)
+        std::stable_sort(tasks.begin(), tasks.end(),
+                         [](const vf::LgeTask& x, const vf::LgeTask& y) { return x.m > y.m; });
+    uint32_t m_cap = 1, v_cap = 32;
+    for (auto& t : tasks) {
+        m_cap = std::max(m_cap, t.m);
+        v_cap = std::max(v_cap, t.cells);
+    }
+    unsigned grid = vf::lge_grid();
+    grid = unsigned(std::min<uint64_t>(grid, std::max<size_t>(tasks.size(), 1)));
+    const uint64_t per_cta = vf::lge_scratch_words_per_cta(m_cap, v_cap);
+    DevBuf scratch, misc, tbuf;
+    VF_CK(scratch.alloc(per_cta * grid * 4, st));
+    VF_CK(misc.alloc(64, st));
+    rs = h2d(tbuf, tasks, st);
+    if (rs != VF_OK) return free_data(), rs;
+    vf::LgeArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.tasks = tbuf.as<vf::LgeTask>();
+    a.ntasks = uint32_t(tasks.size());
+    a.loc = loc.as<uint64_t>();
+    a.val = val.as<uint32_t>();
+    a.item_fail = fails.as<uint32_t>();
+    a.scratch = scratch.as<uint32_t>();
+    a.scratch_words_per_cta = per_cta;
+    a.m_cap = m_cap;
+    a.v_cap = v_cap;
+    a.err = misc.as<uint32_t>();
+    a.stats = misc.as<uint32_t>() + 4;
+    // scatter + solver: one CUDA graph (or plain launches)
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(fails.p, 0, std::max<uint64_t>(P, 1) * 4, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(misc.p, 0, 64, st);
+        if (e == cudaSuccess)
+            e = vf::launch_batch_scatter(ddesc.as<vf::BatchItem>(), doff.as<uint64_t>(), P, total,
+                                         dcur.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(), st);
+        if (e == cudaSuccess) e = vf::launch_lge(a, grid, st);
+        return e;
+    };
+    if (opts.use_graph) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        VF_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue();
+        cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            free_data();
+            return fail(VF_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) {
+            PhaseTimer t(kPhLge, st);
+            e = cudaGraphLaunch(exec, st);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            free_data();
+            return fail(VF_ECUDA, std::string("graph launch failed: ") + cudaGetErrorString(e));
+        }
+    } else {
+        PhaseTimer t(kPhLge, st);
+        cudaError_t e = enqueue();
+        if (e != cudaSuccess) {
+            free_data();
+            return fail(VF_ECUDA, std::string("batched solve launch failed: ") + cudaGetErrorString(e));
+        }
+    }
+    std::vector<uint32_t> fail_bits(P, 0);
+    VF_CK(cudaMemcpyAsync(fail_bits.data(), fails.p, P * 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaStreamSynchronize(st));
+    // fuse-regime structures (above the threshold): one solver each
+    for (uint32_t j = 0; j < P; j++) {
+        if (info[j].regime != VF_REGIME_FUSE) continue;
+        std::vector<unsigned long long> start(info[j].shards + 1, 0);
+        for (uint64_t s2 = 0; s2 < info[j].shards; s2++) start[s2 + 1] = start[s2] + counts[hist_off[j] + s2];
+        DevBuf dstart;
+        rs = h2d(dstart, start, st);
+        if (rs != VF_OK) return free_data(), rs;
+        uint64_t peeled = 0, rounds = 0;
+        rs = solve_fuse(info[j], make_geom(info[j]), loc.as<uint64_t>() + key_off[j],
+                        info[j].kind == VF_FUNC ? val.as<uint32_t>() + key_off[j] : nullptr,
+                        dstart.as<unsigned long long>(), data[j], st, &peeled, &rounds);
+        if (rs == VF_EBUILD) fail_bits[j] |= vf::kErrUnsolvable;
+        else if (rs != VF_OK) return free_data(), rs;
+        info[j].peeled = peeled;
+        info[j].rounds = rounds;
+    }
+    VF_CK(cudaStreamSynchronize(st));
+    for (uint32_t j = 0; j < P; j++) {
+        if (fail_bits[j] & vf::kErrCapacity) {
+            free_data();
+            return fail(VF_ECAPACITY, "batched LGE shard exceeds the solver capacity");
+        }
+        if (fail_bits[j]) {
+            cudaFreeAsync(data[j], st);
+            data[j] = nullptr;
+            failed.push_back(pending[j]);
+            continue;
+        }
+        vf_struct* sp = new vf_struct;
+        sp->info = info[j];
+        sp->geom = make_geom(info[j]);
+        sp->data = data[j];
+        sp->device = dev;
+        out[pending[j]] = sp;
+        data[j] = nullptr;
+    }
+    return VF_OK;
+}
+
+struct TuneKey {
+    uint32_t count;
+    uint64_t total, nmax;
+    bool operator<(const TuneKey& o) const {
+        return count != o.count ? count < o.count : total != o.total ? total < o.total : nmax < o.nmax;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, vf_batch_opts> g_tune_cache;
 
 }  // namespace
 
@@ -502,8 +787,8 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
             rs = solve_fuse(in, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
                             startb.as<unsigned long long>(), data.as<uint8_t>(), st, &peeled, &rounds);
         else
-            rs = solve_lge(in, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
-                           startb.as<unsigned long long>(), data.as<uint8_t>(), st, &peeled, &core);
+            rs = solve_lge(in, start, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
+                           data.as<uint8_t>(), st, &peeled, &core);
         in.peeled = peeled;
         in.core = in.regime == VF_REGIME_FUSE ? 0 : core;
         in.rounds = rounds;
@@ -617,6 +902,149 @@ vf_status vf_timing_read(double* ms, uint64_t* launches) {
     }
     g_timed.clear();
     return rs;
+}
+
+vf_status vf_batch_opts_default(vf_batch_opts* o) {
+    if (!o) return fail(VF_EINVAL, "vf_batch_opts_default: NULL");
+    std::memset(o, 0, sizeof *o);
+    o->lge_threshold = 800000;
+    o->lge_target = 16384;
+    o->lpt = 1;
+    o->use_graph = 1;
+    return VF_OK;
+}
+
+vf_status vf_build_batch(const vf_batch_item* items, uint32_t count, const vf_params* common,
+                         const vf_batch_opts* opts, void* stream, vf_struct** out) {
+    g_last_error.clear();
+    if (!common || !out || (count > 0 && !items)) return fail(VF_EINVAL, "vf_build_batch: NULL argument");
+    vf_batch_opts o;
+    if (opts) o = *opts; else vf_batch_opts_default(&o);
+    if (o.lge_target == 0) return fail(VF_EINVAL, "vf_build_batch: lge_target must be positive");
+    for (uint32_t i = 0; i < count; i++) {
+        out[i] = nullptr;
+        const vf_batch_item& it = items[i];
+        if (it.b < 1 || it.b > 32 || (it.kind != VF_FUNC && it.kind != VF_FILTER))
+            return fail(VF_EINVAL, "vf_build_batch: bad b or kind");
+        if (it.n > 0 && !it.keys) return fail(VF_EINVAL, "vf_build_batch: keys is NULL");
+        if (it.kind == VF_FUNC && it.n > 0 && !it.values) return fail(VF_EINVAL, "vf_build_batch: a function needs values");
+        if (it.n >= (uint64_t(1) << 32)) return fail(VF_ECAPACITY, "vf_build_batch: at most 2^32-1 keys per structure");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    VF_CK(cudaGetDevice(&dev));
+    std::vector<Staged> staged(count);
+    std::vector<const uint64_t*> kdev(count);
+    std::vector<const void*> vdev(count, nullptr);
+    for (uint32_t i = 0; i < count; i++) {
+        vf_status rs = stage_keys(VF_KEYS_U64, items[i].keys, nullptr, items[i].n, st, staged[i]);
+        if (rs != VF_OK) return rs;
+        kdev[i] = static_cast<const uint64_t*>(staged[i].keys);
+        if (items[i].kind == VF_FUNC && items[i].n > 0) {
+            if (on_device(items[i].values)) {
+                vdev[i] = items[i].values;
+            } else {
+                const size_t vb = items[i].n * value_bytes(items[i].b);
+                VF_CK(staged[i].vbuf.alloc(vb, st));
+                VF_CK(cudaMemcpyAsync(staged[i].vbuf.p, items[i].values, vb, cudaMemcpyHostToDevice, st));
+                vdev[i] = staged[i].vbuf.p;
+            }
+        }
+    }
+    std::vector<uint32_t> pending(count), attempt(count, 0);
+    for (uint32_t i = 0; i < count; i++) pending[i] = i;
+    for (int round = 0; round <= common->max_retries && !pending.empty(); round++) {
+        std::vector<uint32_t> failed;
+        vf_status rs = build_batch_once(items, pending, attempt, *common, o, kdev, vdev, st, dev, out, failed);
+        if (rs != VF_OK) {
+            for (uint32_t i = 0; i < count; i++) {
+                vf_free(out[i]);
+                out[i] = nullptr;
+            }
+            return rs;
+        }
+        for (uint32_t i : failed) attempt[i]++;
+        pending.swap(failed);
+    }
+    if (!pending.empty()) {
+        for (uint32_t i = 0; i < count; i++) {
+            vf_free(out[i]);
+            out[i] = nullptr;
+        }
+        return fail(VF_EBUILD, "vf_build_batch: a structure failed every attempt");
+    }
+    return VF_OK;
+}
+
+vf_status vf_tune_batch(const vf_batch_item* items, uint32_t count, const vf_params* common, void* stream,
+                        vf_batch_opts* best, double* best_ms) {
+    if (!common || !best || (count > 0 && !items)) return fail(VF_EINVAL, "vf_tune_batch: NULL argument");
+    uint64_t total = 0, nmax = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        total += items[i].n;
+        nmax = std::max<uint64_t>(nmax, items[i].n);
+    }
+    const TuneKey key{count, total, nmax};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best = it->second;
+            if (best_ms) *best_ms = -1.0;
+            return VF_OK;
+        }
+    }
+    // sample: every k-th structure, about 5% of the keys and at least 16 structures
+    std::vector<vf_batch_item> sample;
+    const uint64_t want = std::max<uint64_t>(total / 20, 1);
+    const uint32_t stride = uint32_t(std::max<uint64_t>(1, std::min<uint64_t>(count / 16 + 1, total / want)));
+    for (uint32_t i = 0; i < count; i += stride) sample.push_back(items[i]);
+    std::vector<vf_batch_opts> cands;
+    for (uint64_t thr : {common->lge_threshold, ~uint64_t(0)})
+        for (uint64_t tgt : {uint64_t(8192), uint64_t(16384)})
+            for (int lpt : {1, 0}) {
+                vf_batch_opts o;
+                vf_batch_opts_default(&o);
+                o.lge_threshold = thr;
+                o.lge_target = tgt;
+                o.lpt = lpt;
+                cands.push_back(o);
+            }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    VF_CK(cudaEventCreate(&e0));
+    VF_CK(cudaEventCreate(&e1));
+    std::vector<vf_struct*> outs(sample.size(), nullptr);
+    double bms = 1e300;
+    vf_batch_opts bo = cands[0];
+    for (size_t c = 0; c <= cands.size(); c++) {
+        const vf_batch_opts& o = cands[c == 0 ? 0 : c - 1];  // the first candidate runs twice (warm-up)
+        VF_CK(cudaEventRecord(e0, st));
+        vf_status rs = vf_build_batch(sample.data(), uint32_t(sample.size()), common, &o, stream, outs.data());
+        VF_CK(cudaEventRecord(e1, st));
+        VF_CK(cudaEventSynchronize(e1));
+        for (auto*& p : outs) {
+            vf_free(p);
+            p = nullptr;
+        }
+        if (rs != VF_OK) continue;
+        float ms = 0.f;
+        VF_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (c > 0 && ms < bms) {
+            bms = ms;
+            bo = o;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bms >= 1e300) return fail(VF_EBUILD, "vf_tune_batch: no candidate built the sample");
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = bo;
+    }
+    *best = bo;
+    if (best_ms) *best_ms = bms;
+    return VF_OK;
 }
 
 vf_status vf_free(vf_struct* s) {

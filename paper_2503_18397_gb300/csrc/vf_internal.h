@@ -54,18 +54,30 @@ cudaError_t launch_peel(FuseSolveArgs a, cudaStream_t st);
 cudaError_t launch_assign(FuseSolveArgs a, cudaStream_t st);
 
 // LGE regime: one CTA per shard (peel + lazy Gaussian elimination + assign).
+// A task is one shard of one structure; a launch may mix structures.
+struct LgeTask {
+    uint64_t loc_off;    // first key of the shard in the bucketed loc / val arrays
+    uint64_t cell_base;  // first cell of the shard in `data`
+    uint8_t* data;       // the structure's data array
+    uint32_t m;          // keys in the shard
+    uint32_t cells;      // cells per shard
+    int32_t b;
+    int32_t kind;        // 0 function (values from `val`), 1 filter (fingerprints)
+    uint32_t item;       // structure index: failures are recorded in item_fail[item]
+    uint32_t pad;
+};
+
 struct LgeArgs {
-    const uint64_t* loc;
-    const uint32_t* val;              // NULL for a filter
-    const unsigned long long* start;  // S+1
-    uint32_t S;
-    Geom g;
-    uint8_t* data;
+    const LgeTask* tasks;
+    uint32_t ntasks;
+    const uint64_t* loc;              // bucketed local signatures
+    const uint32_t* val;              // bucketed values (functions)
+    uint32_t* item_fail;              // per-structure failure bits (kErr*)
     uint32_t* scratch;                // per-CTA global scratch
     uint64_t scratch_words_per_cta;
     uint32_t m_cap, v_cap;            // largest shard / cell count the scratch layout holds
-    uint32_t* err;
-    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] shard counter
+    uint32_t* err;                    // OR of all failure bits
+    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] task counter
 };
 // Layout (in 32-bit words) of one CTA's LGE scratch slab for shards of at most
 // m keys and V cells.
@@ -113,6 +125,23 @@ __host__ __device__ constexpr LgeOffsets lge_offsets(uint32_t m, uint32_t V) {
 cudaError_t launch_lge(const LgeArgs& a, unsigned grid, cudaStream_t st);
 unsigned lge_grid();
 uint64_t lge_scratch_words_per_cta(uint32_t m_cap, uint32_t v_cap);
+
+// One structure of a batched build (device descriptor).
+struct BatchItem {
+    const uint64_t* keys;  // this structure's keys
+    const void* vals;      // its values (functions) or NULL
+    uint64_t key_off;      // first index of its keys in the batch's key space
+    uint64_t kh, kl;       // lane keys of its seed
+    uint32_t n;
+    int32_t h;             // shard bits
+    uint32_t hist_off;     // first (structure, shard) slot
+    int32_t b;
+};
+
+cudaError_t launch_batch_hist(const BatchItem* items, const uint64_t* key_off, uint32_t count, uint64_t total,
+                              uint32_t* hist, cudaStream_t st);
+cudaError_t launch_batch_scatter(const BatchItem* items, const uint64_t* key_off, uint32_t count, uint64_t total,
+                                 unsigned long long* cursor, uint64_t* loc, uint32_t* val, cudaStream_t st);
 
 cudaError_t launch_query(int key_kind, const void* keys, const uint64_t* offs, uint64_t m, const Geom& g,
                          const uint8_t* data, void* out, cudaStream_t st);

@@ -29,8 +29,8 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 uint64_t lge_scratch_words_per_cta(uint32_t m_cap, uint32_t v_cap) { return lge_offsets(m_cap, v_cap).total; }
 
-__device__ __forceinline__ uint32_t rhs_of(const LgeArgs& a, uint64_t ge) {
-    return a.val ? __ldg(a.val + ge) : fingerprint(__ldg(a.loc + ge), a.g.b);
+__device__ __forceinline__ uint32_t rhs_of(const LgeArgs& a, const LgeTask& t, uint64_t ge) {
+    return t.kind == 0 ? __ldg(a.val + ge) : fingerprint(__ldg(a.loc + ge), t.b);
 }
 
 __device__ __forceinline__ uint32_t deg_of(const uint32_t* degw, uint32_t v) {
@@ -98,24 +98,45 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
     uint32_t* dense = scr + o.dense;
     uint32_t* lc = scr + o.lc;
     uint32_t* L = scr + o.L;
-    const int b = a.g.b;
+    constexpr uint32_t kBad = kErrUnsolvable | kErrCapacity | kErrLgeSize | kErrDegOverflow;
 
     for (;;) {
+        __shared__ uint32_t s_skip;
         if (tid == 0) {
-            uint32_t bad = *reinterpret_cast<volatile uint32_t*>(a.err) & (kErrUnsolvable | kErrCapacity | kErrLgeSize |
-                                                                         kErrDegOverflow);
-            s_shard = bad ? kNone : atomicAdd(&a.stats[2], 1u);
+            s_shard = atomicAdd(&a.stats[2], 1u);
+            s_skip = s_shard < a.ntasks &&
+                     (*reinterpret_cast<volatile uint32_t*>(a.item_fail + a.tasks[s_shard].item) & kBad) != 0;
             s_fail = 0;
         }
         __syncthreads();
         const uint32_t s = s_shard;
-        if (s >= a.S) break;
-        const uint64_t e0 = a.start[s];
-        const uint32_t m = uint32_t(a.start[s + 1] - e0);
-        const uint32_t V = uint32_t(a.g.cells);
-        const uint64_t cbase = uint64_t(s) * a.g.cells;
+        if (s >= a.ntasks) break;
+        if (s_skip) {  // another shard of this structure already failed: the attempt is void
+            __syncthreads();
+            continue;
+        }
+        const LgeTask task = a.tasks[s];
+        const uint64_t e0 = task.loc_off;
+        const uint32_t m = task.m;
+        const uint32_t V = task.cells;
+        const uint64_t cbase = task.cell_base;
+        const int b = task.b;
+        uint8_t* const data = task.data;
+        Geom gg;
+        gg.kh = gg.kl = 0;
+        gg.cells = V;
+        gg.span = 0;
+        gg.lg_seg = 0;
+        gg.h = 0;
+        gg.regime = kRegimeLge;
+        gg.b = b;
+        gg.kind = task.kind;
+        gg.pad = 0;
         if (m > a.m_cap || V > a.v_cap || V > 65535u) {
-            if (tid == 0) atomicOr(a.err, kErrCapacity);
+            if (tid == 0) {
+                atomicOr(a.err, kErrCapacity);
+                atomicOr(a.item_fail + task.item, kErrCapacity);
+            }
             __syncthreads();
             continue;
         }
@@ -129,7 +150,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
         __syncthreads();
         for (uint32_t e = tid; e < m; e += T) {
             uint64_t v[3];
-            edge_of(a.g, __ldg(a.loc + e0 + e), v);
+            edge_of(gg, __ldg(a.loc + e0 + e), v);
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 uint32_t vk = uint32_t(v[k]);
@@ -142,7 +163,10 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
         }
         __syncthreads();
         if (s_fail) {
-            if (tid == 0) atomicOr(a.err, kErrDegOverflow);
+            if (tid == 0) {
+                atomicOr(a.err, kErrDegOverflow);
+                atomicOr(a.item_fail + task.item, kErrDegOverflow);
+            }
             __syncthreads();
             continue;
         }
@@ -351,7 +375,10 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 __syncthreads();
             }
             if (s_fail) {
-                if (tid == 0) atomicOr(a.err, kErrLgeSize);
+                if (tid == 0) {
+                    atomicOr(a.err, kErrLgeSize);
+                    atomicOr(a.item_fail + task.item, kErrLgeSize);
+                }
                 __syncthreads();
                 continue;
             }
@@ -359,7 +386,10 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             const uint32_t AW = (A + 31) / 32;
             const uint32_t RS = AW | 1u;  // odd row stride: conflict-free shared-memory rows
             if (uint64_t(S) * AW > o.lpool || uint64_t(D) * RS + 2ull * D + A > kLgeSmemWords) {
-                if (tid == 0) atomicOr(a.err, kErrLgeSize);
+                if (tid == 0) {
+                    atomicOr(a.err, kErrLgeSize);
+                    atomicOr(a.item_fail + task.item, kErrLgeSize);
+                }
                 __syncthreads();
                 continue;
             }
@@ -387,7 +417,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                         }
                     }
                     L[uint64_t(si) * AW + w] = acc;
-                    if (w == 0) lc[si] = c ^ rhs_of(a, e0 + e);
+                    if (w == 0) lc[si] = c ^ rhs_of(a, task, e0 + e);
                 }
                 __syncthreads();
             }
@@ -413,7 +443,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 }
                 rows[d * RS + w] = acc;
                 if (w == 0) {
-                    rhs[d] = c ^ rhs_of(a, e0 + e);
+                    rhs[d] = c ^ rhs_of(a, task, e0 + e);
                     pivf[d] = 0;
                 }
             }
@@ -447,12 +477,15 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 if (!pivf[d] && rhs[d] != 0) s_fail = 1;
             __syncthreads();
             if (s_fail) {
-                if (tid == 0) atomicOr(a.err, kErrUnsolvable);
+                if (tid == 0) {
+                    atomicOr(a.err, kErrUnsolvable);
+                    atomicOr(a.item_fail + task.item, kErrUnsolvable);
+                }
                 __syncthreads();
                 continue;
             }
             for (uint32_t c = tid; c < A; c += T)
-                cell_put_zero(a.data, b, cbase + __ldcg(&actv[c]), colrow[c] != kNone ? rhs[colrow[c]] : 0u);
+                cell_put_zero(data, b, cbase + __ldcg(&actv[c]), colrow[c] != kNone ? rhs[colrow[c]] : 0u);
             __syncthreads();
             // solved variables, in solve order (their equations as generated)
             for (uint32_t r = 0; r < R; r++) {
@@ -461,13 +494,13 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 for (uint32_t si = lo + tid; si < hi; si += T) {
                     const uint32_t j = __ldcg(&solves[si]) >> 16, x = __ldcg(&solves[si]) & 0xFFFFu;
                     const uint32_t e = __ldcg(&core[j]);
-                    uint32_t val = rhs_of(a, e0 + e);
+                    uint32_t val = rhs_of(a, task, e0 + e);
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
                         uint32_t u = __ldcg(&cev[3 * e + k]);
-                        if (u != x) val ^= cell_get_cg(a.data, b, cbase + u);
+                        if (u != x) val ^= cell_get_cg(data, b, cbase + u);
                     }
-                    cell_put_zero(a.data, b, cbase + x, val);
+                    cell_put_zero(data, b, cbase + x, val);
                 }
                 __syncthreads();
             }
@@ -479,11 +512,11 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             for (uint32_t i = lo + tid; i < hi; i += T) {
                 const uint32_t ent = __ldcg(&porder[i]);
                 const uint32_t e = ent >> 2, side = ent & 3u;
-                uint32_t val = rhs_of(a, e0 + e);
+                uint32_t val = rhs_of(a, task, e0 + e);
 #pragma unroll
                 for (uint32_t k = 0; k < 3; k++)
-                    if (k != side) val ^= cell_get_cg(a.data, b, cbase + __ldcg(&cev[3 * e + k]));
-                cell_put_zero(a.data, b, cbase + __ldcg(&cev[3 * e + side]), val);
+                    if (k != side) val ^= cell_get_cg(data, b, cbase + __ldcg(&cev[3 * e + k]));
+                cell_put_zero(data, b, cbase + __ldcg(&cev[3 * e + side]), val);
             }
             __syncthreads();
         }
@@ -508,7 +541,7 @@ unsigned lge_grid() {
 }
 
 cudaError_t launch_lge(const LgeArgs& a, unsigned grid, cudaStream_t st) {
-    if (a.S == 0) return cudaSuccess;
+    if (a.ntasks == 0) return cudaSuccess;
     lge_grid();
     k_lge<<<grid, kLT, kLgeSmemWords * 4, st>>>(a);
     return cudaGetLastError();

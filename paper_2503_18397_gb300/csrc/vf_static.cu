@@ -17,10 +17,11 @@ constexpr uint32_t kStaticMaxKeys = 16384;
 constexpr uint32_t kStaticMaxCells = (kStaticMaxKeys * 112u + 99u) / 100u;
 constexpr uint64_t kMiscWords = 64;   // [0] error word, [4..] solver statistics
 constexpr uint64_t kStartWords = 4;   // shard starts {0, n} as two 64-bit words
+constexpr uint64_t kTaskWords = (sizeof(LgeTask) + 15) / 16 * 4;  // the solver's one task
 constexpr uint64_t kLocWords = 2ull * kStaticMaxKeys;
 constexpr uint64_t kValWords = kStaticMaxKeys;
 constexpr uint64_t kSlabWords = lge_offsets(kStaticMaxKeys, kStaticMaxCells).total;
-constexpr uint64_t kStaticWords = kMiscWords + kStartWords + kLocWords + kValWords + kSlabWords;
+constexpr uint64_t kStaticWords = kMiscWords + kStartWords + kTaskWords + kLocWords + kValWords + kSlabWords;
 
 // The scratch itself: about 4.2 MB, resident on every GPU that loads the
 // library for the life of the process. Shared by every call.
@@ -114,8 +115,9 @@ extern "C" vf_status vf_build_static(const uint64_t* keys, const void* values, u
     if (rs != VF_OK) return rs;
     uint32_t* misc = base;
     unsigned long long* start = reinterpret_cast<unsigned long long*>(base + kMiscWords);
-    uint64_t* loc = reinterpret_cast<uint64_t*>(base + kMiscWords + kStartWords);
-    uint32_t* val = base + kMiscWords + kStartWords + kLocWords;
+    LgeTask* tasks_dev = reinterpret_cast<LgeTask*>(base + kMiscWords + kStartWords);
+    uint64_t* loc = reinterpret_cast<uint64_t*>(base + kMiscWords + kStartWords + kTaskWords);
+    uint32_t* val = base + kMiscWords + kStartWords + kTaskWords + kLocWords;
     uint32_t* slab = val + kValWords;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
@@ -137,14 +139,25 @@ extern "C" vf_status vf_build_static(const uint64_t* keys, const void* values, u
             return fail_static(VF_ECUDA, "vf_build_static: clearing scratch failed");
         k_static_prep<<<32, 256, 0, st>>>(keys, p.kind == VF_FUNC ? values : nullptr, uint32_t(n), in.b, g.kh, g.kl,
                                           loc, val, start);
+        LgeTask task;
+        std::memset(&task, 0, sizeof task);
+        task.loc_off = 0;
+        task.cell_base = 0;
+        task.data = static_cast<uint8_t*>(data);
+        task.m = uint32_t(n);
+        task.cells = uint32_t(in.cells);
+        task.b = in.b;
+        task.kind = in.kind;
+        task.item = 0;
+        if (cudaMemcpyAsync(tasks_dev, &task, sizeof task, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return fail_static(VF_ECUDA, "vf_build_static: task upload failed");
         LgeArgs a;
         std::memset(&a, 0, sizeof a);
+        a.tasks = tasks_dev;
+        a.ntasks = n > 0 ? 1u : 0u;
         a.loc = loc;
-        a.val = p.kind == VF_FUNC ? val : nullptr;
-        a.start = start;
-        a.S = 1;
-        a.g = g;
-        a.data = static_cast<uint8_t*>(data);
+        a.val = val;
+        a.item_fail = misc;
         a.scratch = slab;
         a.scratch_words_per_cta = kSlabWords;
         a.m_cap = kStaticMaxKeys;

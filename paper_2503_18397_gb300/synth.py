@@ -87,3 +87,37 @@ def log_uniform_sizes(count: int, lo: float, hi: float, seed: int) -> np.ndarray
     rng = np.random.Generator(np.random.PCG64(seed ^ 0x10C))
     u = rng.uniform(np.log10(lo), np.log10(hi), size=count)
     return np.floor(10.0 ** u).astype(np.int64)
+
+
+def _signed(c: int) -> int:
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def u64_keys_torch(start: int, count: int, seed: int, device="cuda"):
+    """u64_keys on a device as an int64 tensor holding the same 64-bit patterns
+    (wrapping int64 arithmetic; logical shifts by masking)."""
+    import torch
+
+    k = torch.arange(start, start + count, dtype=torch.int64, device=device)
+    k ^= _signed(key_salt(seed))
+    m31 = (1 << 31) - 1
+    k ^= (k >> 33) & m31
+    k *= _signed(0xFF51AFD7ED558CCD)
+    k ^= (k >> 33) & m31
+    k *= _signed(0xC4CEB9FE1A85EC53)
+    k ^= (k >> 33) & m31
+    return k
+
+
+def values_torch(count: int, b: int, seed: int, device="cuda"):
+    """Uniform b-bit values on a device (narrowest unsigned dtype), seeded."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed ^ 0xA11CE)
+    v = torch.randint(0, 1 << b, (count,), dtype=torch.int64, device=device, generator=g)
+    if b <= 8:
+        return v.to(torch.uint8)
+    if b <= 16:
+        return v.to(torch.int32).to(torch.int16).view(torch.uint16)
+    return v.to(torch.int64).to(torch.int32).view(torch.uint32)

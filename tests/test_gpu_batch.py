@@ -1,0 +1,112 @@
+"""Batched construction (the batching pattern): many independent structures of
+uneven sizes built together must each equal the structure vf_build makes from
+the same keys, seed and parameters (same geometry, seed, retries; every key
+decodes; the oracle's query on the batch-built array matches the GPU query)."""
+import numpy as np
+import pytest
+
+from paper_2503_18397_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_18397_gb300 import build
+
+    build.build()
+    import paper_2503_18397_gb300 as vf
+
+    vf.lib()
+    return vf
+
+
+def _dev(a):
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).cuda()
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.view(np.int16)).cuda().view(torch.uint16)
+    if a.dtype == np.uint32:
+        return torch.from_numpy(a.view(np.int32)).cuda().view(torch.uint32)
+    return torch.from_numpy(a).cuda()
+
+
+def _host(t):
+    m = {torch.uint16: (torch.int16, np.uint16), torch.uint32: (torch.int32, np.uint32)}
+    if t.dtype in m:
+        return t.view(m[t.dtype][0]).cpu().numpy().view(m[t.dtype][1])
+    return t.cpu().numpy()
+
+
+FIELDS = ("regime", "h", "h_bb", "h_dup", "shards", "M", "c", "lg_seg", "seg", "l", "T", "cells", "total_cells",
+          "data_bytes", "seed", "retries")
+
+
+def _make(sizes, seed0):
+    rng = np.random.default_rng(seed0)
+    items, host = [], []
+    for i, n in enumerate(sizes):
+        kind = int(rng.integers(0, 2))
+        b = int(rng.choice([1, 8, 16, 32]))
+        keys = synth.u64_keys(i * 10_000_000, int(n), seed0)
+        vals = synth.values(int(n), b, seed0 + i) if kind == 0 else None
+        items.append((_dev(keys), None if vals is None else _dev(vals), kind, b, 100 + i))
+        host.append((keys, vals, kind, b))
+    return items, host
+
+
+def _check_against_single(vf, orc, items, host, structs, opts_like_default=True):
+    for (kd, vd, kind, b, seed), (keys, vals, _, _), s in zip(items, host, structs):
+        info = s.info
+        out = _host(s.query(kd))
+        if kind == 0:
+            assert (out == vals).all()
+        else:
+            assert out.all()
+        oi = orc.Info()
+        for f, _ in orc.Info._fields_:
+            setattr(oi, f, getattr(info, f))
+        ref_q = orc.query(oi, vf.vf_export(s), keys)
+        assert (ref_q == out).all()
+        if opts_like_default:
+            single = vf.vf_build(kd, vd, params=vf.vf_params_default(kind=kind, b=b, seed=seed))
+            si = single.info
+            for f in FIELDS:
+                assert getattr(info, f) == getattr(si, f), f
+            single.free()
+
+
+def test_batch_matches_single_builds(vf, orc):
+    sizes = [0, 1, 3, 40, 999, 5000, 20_000, 70_000, 150_000, 12, 333, 31_000]
+    items, host = _make(sizes, 7)
+    structs = vf.vf_build_batch(items, params=vf.vf_params_default(), opts=vf.vf_batch_opts_default(use_graph=1))
+    _check_against_single(vf, orc, items, host, structs)
+
+
+def test_batch_without_graph_and_natural_order(vf, orc):
+    items, host = _make([100, 2000, 17_000, 40_000], 9)
+    structs = vf.vf_build_batch(items, opts=vf.vf_batch_opts_default(use_graph=0, lpt=0))
+    _check_against_single(vf, orc, items, host, structs)
+
+
+def test_batch_mixed_regimes(vf, orc):
+    # one structure above the fuse threshold among small LGE ones
+    items, host = _make([900_000, 3_000, 60_000], 11)
+    structs = vf.vf_build_batch(items)
+    assert structs[0].info.regime == vf.REGIME_FUSE and structs[1].info.regime == vf.REGIME_LGE
+    _check_against_single(vf, orc, items, host, structs)
+
+
+def test_batch_all_lge_threshold_and_tuner(vf, orc):
+    sizes = synth.log_uniform_sizes(48, 1e3, 3e5, 5)
+    items, host = _make(sizes, 13)
+    best, ms = vf.vf_tune_batch(items)
+    assert best.lge_target in (8192, 16384) and best.lpt in (0, 1)
+    structs = vf.vf_build_batch(items, opts=best)
+    _check_against_single(vf, orc, items, host, structs, opts_like_default=False)
+    best2, ms2 = vf.vf_tune_batch(items)
+    assert ms2 == -1.0 and best2.as_dict() == best.as_dict()  # cached per batch shape
