@@ -414,9 +414,18 @@ vf_status solve_lge(const vf_info& in, const std::vector<unsigned long long>& st
 
 // ------------------------------------------------------------ batched builds
 
-struct BatchState {
-    std::vector<uint32_t> attempt;  // per item
-};
+// One non-blocking stream per host thread and device for graph capture.
+cudaStream_t capture_stream() {
+    thread_local std::map<int, cudaStream_t> streams;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    auto it = streams.find(dev);
+    if (it != streams.end()) return it->second;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    streams[dev] = s;
+    return s;
+}
 
 // One attempt of every pending item: plan, histogram, scatter, solve.
 // Built items go to out[]; failed ones to `failed`.
@@ -560,21 +569,25 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     a.err = misc.as<uint32_t>();
     a.stats = misc.as<uint32_t>() + 4;
     // scatter + solver: one CUDA graph (or plain launches)
-    auto enqueue = [&]() -> cudaError_t {
-        cudaError_t e = cudaMemsetAsync(fails.p, 0, std::max<uint64_t>(P, 1) * 4, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(misc.p, 0, 64, st);
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(fails.p, 0, std::max<uint64_t>(P, 1) * 4, q);
+        if (e == cudaSuccess) e = cudaMemsetAsync(misc.p, 0, 64, q);
         if (e == cudaSuccess)
             e = vf::launch_batch_scatter(ddesc.as<vf::BatchItem>(), doff.as<uint64_t>(), P, total,
-                                         dcur.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(), st);
-        if (e == cudaSuccess) e = vf::launch_lge(a, grid, st);
+                                         dcur.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(), q);
+        if (e == cudaSuccess) e = vf::launch_lge(a, grid, q);
         return e;
     };
     if (opts.use_graph) {
+        // Captured on a private stream (the legacy default stream cannot be
+        // captured); the graph then runs in order on the caller's stream.
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-        VF_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = enqueue();
-        cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+        cudaStream_t cs = capture_stream();
+        if (!cs) return free_data(), fail(VF_ECUDA, "could not create the capture stream");
+        VF_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue(cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             free_data();
@@ -593,7 +606,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
         }
     } else {
         PhaseTimer t(kPhLge, st);
-        cudaError_t e = enqueue();
+        cudaError_t e = enqueue(st);
         if (e != cudaSuccess) {
             free_data();
             return fail(VF_ECUDA, std::string("batched solve launch failed: ") + cudaGetErrorString(e));
