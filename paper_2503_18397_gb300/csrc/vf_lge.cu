@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ uint32_t s_shard, s_fail;
     __shared__ uint32_t s_cnt[4];
-    __shared__ uint32_t s_C, s_rem, s_A, s_S, s_D, s_r, s_apos, s_nact, s_nbatch, s_piv;
+    __shared__ uint32_t s_C, s_rem, s_A, s_S, s_D, s_r, s_apos, s_nact, s_nbatch, s_piv, s_lo;
     __shared__ uint32_t s_hist[256];
     __shared__ uint32_t s_batch[kMaxBatch];
     __shared__ uint32_t s_part[kLT];
@@ -231,21 +231,26 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             for (uint32_t v = tid; v <= V; v += T) inc_off[v] = 0;
             __syncthreads();
             C = s_C;
+            // Variable states and equation states move to shared memory when they
+            // fit (the peel's arrays are dead now); otherwise they stay in the slab.
+            // Equation word: bits 0-1 idle count, bit 2 done, bits 3.. XOR of its idle variables.
+            const bool in_smem = uint64_t(V) + C <= kLgeSmemWords;
+            uint32_t* vst = in_smem ? sm : vstate;
+            uint32_t* est = in_smem ? sm + V : eqst;
             for (uint32_t j = tid; j < C; j += T) {
                 const uint32_t* evp = cev + 3 * __ldcg(&core[j]);
                 const uint32_t ev[3] = {__ldcg(evp), __ldcg(evp + 1), __ldcg(evp + 2)};
                 atomicAdd(&inc_off[ev[0]], 1u);
                 atomicAdd(&inc_off[ev[1]], 1u);
                 atomicAdd(&inc_off[ev[2]], 1u);
-                eqst[j] = ((ev[0] ^ ev[1] ^ ev[2]) << 2) | 3u;
-                eqdone[j] = 0;
+                est[j] = ((ev[0] ^ ev[1] ^ ev[2]) << 3) | 3u;
             }
+            for (uint32_t v = tid; v < V; v += T) vst[v] = 0;
             for (uint32_t i = tid; i < 256; i += T) s_hist[i] = 0;
             __syncthreads();
             // activation order: core degree, heaviest first (counting sort)
             for (uint32_t v = tid; v < V; v += T) {
                 uint32_t d = __ldcg(&inc_off[v]);
-                vstate[v] = 0;
                 if (d) atomicAdd(&s_hist[min(d, 255u)], 1u);
             }
             cta_exclusive_scan(inc_off, V + 1, s_part);
@@ -273,12 +278,13 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             }
             if (tid == 0) {
                 s_rem = C;
-                s_A = s_S = s_D = s_r = s_apos = 0;
+                s_A = s_S = s_D = s_r = s_apos = s_lo = 0;
                 s_cnt[0] = s_cnt[1] = 0;
                 soff[0] = 0;
             }
             fi = 0;
             const uint32_t max_rounds = m + V + 2;
+            const unsigned lane = tid & 31u, warp = tid >> 5;
             __syncthreads();
             for (;;) {
                 if (s_rem == 0 || s_fail) break;
@@ -290,38 +296,64 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 const uint32_t nF = s_cnt[fi];
                 uint32_t* G = fr[fi ^ 1];
                 if (nF == 0) {
-                    // activate the next heaviest idle variables that still occur in open equations
-                    if (tid == 0) {
-                        uint32_t K = max(1u, min(kMaxBatch, s_rem / 100u));
-                        uint32_t nb = 0;
-                        while (nb < K && s_apos < s_nact) {
-                            uint32_t v = __ldcg(&act[s_apos++]);
-                            if (__ldcg(&vstate[v]) != 0) continue;
-                            bool live = false;
-                            for (uint32_t q = __ldcg(&inc_off[v]); q < __ldcg(&inc_off[v + 1]) && !live; q++)
-                                live = __ldcg(&eqdone[__ldcg(&inc_list[q])]) == 0;
-                            if (live) s_batch[nb++] = v;
+                    // Activate the next heaviest idle variables that still occur in
+                    // open equations: the block examines a window of the activation
+                    // order in parallel and keeps the first K eligible ones.
+                    const uint32_t K = max(1u, min(kMaxBatch, s_rem / 100u));
+                    const uint32_t base = s_apos;
+                    const uint32_t wn = min(T, s_nact - base);
+                    bool elig = false;
+                    uint32_t v = 0;
+                    if (tid < wn) {
+                        v = __ldcg(&act[base + tid]);
+                        if (vst[v] == 0) {
+                            const uint32_t q1 = __ldcg(&inc_off[v + 1]);
+                            for (uint32_t q = __ldcg(&inc_off[v]); q < q1 && !elig; q++)
+                                elig = (est[__ldcg(&inc_list[q])] & 4u) == 0;
                         }
+                    }
+                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, elig);
+                    if (lane == 0) s_part[warp] = __popc(bal);
+                    __syncthreads();
+                    if (tid == 0) {
+                        uint32_t run = 0;
+                        for (uint32_t w = 0; w < (T + 31) / 32; w++) {
+                            const uint32_t x = s_part[w];
+                            s_part[w] = run;
+                            run += x;
+                        }
+                        s_part[kLT - 1] = run;  // total eligible
+                    }
+                    __syncthreads();
+                    const uint32_t rank = s_part[warp] + __popc(bal & ((1u << lane) - 1u));
+                    const uint32_t tot = s_part[kLT - 1];
+                    if (elig && rank < K) s_batch[rank] = v;
+                    if (elig && rank == K - 1) s_nbatch = base + tid + 1;  // new scan position
+                    __syncthreads();
+                    if (tid == 0) {
+                        const uint32_t nb = min(K, tot);
+                        s_apos = tot >= K ? s_nbatch : base + wn;
                         s_nbatch = nb;
-                        if (nb == 0 || s_A + nb > kMaxActive) s_fail = 2;
+                        if (s_A + nb > kMaxActive || (nb == 0 && s_apos >= s_nact)) s_fail = 2;
                     }
                     __syncthreads();
                     if (s_fail) break;
                     const uint32_t nb = s_nbatch, abase = s_A;
                     for (uint32_t i = tid; i < nb; i += T) {
-                        uint32_t v = s_batch[i];
-                        atomicExch(&vstate[v], 1u | ((abase + i) << 2));
-                        actv[abase + i] = v;
-                        for (uint32_t q = __ldcg(&inc_off[v]); q < __ldcg(&inc_off[v + 1]); q++) {
-                            uint32_t k = __ldcg(&inc_list[q]);
-                            if (__ldcg(&eqdone[k])) continue;
-                            uint32_t old = atomicSub(&eqst[k], 1u);
-                            atomicXor(&eqst[k], v << 2);
-                            uint32_t c = (old & 3u) - 1u;
+                        const uint32_t u = s_batch[i];
+                        vst[u] = 1u | ((abase + i) << 2);
+                        actv[abase + i] = u;
+                        const uint32_t q1 = __ldcg(&inc_off[u + 1]);
+                        for (uint32_t q = __ldcg(&inc_off[u]); q < q1; q++) {
+                            const uint32_t k = __ldcg(&inc_list[q]);
+                            if (est[k] & 4u) continue;
+                            const uint32_t old = atomicSub(&est[k], 1u);
+                            atomicXor(&est[k], u << 3);
+                            const uint32_t c = (old & 3u) - 1u;
                             if (c == 1u) {
                                 G[atomicAdd(&s_cnt[fi ^ 1], 1u)] = k;
                             } else if (c == 0u) {
-                                eqdone[k] = 1;
+                                atomicOr(&est[k], 4u);
                                 dense[atomicAdd(&s_D, 1u)] = k;
                                 atomicSub(&s_rem, 1u);
                             }
@@ -331,34 +363,35 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                     if (tid == 0) s_A += nb;
                 } else {
                     const uint32_t* F = fr[fi];
-                    const uint32_t lo = __ldcg(&soff[s_r]);  // solves of earlier rounds; s_S moves below
+                    const uint32_t lo = s_lo;  // solves of earlier rounds; s_S moves below
                     for (uint32_t i = tid; i < nF; i += T) {
-                        uint32_t j = __ldcg(&F[i]);
-                        if (__ldcg(&eqdone[j])) continue;
-                        uint32_t w = __ldcg(&eqst[j]);
-                        if ((w & 3u) != 1u) continue;
-                        uint32_t x = w >> 2;
-                        if (atomicCAS(&vstate[x], 0u, 3u) != 0u) continue;
-                        uint32_t si = atomicAdd(&s_S, 1u);
-                        atomicExch(&vstate[x], 2u | (si << 2));
+                        const uint32_t j = __ldcg(&F[i]);
+                        const uint32_t w = est[j];
+                        if ((w & 4u) || (w & 3u) != 1u) continue;
+                        const uint32_t x = w >> 3;
+                        if (atomicCAS(&vst[x], 0u, 3u) != 0u) continue;
+                        const uint32_t si = atomicAdd(&s_S, 1u);
+                        vst[x] = 2u | (si << 2);
                         solves[si] = (j << 16) | x;
-                        eqdone[j] = 1;
+                        atomicOr(&est[j], 4u);
                         atomicSub(&s_rem, 1u);
                     }
                     __syncthreads();
                     const uint32_t hi = s_S;
                     for (uint32_t si = lo + tid; si < hi; si += T) {
-                        uint32_t j = __ldcg(&solves[si]) >> 16, x = __ldcg(&solves[si]) & 0xFFFFu;
-                        for (uint32_t q = __ldcg(&inc_off[x]); q < __ldcg(&inc_off[x + 1]); q++) {
-                            uint32_t k = __ldcg(&inc_list[q]);
-                            if (k == j || __ldcg(&eqdone[k])) continue;
-                            uint32_t old = atomicSub(&eqst[k], 1u);
-                            atomicXor(&eqst[k], x << 2);
-                            uint32_t c = (old & 3u) - 1u;
+                        const uint32_t sv = __ldcg(&solves[si]);
+                        const uint32_t j = sv >> 16, x = sv & 0xFFFFu;
+                        const uint32_t q1 = __ldcg(&inc_off[x + 1]);
+                        for (uint32_t q = __ldcg(&inc_off[x]); q < q1; q++) {
+                            const uint32_t k = __ldcg(&inc_list[q]);
+                            if (k == j || (est[k] & 4u)) continue;
+                            const uint32_t old = atomicSub(&est[k], 1u);
+                            atomicXor(&est[k], x << 3);
+                            const uint32_t c = (old & 3u) - 1u;
                             if (c == 1u) {
                                 G[atomicAdd(&s_cnt[fi ^ 1], 1u)] = k;
                             } else if (c == 0u) {
-                                eqdone[k] = 1;
+                                atomicOr(&est[k], 4u);
                                 dense[atomicAdd(&s_D, 1u)] = k;
                                 atomicSub(&s_rem, 1u);
                             }
@@ -369,6 +402,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 if (tid == 0) {
                     s_r++;
                     soff[s_r] = s_S;
+                    s_lo = s_S;
                     s_cnt[fi] = 0;
                 }
                 fi ^= 1;
@@ -382,6 +416,10 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 __syncthreads();
                 continue;
             }
+            // the affine rows and the dense system need shared memory: states go back to the slab
+            if (in_smem)
+                for (uint32_t v = tid; v < V; v += T) vstate[v] = vst[v];
+            __syncthreads();
             const uint32_t A = s_A, S = s_S, D = s_D, R = s_r;
             const uint32_t AW = (A + 31) / 32;
             const uint32_t RS = AW | 1u;  // odd row stride: conflict-free shared-memory rows
