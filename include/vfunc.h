@@ -110,6 +110,19 @@ vf_status vf_build(const void *keys, const uint64_t *offsets, const void *values
 vf_status vf_query(const vf_struct *s, const void *keys, const uint64_t *offsets, uint64_t m,
                    void *out, void *stream);
 
+/* Queries against many resident structures in one launch (the serving
+ * pattern): request i answers m 64-bit keys against structure s exactly as
+ * vf_query would. keys and out must be device memory; the descriptor table is
+ * copied before the call returns, the launch is asynchronous on `stream`. */
+typedef struct {
+    const vf_struct *s;
+    const uint64_t *keys;
+    uint64_t m;
+    void *out;               /* function: value type of b; filter: uint8 0/1 */
+} vf_query_req;
+
+vf_status vf_query_batch(const vf_query_req *reqs, uint32_t count, void *stream);
+
 vf_status vf_get_info(const vf_struct *s, vf_info *info);
 
 /* Parameter planning without building: regime and shard bits for n keys

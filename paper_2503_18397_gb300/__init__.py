@@ -33,6 +33,8 @@ from ._binding import (  # noqa: F401
     vf_params_default,
     vf_plan,
     vf_query,
+    vf_query_batch,
+    VfQueryReq,
     vf_signatures,
     vf_timing_enable,
     vf_timing_read,

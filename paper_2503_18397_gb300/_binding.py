@@ -70,6 +70,10 @@ class VfBatchOpts(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class VfQueryReq(C.Structure):
+    _fields_ = [("s", C.c_void_p), ("keys", C.c_void_p), ("m", C.c_uint64), ("out", C.c_void_p)]
+
+
 EXPORTS = ["vf_params_default", "vf_build", "vf_query", "vf_get_info", "vf_plan", "vf_data", "vf_export",
            "vf_signatures", "vf_free", "vf_last_error"]
 
@@ -103,6 +107,8 @@ def lib():
                                     C.POINTER(VfBatchOpts), C.POINTER(C.c_double)]
         for name in ("vf_batch_opts_default", "vf_build_batch", "vf_tune_batch"):
             getattr(L, name).restype = C.c_int
+        L.vf_query_batch.argtypes = [C.POINTER(VfQueryReq), C.c_uint32, vp]
+        L.vf_query_batch.restype = C.c_int
         L.vf_timing_enable.argtypes = [i32]
         L.vf_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(u64)]
         L.vf_last_error.argtypes = []
@@ -221,6 +227,26 @@ def vf_query(s: Structure, keys, offsets=None, out=None, stream=None):
             out = np.empty(m, dtype=dt)
     _check(lib().vf_query(s.handle, _ptr(keys), _ptr(offsets), m, _ptr(out), _stream(stream, keys, out)))
     return out
+
+
+def vf_query_batch(requests, stream=None):
+    """requests: sequence of (Structure, keys (CUDA u64 tensor), out (CUDA tensor or None)).
+    Returns the outputs (allocated when None). One launch for all requests."""
+    arr = (VfQueryReq * max(len(requests), 1))()
+    outs = []
+    for i, (s, keys, out) in enumerate(requests):
+        if out is None:
+            dt = _out_dtype(vf_get_info(s))
+            tdt = {np.uint8: torch.uint8, np.uint16: torch.uint16, np.uint32: torch.uint32}[dt]
+            out = torch.empty(len(keys), dtype=tdt, device=keys.device)
+        outs.append(out)
+        arr[i].s = s.handle
+        arr[i].keys = _ptr(keys)
+        arr[i].m = len(keys)
+        arr[i].out = _ptr(out)
+    bufs = [r[1] for r in requests]
+    _check(lib().vf_query_batch(arr, len(requests), _stream(stream, *bufs)))
+    return outs
 
 
 def vf_get_info(s: Structure) -> VfInfo:

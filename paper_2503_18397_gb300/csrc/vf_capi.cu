@@ -851,6 +851,40 @@ vf_status vf_query(const vf_struct* s, const void* keys, const uint64_t* offsets
     return VF_OK;
 }
 
+vf_status vf_query_batch(const vf_query_req* reqs, uint32_t count, void* stream) {
+    if (count > 0 && !reqs) return fail(VF_EINVAL, "vf_query_batch: NULL requests");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<vf::QueryReq> d;
+    d.reserve(count);
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        const vf_query_req& r = reqs[i];
+        if (!r.s) return fail(VF_EINVAL, "vf_query_batch: NULL structure");
+        if (r.m == 0) continue;
+        if (!on_device(r.keys) || !on_device(r.out))
+            return fail(VF_EINVAL, "vf_query_batch: keys and outputs must be device memory");
+        vf::QueryReq q;
+        std::memset(&q, 0, sizeof q);
+        q.g = r.s->geom;
+        q.data = r.s->data;
+        q.keys = r.keys;
+        q.out = r.out;
+        q.key_off = total;
+        q.m = r.m;
+        total += r.m;
+        d.push_back(q);
+    }
+    if (d.empty()) return VF_OK;
+    DevBuf db;
+    vf_status rs = h2d(db, d, st);
+    if (rs != VF_OK) return rs;
+    {
+        PhaseTimer t(kPhQuery, st);
+        VF_CK(vf::launch_query_batch(db.as<vf::QueryReq>(), uint32_t(d.size()), total, st));
+    }
+    return VF_OK;
+}
+
 vf_status vf_get_info(const vf_struct* s, vf_info* info) {
     if (!s || !info) return fail(VF_EINVAL, "vf_get_info: NULL argument");
     *info = s->info;

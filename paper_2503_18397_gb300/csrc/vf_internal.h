@@ -143,6 +143,17 @@ cudaError_t launch_batch_hist(const BatchItem* items, const uint64_t* key_off, u
 cudaError_t launch_batch_scatter(const BatchItem* items, const uint64_t* key_off, uint32_t count, uint64_t total,
                                  unsigned long long* cursor, uint64_t* loc, uint32_t* val, cudaStream_t st);
 
+// One request of a cross-structure query batch (device descriptor).
+struct QueryReq {
+    Geom g;
+    const uint8_t* data;
+    const uint64_t* keys;
+    void* out;
+    uint64_t key_off;
+    uint64_t m;
+};
+cudaError_t launch_query_batch(const QueryReq* reqs, uint32_t count, uint64_t total, cudaStream_t st);
+
 cudaError_t launch_query(int key_kind, const void* keys, const uint64_t* offs, uint64_t m, const Geom& g,
                          const uint8_t* data, void* out, cudaStream_t st);
 

@@ -94,6 +94,53 @@ static void launch_w(bool bytes, const void* keys, const uint64_t* offs, uint64_
     }
 }
 
+// ------------------------------------------------------- cross-structure batch
+
+constexpr int kReqCache = 4096;
+
+// Requests against many resident structures in one launch: request r owns
+// keys [key_off, key_off + m) of the launch's key space. Neighbouring keys of a
+// warp mostly share a request, so descriptor reads are broadcasts.
+__global__ void __launch_bounds__(kQThreads) k_query_batch(const QueryReq* __restrict__ reqs, uint32_t count,
+                                                           uint64_t total) {
+    __shared__ uint64_t s_off[kReqCache];
+    const bool cached = count <= kReqCache;
+    if (cached)
+        for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) s_off[i] = reqs[i].key_off;
+    __syncthreads();
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t g = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; g < total; g += stride) {
+        uint32_t lo = 0, hi = count;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            const uint64_t o = cached ? s_off[mid] : reqs[mid].key_off;
+            if (o <= g) lo = mid; else hi = mid;
+        }
+        const QueryReq& r = reqs[lo];
+        const uint64_t i = g - r.key_off;
+        const Sig s = sig_u64(__ldg(r.keys + i), r.g.kh, r.g.kl);
+        const uint64_t base = shard_of(s, r.g.h) * r.g.cells;
+        const uint64_t local = local_of(s, r.g.h);
+        uint64_t v[3];
+        edge_of(r.g, local, v);
+        const uint32_t x = cell_get_nc(r.data, r.g.b, base + v[0]) ^ cell_get_nc(r.data, r.g.b, base + v[1]) ^
+                           cell_get_nc(r.data, r.g.b, base + v[2]);
+        if (r.g.kind == 1) static_cast<uint8_t*>(r.out)[i] = uint8_t(x == fingerprint(local, r.g.b));
+        else if (r.g.b <= 8) static_cast<uint8_t*>(r.out)[i] = uint8_t(x);
+        else if (r.g.b <= 16) static_cast<uint16_t*>(r.out)[i] = uint16_t(x);
+        else static_cast<uint32_t*>(r.out)[i] = x;
+    }
+}
+
+cudaError_t launch_query_batch(const QueryReq* reqs, uint32_t count, uint64_t total, cudaStream_t st) {
+    if (total == 0 || count == 0) return cudaSuccess;
+    uint64_t blocks = (total + kQThreads - 1) / kQThreads;
+    const uint64_t cap = uint64_t(num_sms()) * 16;
+    if (blocks > cap) blocks = cap;
+    k_query_batch<<<unsigned(blocks < 1 ? 1 : blocks), kQThreads, 0, st>>>(reqs, count, total);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_query(int key_kind, const void* keys, const uint64_t* offs, uint64_t m, const Geom& g,
                          const uint8_t* data, void* out, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
