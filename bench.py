@@ -45,6 +45,10 @@ WORKLOADS = {
     "c4": ("mixed", 0, 4096, "u64",
            "4096 independent VFunc/VFilter structures, sizes log-uniform in 1e3..1e6 uniform 64-bit keys, "
            "b in {1,8,16,32}, kind 50/50; batched persistent graph-captured build vs one vf_build per structure"),
+    "c5": ("serve", 8, 5_000_000_000, "u64",
+           "serving: Poisson arrivals of builds (log-uniform 1e4..1e8 keys, b in {8,16}) and query batches "
+           "(log-uniform 1e3..1e7 keys, half members) under a device-memory budget, plus one VFilter of 5e9 "
+           "uniform 64-bit keys (b=8) generated on the device in chunks and built by shard group"),
     "c3": ("func", 16, 10_000_000, "bytes",
            "VFunc n=1e7 byte strings (length 8..64), 16-bit values, LGE regime shards; "
            "query 1e7 members + 1e7 disjoint strings", "lge"),
@@ -485,6 +489,111 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(args):
+    """Scale (one 5e9-key VFilter built by shard group) and serving (Poisson mix)."""
+    import torch
+
+    import paper_2503_18397_gb300 as vf
+    from paper_2503_18397_gb300 import build as vbuild
+    from paper_2503_18397_gb300 import serve, synth
+
+    torch.cuda.set_device(0)
+    vbuild.build()
+    vf.lib()
+    out = {"metric": METRIC, "unit": "ns/key", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": WORKLOADS["c5"][4]}}
+    # ---- scale: keys generated on the device in chunks
+    n = args.n or 5_000_000_000
+    keys = torch.empty(n, dtype=torch.int64, device="cuda")
+    chunk = 1 << 28
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        keys[c0:c1] = synth.u64_keys_torch(c0, c1 - c0, 0xC5)
+    torch.cuda.synchronize()
+    p = vf.vf_params_default(kind=vf.FILTER, b=8, seed=3)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    clocks = Clocks(0)
+    clocks.start()
+    vf.vf_timing_read()
+    vf.vf_timing_enable(True)
+    ev[0].record(stream)
+    s = vf.vf_build(keys, None, params=p, stream=stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    info = s.info
+    mq = min(n, 100_000_000)
+    member = keys[:: max(1, n // mq)][:mq].contiguous()
+    other = synth.u64_keys_torch(n, mq, 0xC5)
+    ev[2].record(stream)
+    o1 = s.query(member, stream=stream)
+    o2 = s.query(other, stream=stream)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    vf.vf_timing_enable(False)
+    phases = vf.vf_timing_read()
+    clk = clocks.stop()
+    b_ms, q_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    out["value"] = round(b_ms * 1e6 / n, 4)
+    out["ms_per_step"] = round(b_ms + q_ms, 3)
+    out["scale"] = {"n": n, "build_ms": round(b_ms, 3), "shards": int(info.shards), "cells_per_shard": int(info.cells),
+                    "lg_seg": int(info.lg_seg), "c": info.c, "space_overhead": round(info.total_cells / n - 1, 4),
+                    "retries": int(info.retries), "peel_rounds": int(info.rounds),
+                    "query_gqps": round(2 * mq / (q_ms * 1e-3) / 1e9, 3),
+                    "members_ok": bool(o1.bool().all().item()), "fpr": float(o2.float().mean().item()),
+                    "phases": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in phases.items() if v[1]}}
+    out["gpu_launches"] = int(sum(v[1] for v in phases.values()))
+    out["clocks"] = clk
+    s.free()
+    del keys, member, other, o1, o2
+    torch.cuda.empty_cache()
+    # ---- serving: Poisson arrivals under a memory budget
+    rng = np.random.default_rng(0x5E)
+    nb, nq = 24, 96
+    sizes = synth.log_uniform_sizes(nb, 1e4, 1e8, 0x5E)
+    qsizes = synth.log_uniform_sizes(nq, 1e3, 1e7, 0x5F)
+    work = float(sum(sizes)) * 4e-9 + nb * 5e-3 + float(sum(qsizes)) * 1e-9 + nq * 1e-3
+    rate = (nb + nq) / (work / 0.7)  # about 70% of the estimated capacity
+    t, reqs, bkeys, rid, qi = 0.0, [], {}, 0, 0
+    for i in range(nb):
+        t += rng.exponential(1 / rate)
+        nn = int(sizes[i])
+        b = int(rng.choice([8, 16]))
+        kind = int(rng.integers(0, 2))
+        k = synth.u64_keys(i * 10**9, nn, 0x5E)
+        v = synth.values(nn, b, 0x5E + i) if kind == 0 else None
+        bkeys[i] = k
+        kt = torch.from_numpy(k.view(np.int64)).pin_memory()
+        vt = None if v is None else torch.from_numpy(v.view({1: np.uint8, 2: np.int16}[v.dtype.itemsize])).pin_memory()
+        reqs.append(serve.BuildRequest(rid, t, i, kt, vt, kind, b, 77 + i))
+        rid += 1
+        for _ in range(nq // nb):
+            t += rng.exponential(1 / rate)
+            sid = int(rng.integers(0, i + 1))
+            m = int(qsizes[qi])
+            qi += 1
+            kk = bkeys[sid]
+            q = np.concatenate([kk[rng.integers(0, len(kk), size=m // 2)],
+                                synth.u64_keys(10**15 + rid * 10**7, m - m // 2, 0x5E)])
+            reqs.append(serve.QueryRequest(rid, t, sid, torch.from_numpy(q.view(np.int64)).pin_memory()))
+            rid += 1
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.Server(budget=int(free * 0.25))
+    t0 = time.perf_counter()
+    recs = srv.run(reqs)
+    span = time.perf_counter() - t0
+    srv.close()
+    total_b = int(sum(sizes))
+    total_q = int(sum(qsizes))
+    out["serving"] = {"requests": len(reqs), "builds": serve.percentiles(recs, "build"),
+                      "queries": serve.percentiles(recs, "query"), "span_s": round(span, 3),
+                      "arrival_rate_per_s": round(rate, 2), "budget_gb": round(free * 0.25 / 2**30, 1),
+                      "build_keys": total_b, "query_keys": total_q,
+                      "throughput_keys_per_s": round((total_b + total_q) / span, 1)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,6 +608,8 @@ def main():
         run_reference(args)
     elif args.workload == "c4":
         run_batch(args)
+    elif args.workload == "c5":
+        run_serving(args)
     else:
         run_gpu(args)
 

@@ -97,8 +97,12 @@ void vf_params_default(vf_params *p);
  * (fuse graph, Sec. 4.2), peel (Sec. 4.3), solve 2-cores by lazy Gaussian
  * elimination in the LGE regime (Sec. 4.2), assign in reverse peel order.
  * Waits for completion (the shard sizes and the outcome are read back).
+ * Above 2^30 keys (64-bit keys, fuse regime, up to 2^36) the shards are built
+ * one group of consecutive shards (<= 2^30 keys) at a time, so scratch memory
+ * is bounded by the group, not by n (Sec. 6, shard-at-a-time construction).
  * Errors: VF_EINVAL, VF_ENOMEM, VF_EBUILD, VF_ETIMEOUT, VF_ECUDA, VF_ECAPACITY
- * (a fuse shard above 2^27 keys, or more than 2^32 keys in one call). */
+ * (a fuse shard above 2^27 keys; more than 2^30 keys with byte strings or in
+ * the LGE regime). */
 vf_status vf_build(const void *keys, const uint64_t *offsets, const void *values, uint64_t n,
                    const vf_params *params, void *stream, vf_struct **out);
 

@@ -75,7 +75,8 @@ constexpr int kItems = 4;
 __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict__ keys,
                                                       const Sig* __restrict__ sig_in, const void* __restrict__ values,
                                                       uint64_t n, Geom g, unsigned long long* __restrict__ cursor,
-                                                      uint64_t* __restrict__ loc_out, uint32_t* __restrict__ val_out) {
+                                                      uint64_t* __restrict__ loc_out, uint32_t* __restrict__ val_out,
+                                                      uint32_t s_lo, uint32_t s_hi) {
     __shared__ uint32_t cnt[kSmemBinsMax];
     __shared__ unsigned long long base[kSmemBinsMax];
     const uint32_t S = 1u << g.h;
@@ -92,10 +93,13 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict
             sh[k] = 0xFFFFFFFFu;
             if (i < n) {
                 Sig s = sig_in ? sig_in[i] : sig_u64(__ldg(keys + i), g.kh, g.kl);
-                sh[k] = uint32_t(shard_of(s, g.h));
-                loc[k] = local_of(s, g.h);
-                val[k] = has_val ? load_value(values, g.b, i) : 0u;
-                rank[k] = atomicAdd(&cnt[sh[k]], 1u);
+                const uint32_t shard = uint32_t(shard_of(s, g.h));
+                if (shard >= s_lo && shard < s_hi) {  // only the shard group being built
+                    sh[k] = shard;
+                    loc[k] = local_of(s, g.h);
+                    val[k] = has_val ? load_value(values, g.b, i) : 0u;
+                    rank[k] = atomicAdd(&cnt[shard], 1u);
+                }
             }
         }
         __syncthreads();
@@ -120,11 +124,14 @@ __global__ void __launch_bounds__(kThreads) k_scatter_wide(const uint64_t* __res
                                                            const void* __restrict__ values, uint64_t n, Geom g,
                                                            unsigned long long* __restrict__ cursor,
                                                            uint64_t* __restrict__ loc_out,
-                                                           uint32_t* __restrict__ val_out) {
+                                                           uint32_t* __restrict__ val_out, uint32_t s_lo,
+                                                           uint32_t s_hi) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
         Sig s = sig_in ? sig_in[i] : sig_u64(__ldg(keys + i), g.kh, g.kl);
-        uint64_t pos = atomicAdd(&cursor[shard_of(s, g.h)], 1ull);
+        const uint32_t shard = uint32_t(shard_of(s, g.h));
+        if (shard < s_lo || shard >= s_hi) continue;
+        uint64_t pos = atomicAdd(&cursor[shard], 1ull);
         loc_out[pos] = local_of(s, g.h);
         if (values) val_out[pos] = load_value(values, g.b, i);
     }
@@ -218,14 +225,14 @@ cudaError_t launch_hist(int key_kind, const void* keys, const uint64_t* offs, ui
 
 cudaError_t launch_scatter(const uint64_t* keys_u64, const Sig* sig_in, const void* values, uint64_t n,
                            const Geom& g, unsigned long long* cursor, uint64_t* loc_out, uint32_t* val_out,
-                           cudaStream_t st) {
+                           uint32_t s_lo, uint32_t s_hi, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     if ((1u << g.h) <= uint32_t(kSmemBinsMax))
         k_scatter<<<stream_grid(n, kItems), kThreads, 0, st>>>(keys_u64, sig_in, values, n, g, cursor, loc_out,
-                                                               val_out);
+                                                               val_out, s_lo, s_hi);
     else
         k_scatter_wide<<<stream_grid(n), kThreads, 0, st>>>(keys_u64, sig_in, values, n, g, cursor, loc_out,
-                                                            val_out);
+                                                            val_out, s_lo, s_hi);
     return cudaGetLastError();
 }
 

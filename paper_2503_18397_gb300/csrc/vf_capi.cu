@@ -261,7 +261,7 @@ vf_status h2d(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
 // failed: the attempt must be retried), or an error.
 vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
                      const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
-                     uint64_t* rounds_out) {
+                     uint64_t* rounds_out, uint64_t cell_base = 0) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
     DevBuf W, claimed, f0, f1, rec, roff, ctr;
@@ -299,6 +299,7 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.err = c32 + 6;
     a.bar = reinterpret_cast<vf::Bar2*>(c32 + 16);
     a.data = data;
+    a.cell_base = cell_base;
     {
         PhaseTimer t(kPhAccum, st);
         VF_CK(vf::launch_accumulate(loc, n, start, a.S, g, a.W, a.err, st));
@@ -720,7 +721,11 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
     if (!(p.eps > 0.0) || !(p.eta > 0.0 && p.eta < 1.0) || p.max_retries < 0 || p.lge_target == 0 ||
         p.lge_max_shard < 2)
         return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes");
-    if (n > (uint64_t(1) << 30)) return fail(VF_ECAPACITY, "at most 2^30 keys per vf_build call");
+    // More than 2^30 keys: only 64-bit keys in the fuse regime, built one shard
+    // group (<= 2^30 keys) at a time.
+    const bool big = n > (uint64_t(1) << 30);
+    if (big && (p.key_kind != VF_KEYS_U64 || p.mode == VF_MODE_LGE || n < p.lge_threshold || n > (uint64_t(1) << 36)))
+        return fail(VF_ECAPACITY, "above 2^30 keys: 64-bit keys, fuse regime, at most 2^36 keys");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     VF_CK(cudaGetDevice(&dev));
@@ -741,8 +746,6 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
 
     DevBuf hist, sigs, loc, val, startb, cursor, data;
     if (p.key_kind == VF_KEYS_BYTES) VF_CK(sigs.alloc(n * sizeof(vf::Sig), st));
-    VF_CK(loc.alloc(n * 8, st));
-    if (p.kind == VF_FUNC) VF_CK(val.alloc(n * 4, st));
 
     vf_status last = VF_EBUILD;
     for (int attempt = 0; attempt <= p.max_retries; attempt++) {
@@ -780,28 +783,71 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
             return fail(VF_ECAPACITY, "fuse shard above 2^27 keys");
         if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard)
             return fail(VF_ECAPACITY, "LGE shard above lge_max_shard");
-        if (in.total_cells >= (uint64_t(1) << 32)) return fail(VF_ECAPACITY, "more than 2^32 cells");
         const vf::Geom g = make_geom(in);
-        std::vector<unsigned long long> start(in.shards + 1, 0);
-        for (uint64_t s = 0; s < in.shards; s++) start[s + 1] = start[s] + counts[s];
-        rs = h2d(startb, start, st);
-        if (rs != VF_OK) return rs;
-        VF_CK(cursor.alloc(in.shards * 8, st));
-        VF_CK(cudaMemcpyAsync(cursor.p, startb.p, in.shards * 8, cudaMemcpyDeviceToDevice, st));
+        // shard groups: consecutive shards with at most 2^30 keys and 2^32 cells each
+        std::vector<uint32_t> group{0};
         {
-            PhaseTimer t(kPhScatter, st);
-            VF_CK(vf::launch_scatter(static_cast<const uint64_t*>(in_keys.keys), sigs.as<vf::Sig>(), vals_dev, n, g,
-                                     cursor.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(), st));
+            uint64_t keys_in = 0, cells_in = 0;
+            for (uint32_t s = 0; s < in.shards; s++) {
+                if (s > group.back() && (keys_in + counts[s] > (uint64_t(1) << 30) ||
+                                         cells_in + in.cells >= (uint64_t(1) << 32))) {
+                    group.push_back(s);
+                    keys_in = cells_in = 0;
+                }
+                keys_in += counts[s];
+                cells_in += in.cells;
+            }
+            group.push_back(uint32_t(in.shards));
         }
+        if (group.size() > 2 && in.regime != VF_REGIME_FUSE)
+            return fail(VF_ECAPACITY, "more than 2^30 keys or 2^32 cells in the LGE regime");
+        uint64_t group_max = 0;
+        for (size_t k = 0; k + 1 < group.size(); k++) {
+            uint64_t sum = 0;
+            for (uint32_t s = group[k]; s < group[k + 1]; s++) sum += counts[s];
+            group_max = std::max(group_max, sum);
+        }
+        if (loc.bytes < std::max<uint64_t>(group_max, 1) * 8) VF_CK(loc.alloc(std::max<uint64_t>(group_max, 1) * 8, st));
+        if (p.kind == VF_FUNC && val.bytes < std::max<uint64_t>(group_max, 1) * 4)
+            VF_CK(val.alloc(std::max<uint64_t>(group_max, 1) * 4, st));
         VF_CK(data.alloc(in.data_bytes + 16, st));
         VF_CK(cudaMemsetAsync(data.p, 0, in.data_bytes + 16, st));
+        VF_CK(cursor.alloc(in.shards * 8, st));
         uint64_t peeled = 0, core = 0, rounds = 0;
-        if (in.regime == VF_REGIME_FUSE)
-            rs = solve_fuse(in, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
-                            startb.as<unsigned long long>(), data.as<uint8_t>(), st, &peeled, &rounds);
-        else
-            rs = solve_lge(in, start, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
-                           data.as<uint8_t>(), st, &peeled, &core);
+        rs = VF_OK;
+        std::vector<unsigned long long> start;
+        for (size_t k = 0; k + 1 < group.size() && rs == VF_OK; k++) {
+            const uint32_t g0s = group[k], g1s = group[k + 1];
+            vf_info gi = in;
+            gi.shards = g1s - g0s;
+            start.assign(gi.shards + 1, 0);
+            for (uint32_t s = g0s; s < g1s; s++) start[s - g0s + 1] = start[s - g0s] + counts[s];
+            gi.n_eff = start[gi.shards];
+            gi.total_cells = gi.shards * in.cells;
+            // cursors of the group's shards start at the group-local shard starts
+            std::vector<unsigned long long> cur(in.shards, 0);
+            for (uint32_t s = g0s; s < g1s; s++) cur[s] = start[s - g0s];
+            VF_CK(cudaMemcpyAsync(cursor.p, cur.data(), in.shards * 8, cudaMemcpyHostToDevice, st));
+            rs = h2d(startb, start, st);
+            if (rs != VF_OK) return rs;
+            {
+                PhaseTimer t(kPhScatter, st);
+                VF_CK(vf::launch_scatter(static_cast<const uint64_t*>(in_keys.keys), sigs.as<vf::Sig>(), vals_dev, n,
+                                         g, cursor.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(),
+                                         g0s, g1s, st));
+            }
+            uint64_t pe = 0, co = 0, ro = 0;
+            if (in.regime == VF_REGIME_FUSE)
+                rs = solve_fuse(gi, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
+                                startb.as<unsigned long long>(), data.as<uint8_t>(), st, &pe, &ro,
+                                uint64_t(g0s) * in.cells);
+            else
+                rs = solve_lge(in, start, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
+                               data.as<uint8_t>(), st, &pe, &co);
+            peeled += pe;
+            core += co;
+            rounds += ro;
+        }
         in.peeled = peeled;
         in.core = in.regime == VF_REGIME_FUSE ? 0 : core;
         in.rounds = rounds;

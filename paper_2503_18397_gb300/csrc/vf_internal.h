@@ -38,14 +38,16 @@ struct FuseSolveArgs {
     Bar2* bar;
     uint32_t* err;
     uint8_t* data;                    // assignment target
+    uint64_t cell_base;               // cell of the first vertex (shard groups)
     uint32_t rounds;                  // assignment: rounds recorded by the peel
 };
 
 cudaError_t launch_hist(int key_kind, const void* keys, const uint64_t* offs, uint64_t n, const Geom& g,
                         uint32_t* hist, Sig* sig_out, cudaStream_t st);
+// Buckets the keys whose shard lies in [s_lo, s_hi) (a shard group).
 cudaError_t launch_scatter(const uint64_t* keys_u64, const Sig* sig_in, const void* values, uint64_t n,
                            const Geom& g, unsigned long long* cursor, uint64_t* loc_out, uint32_t* val_out,
-                           cudaStream_t st);
+                           uint32_t s_lo, uint32_t s_hi, cudaStream_t st);
 cudaError_t launch_sigs(int key_kind, const void* keys, const uint64_t* offs, uint64_t n, uint64_t kh,
                         uint64_t kl, Sig* out, cudaStream_t st);
 cudaError_t launch_accumulate(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,

@@ -216,8 +216,9 @@ __global__ void __launch_bounds__(kPT, 1) k_assign2(FuseSolveArgs a) {
         const uint32_t lo = __ldg(a.round_off + r), hi = __ldg(a.round_off + r + 1);
         for (uint64_t i = lo + tid; i < hi; i += nthreads) {
             const uint4 rec = __ldg(a.rec + i);
-            const uint32_t x = rec.w ^ cell_get_cg(a.data, b, rec.y) ^ cell_get_cg(a.data, b, rec.z);
-            cell_put_zero(a.data, b, rec.x, x);
+            const uint32_t x =
+                rec.w ^ cell_get_cg(a.data, b, a.cell_base + rec.y) ^ cell_get_cg(a.data, b, a.cell_base + rec.z);
+            cell_put_zero(a.data, b, a.cell_base + rec.x, x);
         }
         if (r > 0 && !bar2(a.bar, nblocks, a.err, [] {})) return;
     }
