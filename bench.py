@@ -185,7 +185,13 @@ def run_gpu(args):
     kd, vd, od, xd, xo = (to_dev(a, torch) for a in (keys, vals, offs, other, ooffs))
     stream = torch.cuda.current_stream()
 
+    step_no = [0]
+
     def step(timing):
+        # every step builds with its own seed, so retries (a ~5% event at the
+        # paper's eta) show up in the average as often as they occur
+        p.seed = 1 + rank + 1000 * step_no[0]
+        step_no[0] += 1
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         s = vf.vf_build(kd, vd, offsets=od, params=p, stream=stream)
