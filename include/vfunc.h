@@ -49,6 +49,13 @@ enum { VF_FUNC = 0, VF_FILTER = 1 };
 enum { VF_KEYS_U64 = 0, VF_KEYS_BYTES = 1 };
 enum { VF_MODE_AUTO = 0, VF_MODE_FUSE = 1, VF_MODE_LGE = 2 };
 enum { VF_REGIME_FUSE = 1, VF_REGIME_LGE = 2 };
+/* Fuse-regime solver. Both peel the same hypergraph (Sec. 4.3) and give the
+ * same query results; they differ in how the work is scheduled on the GPU.
+ * VF_SOLVER_FLOW: asynchronous worklist peeling that records peeled edges in
+ * an order whose reverse is a valid assignment order, then a dataflow
+ * assignment. VF_SOLVER_ROUNDS: peeling in synchronous rounds with a grid
+ * barrier, assignment in reverse rounds. */
+enum { VF_SOLVER_FLOW = 0, VF_SOLVER_ROUNDS = 1 };
 
 /* Build parameters. vf_params_default() fills the paper's defaults. */
 typedef struct {
@@ -66,6 +73,7 @@ typedef struct {
     uint64_t lge_target;     /* LGE regime: shard bits chosen so mean shard <= this (16384) */
     uint64_t lge_max_shard;  /* LGE regime: shard bits grow until no shard exceeds this
                                 (24576, the per-CTA solver's capacity) */
+    int fuse_solver;         /* VF_SOLVER_FLOW (default) or VF_SOLVER_ROUNDS */
 } vf_params;
 
 /* Geometry and outcome of a built structure. */
@@ -86,7 +94,8 @@ typedef struct {
     uint64_t seed;           /* seed of the successful attempt */
     int retries;             /* failed attempts before it */
     uint64_t peeled, core;   /* edges peeled / edges solved by elimination (last attempt) */
-    uint64_t rounds;         /* fuse regime: synchronous peeling rounds (last attempt) */
+    uint64_t rounds;         /* fuse regime, VF_SOLVER_ROUNDS: synchronous peeling rounds of
+                                the last attempt, summed over shard groups; 0 otherwise */
 } vf_info;
 
 void vf_params_default(vf_params *p);

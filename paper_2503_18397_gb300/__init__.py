@@ -14,6 +14,8 @@ from ._binding import (  # noqa: F401
     MODE_LGE,
     REGIME_FUSE,
     REGIME_LGE,
+    SOLVER_FLOW,
+    SOLVER_ROUNDS,
     VFError,
     VfInfo,
     VfParams,

@@ -25,6 +25,7 @@ FUNC, FILTER = 0, 1
 KEYS_U64, KEYS_BYTES = 0, 1
 MODE_AUTO, MODE_FUSE, MODE_LGE = 0, 1, 2
 REGIME_FUSE, REGIME_LGE = 1, 2
+SOLVER_FLOW, SOLVER_ROUNDS = 0, 1
 STATUS = {0: "VF_OK", 1: "VF_EINVAL", 2: "VF_ENOMEM", 3: "VF_EBUILD", 4: "VF_EDUP", 5: "VF_ETIMEOUT",
           6: "VF_ECUDA", 7: "VF_ECAPACITY"}
 
@@ -40,6 +41,7 @@ class VfParams(C.Structure):
         ("kind", C.c_int), ("b", C.c_int), ("key_kind", C.c_int), ("mode", C.c_int),
         ("max_retries", C.c_int), ("seed", C.c_uint64), ("eps", C.c_double), ("eta", C.c_double),
         ("lge_threshold", C.c_uint64), ("lge_target", C.c_uint64), ("lge_max_shard", C.c_uint64),
+        ("fuse_solver", C.c_int),
     ]
 
 

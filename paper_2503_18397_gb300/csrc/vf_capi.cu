@@ -257,11 +257,11 @@ vf_status h2d(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
     return VF_OK;
 }
 
-// One attempt of the fuse-regime solver. Returns VF_OK, VF_EBUILD (peel
-// failed: the attempt must be retried), or an error.
-vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
-                     const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
-                     uint64_t* rounds_out, uint64_t cell_base = 0) {
+// One attempt of the round-synchronous fuse-regime solver. Returns VF_OK,
+// VF_EBUILD (peel failed: the attempt must be retried), or an error.
+vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
+                       const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
+                       uint64_t* rounds_out, uint64_t cell_base) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
     DevBuf W, claimed, f0, f1, rec, roff, ctr;
@@ -328,6 +328,93 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     VF_CK(cudaStreamSynchronize(st));
     if (e2 & vf::kErrTimeout) return fail(VF_ETIMEOUT, "assignment barrier timed out");
     return VF_OK;
+}
+
+// One attempt of the asynchronous fuse-regime solver. Returns VF_OK, VF_EBUILD
+// (peel failed: retry), or an error.
+vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
+                     const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
+                     uint64_t cell_base) {
+    const uint64_t n = in.n_eff;
+    const uint64_t V = in.total_cells;
+    DevBuf W, queue, claimed, pv, rec, ctr;
+    VF_CK(W.alloc(V * 4, st));
+    VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
+    VF_CK(queue.alloc(V * 8, st));
+    VF_CK(cudaMemsetAsync(queue.p, 0xFF, V * 8, st));
+    const uint64_t ewords = std::max<uint64_t>((n + 31) / 32, 1), vwords = std::max<uint64_t>((V + 31) / 32, 1);
+    VF_CK(claimed.alloc(ewords * 4, st));
+    VF_CK(cudaMemsetAsync(claimed.p, 0, ewords * 4, st));
+    VF_CK(pv.alloc(vwords * 4, st));
+    VF_CK(cudaMemsetAsync(pv.p, 0, vwords * 4, st));
+    VF_CK(rec.alloc(std::max<uint64_t>(V, 1) * 16, st));  // one slot per item, at most one item per vertex
+    VF_CK(ctr.alloc(vf::kFlowWords * 4, st));
+    VF_CK(cudaMemsetAsync(ctr.p, 0, vf::kFlowWords * 4, st));
+    vf::FlowArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.loc = loc;
+    a.val = val;
+    a.start = start;
+    a.S = uint32_t(in.shards);
+    a.g = g;
+    a.W = W.as<uint32_t>();
+    a.queue = queue.as<unsigned long long>();
+    a.fv = a.queue;
+    a.queue_cap = V;
+    a.claimed = claimed.as<uint32_t>();
+    a.pv = pv.as<uint32_t>();
+    a.rec = rec.as<uint4>();
+    a.ctr = ctr.as<uint32_t>();
+    a.err = a.ctr + vf::kFlowErr;
+    a.data = data;
+    a.cell_base = cell_base;
+    {
+        PhaseTimer t(kPhAccum, st);
+        VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, st));
+    }
+    {
+        PhaseTimer t(kPhPeel, st);
+        VF_CK(vf::launch_flow_peel(a, st));
+    }
+    std::vector<uint32_t> h(vf::kFlowWords);
+    VF_CK(cudaMemcpyAsync(h.data(), a.ctr, vf::kFlowWords * 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaStreamSynchronize(st));
+    const uint32_t count = h[vf::kFlowPeeled], err = h[vf::kFlowErr];
+    uint64_t slots = 0;
+    std::memcpy(&slots, &h[vf::kFlowRecs], 8);
+    *peeled = count;
+    if (err & vf::kErrTimeout) return fail(VF_ETIMEOUT, "asynchronous peeling wait timed out");
+    if (err & (vf::kErrDegOverflow | vf::kErrFrontier)) return VF_EBUILD;
+    if (count != n) return VF_EBUILD;  // non-empty 2-core
+    if (slots > V) return fail(VF_ECUDA, "asynchronous peeling took more record slots than items");
+    a.nrec = slots;
+    {
+        PhaseTimer t(kPhAssign, st);
+        VF_CK(vf::launch_flow_assign(a, st));
+    }
+    uint32_t e2 = 0;
+    VF_CK(cudaMemcpyAsync(&e2, a.err, 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaStreamSynchronize(st));
+    if (e2 & vf::kErrTimeout) return fail(VF_ETIMEOUT, "dataflow assignment wait timed out");
+    return VF_OK;
+}
+
+// One attempt of the fuse-regime solver: the asynchronous solver (default) or
+// the round-synchronous one. Reorders loc / val within each shard.
+vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32_t* val,
+                     const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
+                     uint64_t* rounds_out, int solver, uint64_t cell_base = 0) {
+    // edges of each tile in the order of their first vertex's segment (locality
+    // of the peeling wave); the solvers only see edge indices within a shard
+    {
+        PhaseTimer t(kPhScatter, st);
+        VF_CK(vf::launch_tile_order(loc, val, in.n_eff, start, uint32_t(in.shards), g, st));
+    }
+    if (solver == VF_SOLVER_FLOW) {
+        *rounds_out = 0;
+        return solve_flow(in, g, loc, val, start, data, st, peeled, cell_base);
+    }
+    return solve_rounds(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base);
 }
 
 // Tasks of the LGE solver for the shards of one or more structures, largest
@@ -627,7 +714,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
         uint64_t peeled = 0, rounds = 0;
         rs = solve_fuse(info[j], make_geom(info[j]), loc.as<uint64_t>() + key_off[j],
                         info[j].kind == VF_FUNC ? val.as<uint32_t>() + key_off[j] : nullptr,
-                        dstart.as<unsigned long long>(), data[j], st, &peeled, &rounds);
+                        dstart.as<unsigned long long>(), data[j], st, &peeled, &rounds, common.fuse_solver);
         if (rs == VF_EBUILD) fail_bits[j] |= vf::kErrUnsolvable;
         else if (rs != VF_OK) return free_data(), rs;
         info[j].peeled = peeled;
@@ -686,6 +773,7 @@ void vf_params_default(vf_params* p) {
     p->lge_threshold = 800000;
     p->lge_target = 16384;
     p->lge_max_shard = 24576;
+    p->fuse_solver = VF_SOLVER_FLOW;
 }
 
 const char* vf_last_error(void) { return g_last_error.c_str(); }
@@ -840,7 +928,7 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
             if (in.regime == VF_REGIME_FUSE)
                 rs = solve_fuse(gi, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
                                 startb.as<unsigned long long>(), data.as<uint8_t>(), st, &pe, &ro,
-                                uint64_t(g0s) * in.cells);
+                                p.fuse_solver, uint64_t(g0s) * in.cells);
             else
                 rs = solve_lge(in, start, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
                                data.as<uint8_t>(), st, &pe, &co);

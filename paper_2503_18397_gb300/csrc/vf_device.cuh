@@ -26,6 +26,7 @@ constexpr uint32_t kErrFrontier = 1u << 2;      // frontier or round buffer over
 constexpr uint32_t kErrCapacity = 1u << 3;      // shard larger than the solver handles
 constexpr uint32_t kErrUnsolvable = 1u << 4;    // a shard's system has no solution
 constexpr uint32_t kErrLgeSize = 1u << 5;       // LGE dense system or coefficient pool too large (retry)
+constexpr uint32_t kErrLevel = 1u << 6;         // asynchronous peel: too many levels (use the round solver)
 
 // Stafford Mix13, the SplitMix64 output function.
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {

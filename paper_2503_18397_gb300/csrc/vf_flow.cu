@@ -1,0 +1,460 @@
+// Asynchronous fuse-regime solver of libvfunc (sm_103a): worklist peeling and
+// dataflow assignment, with no grid-wide barrier between peeling steps.
+//
+// Vertex word (32 bits): bits 0..4 degree, bits 5..31 the SUM modulo 2^27 of
+// the shard-local indices of the incident edges (a shard holds fewer than 2^27
+// edges). It plays the part of the XOR trick of Sec. 4.3: at degree one the sum
+// is the one remaining edge index. Removing an edge is a single fetch-and-add,
+// so a peeling step needs no read-modify-write retry loop.
+//
+// Peeling (the visit of Sec. 4.3 with many stacks at once): a lane follows one
+// chain: after peeling an edge it continues with a vertex that the edge brought
+// to degree one and publishes a second such vertex in a global queue. Idle
+// lanes reserve queue slots and take the item once it is written.
+//
+// Order: every item takes a record slot from one global counter together with
+// its claim, before it removes the edge from the other two vertices. A vertex
+// that an edge f still touches can only be peeled (by some edge g) after f's
+// removal from it, hence after f's slot was taken: g's slot is larger. So the
+// records in decreasing slot order are a reverse peeling order, the order in
+// which assignment must run (each peeled vertex is assigned after the vertices
+// its value depends on). Items whose claim failed leave an empty slot.
+//
+// Assignment is a dataflow in decreasing slot order: once final, a vertex's
+// value word (64 bits, in the queue's memory) holds its value with bit 32 set (vertices no edge was peeled from are
+// final from the start, value 0); an edge waits (bounded) until its two other
+// vertices are final. An edge only waits on edges of larger slots, which were
+// taken before it, so the earliest unfinished edge can always proceed.
+#include <atomic>
+
+#include <cuda/atomic>
+
+#include "vf_internal.h"
+
+namespace vf {
+
+constexpr int kFT = 256;
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr unsigned long long kFinal = 1ull << 32;
+constexpr uint32_t kHole = 0xFFFFFFFFu;     // record of an item whose claim failed
+constexpr uint32_t kIdleLimit = 1u << 23;  // polls of ~1 us: a wait gives up after ~8 s
+constexpr unsigned kNapMax = 256;          // ns, peeling
+constexpr unsigned kAssignNapMax = 256;    // ns, assignment
+
+using dev_atomic32 = cuda::atomic_ref<unsigned int, cuda::thread_scope_device>;
+using dev_atomic64 = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
+
+__device__ __forceinline__ unsigned lane32() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanes_below() { return (1u << lane32()) - 1u; }
+
+__device__ __forceinline__ uint32_t flow_shard_of_edge(const unsigned long long* __restrict__ start, uint32_t S,
+                                                       uint64_t e) {
+    uint32_t lo = 0, hi = S;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(start + mid) <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One slot each for the lanes in `mask` (non-empty), from a 64-bit counter.
+__device__ __forceinline__ unsigned long long reserve64(unsigned long long* ctr, unsigned mask, bool me) {
+    const int lead = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (int(lane32()) == lead) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, lead);
+    return me ? base + __popc(mask & lanes_below()) : 0ull;
+}
+
+__device__ __forceinline__ unsigned long long* ctr64(const FlowArgs& a, uint32_t word) {
+    return reinterpret_cast<unsigned long long*>(a.ctr + word);
+}
+
+// Incidence: degree += 1 and sum += shard-local edge index, per vertex.
+__global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict__ loc, uint64_t n,
+                                                     const unsigned long long* __restrict__ start, uint32_t S, Geom g,
+                                                     uint32_t* __restrict__ W, uint32_t* err) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t e = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; e < n; e += stride) {
+        const uint32_t s = flow_shard_of_edge(start, S, e);
+        const uint32_t inc = 1u + (uint32_t(e - __ldg(start + s)) << 5);
+        uint64_t v[3];
+        edge_of(g, __ldg(loc + e), v);
+        const uint64_t base = uint64_t(s) * g.cells;
+        uint32_t old[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) old[k] = atomicAdd(W + base + v[k], inc);
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            if ((old[k] & 31u) == 31u) atomicOr(err, kErrDegOverflow);
+    }
+}
+
+// Initial items: every vertex of degree one with its edge.
+__global__ void __launch_bounds__(kFT) k_flow_seed(FlowArgs a) {
+    const uint64_t V = uint64_t(a.S) * a.g.cells;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    const uint32_t cells = uint32_t(a.g.cells);
+    for (uint64_t v0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); v0 < V; v0 += stride) {
+        const uint64_t v = v0 + lane32();
+        const uint32_t w = v < V ? a.W[v] : 0u;
+        const bool one = (w & 31u) == 1u;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, one);
+        if (!m) continue;
+        const unsigned long long slot = reserve64(ctr64(a, kFlowTail), m, one);
+        if (one) {
+            const uint32_t s = uint32_t(v / cells);
+            a.queue[slot] = (v << 32) | (__ldg(a.start + s) + (w >> 5));
+        }
+    }
+}
+
+// Worklist peeling; one chain per lane at a time. An iteration has two memory
+// phases per warp: first every request that does not depend on this
+// iteration's results (queue slots for idle lanes, polls of reserved slots,
+// the item's signature, its claim, its record slot, the queue slot of an item
+// produced in the previous iteration), then the removals of the claimed edges.
+// Termination: every queue item (tail counter) eventually ends one chain (done
+// counter); reading done, then tail, and finding them equal means no chain was
+// running when done was read, so none can start again.
+__global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
+    const unsigned lane = lane32();
+    const uint32_t cells = uint32_t(a.g.cells);
+    unsigned long long* head = ctr64(a, kFlowHead);
+    unsigned long long* tail = ctr64(a, kFlowTail);
+    unsigned long long* recs = ctr64(a, kFlowRecs);
+    unsigned long long* done = ctr64(a, kFlowDone);
+    bool have = false;                   // holds an item (v, e)
+    unsigned long long slot = ~0ull;     // reserved queue slot, not yet filled
+    bool pend = false;                   // produced item (pu, pe) waiting for a queue slot
+    uint32_t v = 0, e = 0, pu = 0, pe = 0;
+    uint32_t idle = 0;
+    unsigned nap = 32;
+    for (;;) {
+        const bool need = !have && slot == ~0ull;
+        const unsigned mneed = __ballot_sync(0xFFFFFFFFu, need);
+        const unsigned mhave = __ballot_sync(0xFFFFFFFFu, have);
+        const unsigned mpend = __ballot_sync(0xFFFFFFFFu, pend);
+        // ---- phase 1: independent requests, all in flight together
+        unsigned long long hb = 0, rb = 0, tb = 0;
+        if (mneed && int(lane) == __ffs(mneed) - 1) hb = atomicAdd(head, (unsigned long long)__popc(mneed));
+        if (mhave && int(lane) == __ffs(mhave) - 1) rb = atomicAdd(recs, (unsigned long long)__popc(mhave));
+        if (mpend && int(lane) == __ffs(mpend) - 1) tb = atomicAdd(tail, (unsigned long long)__popc(mpend));
+        unsigned long long it = kEmpty;
+        if (!have && slot < a.queue_cap) it = dev_atomic64(a.queue[slot]).load(cuda::memory_order_relaxed);
+        uint64_t local = 0;
+        uint32_t value = 0, cold = 0;
+        const uint32_t bit = 1u << (e & 31u);
+        if (have) {
+            local = __ldg(a.loc + e);
+            if (a.val) value = __ldg(a.val + e);
+            cold = atomicOr(a.claimed + (e >> 5), bit);
+        }
+        if (mneed) {
+            hb = __shfl_sync(0xFFFFFFFFu, hb, __ffs(mneed) - 1);
+            if (need) slot = hb + __popc(mneed & lanes_below());
+        }
+        if (mpend) {
+            tb = __shfl_sync(0xFFFFFFFFu, tb, __ffs(mpend) - 1);
+            if (pend) {
+                const unsigned long long qs = tb + __popc(mpend & lanes_below());
+                if (qs < a.queue_cap)
+                    dev_atomic64(a.queue[qs]).store((unsigned long long)pu << 32 | pe, cuda::memory_order_relaxed);
+                else
+                    atomicOr(a.err, kErrFrontier);
+                pend = false;
+            }
+        }
+        bool got = false;
+        if (!have && it != kEmpty) {
+            got = true;
+            slot = ~0ull;
+        }
+        // ---- phase 2: removals of the claimed edges
+        bool retire = false;
+        if (mhave) {
+            rb = __shfl_sync(0xFFFFFFFFu, rb, __ffs(mhave) - 1);
+            asm volatile("" ::: "memory");  // the record slot is taken before the removals below
+            const bool peeled = have && !(cold & bit);
+            bool next = false;
+            uint32_t nv = 0, ne = 0;
+            if (have) {
+                const unsigned long long rs = rb + __popc(mhave & lanes_below());
+                if (peeled) {
+                    atomicOr(a.pv + (v >> 5), 1u << (v & 31u));
+                    const uint32_t s = v / cells;
+                    const uint32_t base = s * cells;
+                    const unsigned long long st0 = __ldg(a.start + s);
+                    const uint32_t dec = 1u + (uint32_t(e - st0) << 5);
+                    uint64_t vv[3];
+                    edge_of(a.g, local, vv);
+                    const uint32_t lv = v - base;
+                    const uint32_t c0 = uint32_t(vv[0]), c1 = uint32_t(vv[1]), c2 = uint32_t(vv[2]);
+                    const uint32_t o0 = base + (c0 == lv ? c1 : c0);             // the two vertices other
+                    const uint32_t o1 = base + (c0 != lv && c1 != lv ? c1 : c2);  // than v, in edge order
+                    const uint32_t w0 = atomicAdd(a.W + o0, 0u - dec) - dec;
+                    const uint32_t w1 = atomicAdd(a.W + o1, 0u - dec) - dec;
+                    if ((w0 & 31u) == 1u) {
+                        next = true;
+                        nv = o0;
+                        ne = uint32_t(st0 + (w0 >> 5));
+                    }
+                    if ((w1 & 31u) == 1u) {
+                        if (!next) {
+                            next = true;
+                            nv = o1;
+                            ne = uint32_t(st0 + (w1 >> 5));
+                        } else {
+                            pend = true;
+                            pu = o1;
+                            pe = uint32_t(st0 + (w1 >> 5));
+                        }
+                    }
+                    a.rec[rs] = make_uint4(v, o0, o1, a.val ? value : fingerprint(local, a.g.b));
+                } else {
+                    a.rec[rs].x = kHole;
+                }
+                if (next) {
+                    v = nv;
+                    e = ne;
+                } else {
+                    have = false;
+                    retire = true;
+                }
+            }
+            const unsigned mpeeled = __ballot_sync(0xFFFFFFFFu, peeled);
+            if (mpeeled && lane == 0) atomicAdd(a.ctr + kFlowPeeled, uint32_t(__popc(mpeeled)));
+        }
+        // a chain that ended had its produced items' slots taken in earlier iterations
+        const unsigned mret = __ballot_sync(0xFFFFFFFFu, retire);
+        if (mret && lane == 0) atomicAdd(done, (unsigned long long)__popc(mret));
+        if (got) {
+            v = uint32_t(it >> 32);
+            e = uint32_t(it);
+            have = true;
+        }
+        if (__ballot_sync(0xFFFFFFFFu, have || pend) != 0) {
+            idle = 0;
+            nap = 32;
+            continue;
+        }
+        // nothing in flight in this warp: leave once every queue item's chain has
+        // ended (checked every 8th idle pass: the counters' lines are shared by all)
+        unsigned long long f = 0, t = 1;
+        uint32_t er = 0;
+        if (lane == 0 && (idle & 7u) == 0) {
+            f = dev_atomic64(*done).load(cuda::memory_order_acquire);
+            t = dev_atomic64(*tail).load(cuda::memory_order_relaxed);
+            er = dev_atomic32(*a.err).load(cuda::memory_order_relaxed);
+        }
+        f = __shfl_sync(0xFFFFFFFFu, f, 0);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        er = __shfl_sync(0xFFFFFFFFu, er, 0);
+        if (f == t || (er & (kErrTimeout | kErrFrontier))) break;
+        if (++idle > kIdleLimit) {
+            if (lane == 0) atomicOr(a.err, kErrTimeout);
+            break;
+        }
+        __nanosleep(nap);
+        nap = min(nap * 2u, kNapMax);
+    }
+}
+
+// -------------------------------------------------------------- assignment
+
+// Vertices no edge was peeled from are final with value 0; the others wait.
+__global__ void __launch_bounds__(kFT) k_final_init(FlowArgs a) {
+    const uint64_t V = uint64_t(a.S) * a.g.cells;
+    for (uint64_t v = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v < V; v += uint64_t(gridDim.x) * blockDim.x)
+        a.fv[v] = ((__ldg(a.pv + (v >> 5)) >> (v & 31u)) & 1u) ? 0ull : kFinal;
+}
+
+// Dataflow assignment over the record slots, largest slot first.
+__global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
+    const int b = a.g.b;
+    const uint64_t count = a.nrec;
+    const unsigned lane = lane32();
+    const uint32_t vmask = b == 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(ctr64(a, kFlowNext), 32ull);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= count) break;
+        const uint64_t k = base + lane;
+        uint4 r = make_uint4(kHole, 0, 0, 0);
+        if (k < count) r = __ldg(a.rec + (count - 1 - k));
+        bool done = r.x == kHole;
+        uint32_t polls = 0;
+        unsigned nap = 32;
+        bool fail = false;
+        for (;;) {
+            if (!done) {
+                const unsigned long long wy = dev_atomic64(a.fv[r.y]).load(cuda::memory_order_relaxed);
+                const unsigned long long wz = dev_atomic64(a.fv[r.z]).load(cuda::memory_order_relaxed);
+                if (wy & wz & kFinal) {
+                    const uint32_t x = (r.w ^ uint32_t(wy) ^ uint32_t(wz)) & vmask;
+                    dev_atomic64(a.fv[r.x]).store(kFinal | x, cuda::memory_order_relaxed);
+                    cell_put_zero(a.data, b, a.cell_base + r.x, x);
+                    done = true;
+                }
+            }
+            if (__all_sync(0xFFFFFFFFu, done)) break;
+            if (++polls > kIdleLimit) fail = true;
+            if ((polls & 63u) == 0 && (dev_atomic32(*a.err).load(cuda::memory_order_relaxed) & kErrTimeout)) fail = true;
+            if (__any_sync(0xFFFFFFFFu, fail)) {
+                fail = true;
+                break;
+            }
+            __nanosleep(nap);
+            nap = min(nap * 2u, kAssignNapMax);
+        }
+        if (fail) {
+            if (lane == 0) atomicOr(a.err, kErrTimeout);
+            break;
+        }
+    }
+}
+
+// ----------------------------------------------------- segment order (locality)
+
+// Edges of a fuse shard are peeled as a wave that sweeps the segments, and the
+// first vertex of an edge fixes its segment (v0 = mulhi(local, l*seg) grows
+// with the local signature). Sorting every tile of kTile consecutive edges by
+// (shard, segment) in shared memory puts the edges the wave touches at one
+// time into runs of consecutive entries, so their signatures, values and claim
+// bits are read as whole sectors. A tile that spans more than two shards (tiny
+// shards) is left as it is.
+constexpr int kTile = 4096;
+constexpr int kTileThreads = 256;
+constexpr uint32_t kTileBins = 4096;  // (shard, segment group) bins per tile
+
+__global__ void __launch_bounds__(kTileThreads) k_tile_order(uint64_t* __restrict__ loc, uint32_t* __restrict__ val,
+                                                             uint64_t n, const unsigned long long* __restrict__ start,
+                                                             uint32_t S, Geom g, uint32_t nb, uint32_t sshift) {
+    extern __shared__ unsigned long long smem_tile[];
+    uint64_t* s_loc = reinterpret_cast<uint64_t*>(smem_tile);
+    uint32_t* s_val = reinterpret_cast<uint32_t*>(s_loc + kTile);
+    uint32_t* s_cnt = s_val + kTile;  // 2 * nb
+    __shared__ uint32_t s_first, s_split, s_skip, s_warp[kTileThreads / 32];
+    const uint32_t nbins = 2 * nb;
+    for (uint64_t t0 = uint64_t(blockIdx.x) * kTile; t0 < n; t0 += uint64_t(gridDim.x) * kTile) {
+        const uint32_t m = n - t0 < uint64_t(kTile) ? uint32_t(n - t0) : uint32_t(kTile);
+        if (threadIdx.x == 0) {
+            const uint32_t f = flow_shard_of_edge(start, S, t0), l = flow_shard_of_edge(start, S, t0 + m - 1);
+            s_first = f;
+            s_skip = l - f > 1;
+            const unsigned long long sp = __ldg(start + f + 1) - t0;  // first key of shard f+1
+            s_split = sp < m ? uint32_t(sp) : m;
+        }
+        for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        if (s_skip) {
+            __syncthreads();
+            continue;
+        }
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+            const uint64_t x = loc[t0 + i];
+            s_loc[i] = x;
+            if (val) s_val[i] = val[t0 + i];
+            const uint32_t bin = (i >= s_split ? nb : 0u) + (uint32_t(mulhi(x, g.span) >> g.lg_seg) >> sshift);
+            atomicAdd(&s_cnt[bin], 1u);
+        }
+        __syncthreads();
+        // exclusive scan of the bin counts: each thread owns a run of consecutive bins
+        const uint32_t per = (nbins + blockDim.x - 1) / blockDim.x;
+        const uint32_t b0 = min(nbins, threadIdx.x * per), b1 = min(nbins, b0 + per);
+        uint32_t sum = 0;
+        for (uint32_t i = b0; i < b1; i++) sum += s_cnt[i];
+        uint32_t incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane32() >= unsigned(d)) incl += y;
+        }
+        if (lane32() == 31) s_warp[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        uint32_t off = incl - sum;
+        for (uint32_t w = 0; w < (threadIdx.x >> 5); w++) off += s_warp[w];
+        for (uint32_t i = b0; i < b1; i++) {
+            const uint32_t c = s_cnt[i];
+            s_cnt[i] = off;
+            off += c;
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+            const uint64_t x = s_loc[i];
+            const uint32_t bin = (i >= s_split ? nb : 0u) + (uint32_t(mulhi(x, g.span) >> g.lg_seg) >> sshift);
+            const uint32_t pos = atomicAdd(&s_cnt[bin], 1u);
+            loc[t0 + pos] = x;
+            if (val) val[t0 + pos] = s_val[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ launches
+
+static unsigned grid_for(uint64_t work) {
+    uint64_t blocks = (work + kFT - 1) / kFT;
+    const uint64_t cap = uint64_t(num_sms()) * 8;
+    if (blocks > cap) blocks = cap;
+    return unsigned(blocks < 1 ? 1 : blocks);
+}
+
+// Worker grids: one block of 8 warps per SM. Fewer, fuller warps take fewer
+// turns at the shared queue and record counters, whose queueing sets the
+// latency of a peeling step.
+static unsigned worker_grid() { return unsigned(num_sms()); }
+// Assignment polls without hot counters on its path: two blocks per SM.
+static unsigned assign_grid() { return unsigned(num_sms()) * 2u; }
+
+cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
+                               const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_incidence32<<<grid_for(n), kFT, 0, st>>>(loc, n, start, S, g, W, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st) {
+    k_flow_seed<<<grid_for(uint64_t(a.S) * a.g.cells), kFT, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_flow_peel<<<worker_grid(), kFT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st) {
+    k_final_init<<<grid_for(uint64_t(a.S) * a.g.cells), kFT, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.nrec == 0) return e;
+    k_flow_assign<<<assign_grid(), kFT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_order(uint64_t* loc, uint32_t* val, uint64_t n, const unsigned long long* start,
+                              uint32_t S, const Geom& g, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t l = uint32_t(g.span >> g.lg_seg);
+    uint32_t sshift = 0;
+    while (((l - 1) >> sshift) + 1 > kTileBins / 2) sshift++;
+    const uint32_t nb = ((l - 1) >> sshift) + 1;
+    const size_t smem = size_t(kTile) * 12 + size_t(2 * nb) * 4;
+    static std::atomic<uint64_t> attr_set{0};  // one bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (!(attr_set.load() & bit)) {
+        e = cudaFuncSetAttribute(k_tile_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(size_t(kTile) * 12 + size_t(kTileBins) * 4));
+        if (e != cudaSuccess) return e;
+        attr_set.fetch_or(bit);
+    }
+    uint64_t tiles = (n + kTile - 1) / kTile;
+    const uint64_t cap = uint64_t(num_sms()) * 2;
+    k_tile_order<<<unsigned(tiles < cap ? tiles : cap), kTileThreads, smem, st>>>(loc, val, n, start, S, g, nb,
+                                                                                  sshift);
+    return cudaGetLastError();
+}
+
+}  // namespace vf

@@ -55,6 +55,48 @@ cudaError_t launch_accumulate(const uint64_t* loc, uint64_t n, const unsigned lo
 cudaError_t launch_peel(FuseSolveArgs a, cudaStream_t st);
 cudaError_t launch_assign(FuseSolveArgs a, cudaStream_t st);
 
+// Fuse-regime asynchronous solver: worklist peeling that records the peeled
+// edges in slot order, then a dataflow assignment in reverse slot order.
+// Counter words (u32 index into ctr), one 128-byte line each.
+enum : uint32_t {
+    kFlowHead = 0,      // u64: queue slots taken by consumers
+    kFlowTail = 32,     // u64: queue slots filled
+    kFlowRecs = 64,     // u64: record slots taken
+    kFlowDone = 96,     // u64: queue items whose chain has ended
+    kFlowNext = 128,    // u64: assignment: next record position to take
+    kFlowPeeled = 160,  // edges peeled
+    kFlowErr = 192,     // error bits
+    kFlowWords = 224
+};
+struct FlowArgs {
+    const uint64_t* loc;              // bucketed local signatures
+    const uint32_t* val;              // bucketed values, NULL for a filter
+    const unsigned long long* start;  // S+1 shard starts
+    uint32_t S;
+    Geom g;
+    uint32_t* W;                      // S*cells vertex words (degree, sum of edge indices)
+    unsigned long long* queue;        // work items (vertex << 32 | edge); all ones = empty
+    unsigned long long* fv;           // assignment: S*cells value words, value | 1 << 32 once final
+                                      // (the queue's memory, reused)
+    uint64_t queue_cap;
+    uint32_t* claimed;                // one bit per edge
+    uint32_t* pv;                     // one bit per vertex: an edge was peeled from it
+    uint4* rec;                       // per slot {peeled vertex, other, other, value}; x = ~0: empty
+    uint64_t nrec;                    // assignment: record slots taken by the peel
+    uint32_t* ctr;                    // kFlowWords counter words
+    uint32_t* err;                    // == ctr + kFlowErr
+    uint8_t* data;                    // assignment target
+    uint64_t cell_base;               // cell of the first vertex (shard groups)
+};
+cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
+                               const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st);
+cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st);
+cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st);
+// Sorts each tile of consecutive edges by (shard, segment of the first vertex)
+// in place (fuse regime; locality of the peeling wave).
+cudaError_t launch_tile_order(uint64_t* loc, uint32_t* val, uint64_t n, const unsigned long long* start,
+                              uint32_t S, const Geom& g, cudaStream_t st);
+
 // LGE regime: one CTA per shard (peel + lazy Gaussian elimination + assign).
 // A task is one shard of one structure; a launch may mix structures.
 struct LgeTask {

@@ -44,8 +44,11 @@ def test_params_default_match_paper(vf, orc):
     p = vf.vf_params_default()
     o = orc.default_params()
     for f, _ in vf.VfParams._fields_:
+        if f == "fuse_solver":  # a scheduling choice of the CUDA path, not a parameter of the method
+            continue
         assert getattr(p, f) == getattr(o, f), f
     assert p.eps == 0.001 and p.lge_threshold == 800000
+    assert p.fuse_solver == vf.SOLVER_FLOW
 
 
 def _plan_pair(vf, orc, n, M, **kw):

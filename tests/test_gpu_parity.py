@@ -68,7 +68,7 @@ def check_build(vf, orc, keys, vals, offsets=None, n_other=20_000, **kw):
     s = vf.vf_build(dev(keys), None if vals is None else dev(vals), offsets=None if offsets is None else dev(offsets),
                     params=p)
     info = s.info
-    op = orc.default_params(kind=kind, key_kind=key_kind, **kw)
+    op = orc.default_params(kind=kind, key_kind=key_kind, **{k: v for k, v in kw.items() if k != "fuse_solver"})
     st, oi, odata = orc.build(op, keys, vals, offsets=offsets)
     assert st == orc.OK
     for f in ("regime", "h", "h_bb", "h_dup", "shards", "M", "c", "lg_seg", "seg", "l", "T", "cells",
@@ -163,43 +163,54 @@ def test_lge_host_inputs(vf, orc):
     assert isinstance(out, np.ndarray) and (out == vals).all()
 
 
-def test_function_fuse_unsharded_2pow20(vf, orc):
+# both fuse-regime solvers (asynchronous worklist, round-synchronous) must give
+# the oracle's outcome; SOLVER values are 0 (flow) and 1 (rounds)
+SOLVERS = pytest.mark.parametrize("solver", [0, 1], ids=["flow", "rounds"])
+
+
+@SOLVERS
+def test_function_fuse_unsharded_2pow20(vf, orc, solver):
     n = 1 << 20
     keys = synth.u64_keys(0, n, 1)
     vals = synth.values(n, 8, 1)
-    s, info, _ = check_build(vf, orc, keys, vals, seed=1, n_other=1 << 18)
+    s, info, _ = check_build(vf, orc, keys, vals, seed=1, n_other=1 << 18, fuse_solver=solver)
     assert info.regime == vf.REGIME_FUSE and info.h == 0 and info.lg_seg == 13
+    assert (0 < info.rounds < n) if solver == 1 else info.rounds == 0
 
 
+@SOLVERS
 @pytest.mark.parametrize("b", [1, 7, 8, 16, 32])
-def test_filter_fuse_regime(vf, orc, b):
+def test_filter_fuse_regime(vf, orc, b, solver):
     n = 1_000_003
     keys = synth.u64_keys(0, n, 3)
-    s, info, _ = check_build(vf, orc, keys, None, b=b, seed=5, n_other=200_000)
+    s, info, _ = check_build(vf, orc, keys, None, b=b, seed=5, n_other=200_000, fuse_solver=solver)
     other = synth.u64_keys(n, 400_000, 3)
     fpr = host(s.query(dev(other))).mean()
     p = 2.0 ** -b
     assert abs(fpr - p) < 5 * math.sqrt(p * (1 - p) / len(other)) + 1e-9
 
 
-def test_fuse_sharded_byte_strings(vf, orc):
+@SOLVERS
+def test_fuse_sharded_byte_strings(vf, orc, solver):
     # epsilon forced up so that 2M keys shard (h > 0) in the fuse regime
     n = 2_000_000
     data, offs = synth.byte_strings(0, n, 6)
     vals = synth.values(n, 16, 6)
     s, info, _ = check_build(vf, orc, data, vals, offsets=offs, b=16, mode=vf.MODE_FUSE, eps=0.01, seed=2,
-                             n_other=50_000)
+                             n_other=50_000, fuse_solver=solver)
     assert info.h >= 1
 
 
-def test_retries_match_oracle(vf, orc):
+@SOLVERS
+def test_retries_match_oracle(vf, orc, solver):
     # small forced fuse graphs often fail to peel: the GPU must fail exactly when
     # the oracle does (the 2-core is unique) and succeed with the same seed
     keys = synth.u64_keys(0, 600_000, 4)
     vals = synth.values(600_000, 8, 4)
     retried = 0
     for seed in range(8):
-        s, info, oi = check_build(vf, orc, keys, vals, mode=vf.MODE_FUSE, seed=seed, max_retries=20, n_other=0)
+        s, info, oi = check_build(vf, orc, keys, vals, mode=vf.MODE_FUSE, seed=seed, max_retries=20, n_other=0,
+                                  fuse_solver=solver)
         retried += info.retries > 0
     assert retried > 0
 
