@@ -60,8 +60,11 @@ ALGO_BYTES = {
     "hash_hist": lambda b, kind: 8.0,                                   # key read
     "scatter": lambda b, kind: 8.0 + 8.0 + (0 if kind == "filter" else 1.0 + 4.0),  # key in, local sig out (+values)
     "incidence": lambda b, kind: 8.0 + 3 * 32.0,                        # local sig + 3 vertex-word sectors
-    "peel": lambda b, kind: 4 + 32 + 32 + 32 + 2 * 32 + 4 + 8,          # frontier, own word, claim, sig, 2 RMW, order, pushes
-    "assign": lambda b, kind: 4 + 32 + (0 if kind == "filter" else 32) + 3 * 32,  # order, sig, value, 3 cells
+    # asynchronous fuse solver (the default): local signature (tile-ordered, streamed), value,
+    # two vertex-word sectors (fetch-and-add), record written, queue item written + read
+    "peel": lambda b, kind: 8 + (0 if kind == "filter" else 4) + 2 * 32 + 16 + 16,
+    # record read, two value-word sectors polled, own value word, data cell
+    "assign": lambda b, kind: 16 + 2 * 32 + 32 + 32,
     "lge": lambda b, kind: 8.0 + 8.0 * 3,                               # per key, shard state on chip (lower bound)
     "query": lambda b, kind: 8.0 + 3 * 32.0 + 1.0,                      # key, 3 cell sectors, output
 }
@@ -333,7 +336,7 @@ def run_gpu(args):
 # Per-launch DRAM traffic (bytes) from ncu captures of the same kernels, scaled
 # from the captured case by units processed; absent until a capture of the
 # current kernel exists (profiles/ holds the summaries).
-TRAFFIC = {("c2", "peel"): round(2.792688e9 / 2e7 * 1e8), ("c2", "query"): round(198.56e6 / 2e7 * 1e8)}
+TRAFFIC = {("c2", "query"): round(198.56e6 / 2e7 * 1e8)}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -603,7 +606,7 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))

@@ -109,6 +109,9 @@ void vf_params_default(vf_params *p);
  * Above 2^30 keys (64-bit keys, fuse regime, up to 2^36) the shards are built
  * one group of consecutive shards (<= 2^30 keys) at a time, so scratch memory
  * is bounded by the group, not by n (Sec. 6, shard-at-a-time construction).
+ * Scratch memory comes from the device's default stream-ordered pool; the
+ * first build on a device sets that pool to keep up to min(1/8 of device
+ * memory, 32 GiB) of freed memory cached for the process (release threshold).
  * Errors: VF_EINVAL, VF_ENOMEM, VF_EBUILD, VF_ETIMEOUT, VF_ECUDA, VF_ECAPACITY
  * (a fuse shard above 2^27 keys; more than 2^30 keys with byte strings or in
  * the LGE regime). */
@@ -198,8 +201,8 @@ vf_status vf_tune_batch(const vf_batch_item *items, uint32_t count, const vf_par
 /* Per-phase device timing (CUDA events recorded on the launching stream
  * around every kernel of build and query). Phases, in order: hash+histogram,
  * scatter, incidence, peel, assign, LGE solver, query. vf_timing_read waits
- * for the recorded events, adds their durations (milliseconds) and launch
- * counts into ms[7] / launches[7], and clears the record. Off by default;
+ * for the recorded events, adds their durations (milliseconds) and kernel
+ * launch counts into ms[7] / launches[7], and clears the record. Off by default;
  * timing serialises nothing but adds event records. Not thread-safe. */
 vf_status vf_timing_enable(int on);
 vf_status vf_timing_read(double *ms, uint64_t *launches);

@@ -61,6 +61,27 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// Builds allocate their scratch (gigabytes for large fuse shards) from the
+// device's default stream-ordered pool. By default the pool returns freed
+// memory to the system at every synchronisation, so each build would map its
+// scratch again; keep up to an eighth of the device memory (at most 32 GiB)
+// cached instead. Once per device and process.
+void keep_pool_warm(int dev) {
+    static std::mutex mu;
+    static uint64_t done = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || (done >> dev) & 1) return;
+    done |= uint64_t(1) << dev;
+    cudaMemPool_t pool;
+    size_t free_b = 0, total_b = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    uint64_t thr = std::min<uint64_t>(uint64_t(total_b) / 8, uint64_t(32) << 30);
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess) cudaGetLastError();
+}
+
 bool on_device(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -77,6 +98,7 @@ enum Phase { kPhHist = 0, kPhScatter, kPhAccum, kPhPeel, kPhAssign, kPhLge, kPhQ
 
 struct TimedLaunch {
     int phase;
+    int kernels;  // kernel launches between the two events
     cudaEvent_t a, b;
 };
 
@@ -87,8 +109,9 @@ std::vector<TimedLaunch> g_timed;
 struct PhaseTimer {
     int phase;
     cudaStream_t st;
+    int kernels;
     cudaEvent_t a = nullptr;
-    PhaseTimer(int ph, cudaStream_t s) : phase(ph), st(s) {
+    PhaseTimer(int ph, cudaStream_t s, int k = 1) : phase(ph), st(s), kernels(k) {
         if (g_timing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
     }
     ~PhaseTimer() {
@@ -96,7 +119,7 @@ struct PhaseTimer {
         cudaEvent_t b = nullptr;
         if (cudaEventCreate(&b) == cudaSuccess) {
             cudaEventRecord(b, st);
-            g_timed.push_back({phase, a, b});
+            g_timed.push_back({phase, kernels, a, b});
         } else {
             cudaEventDestroy(a);
         }
@@ -362,6 +385,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.fv = a.queue;
     a.queue_cap = V;
     a.claimed = claimed.as<uint32_t>();
+    a.claimed_bits = n;
     a.pv = pv.as<uint32_t>();
     a.rec = rec.as<uint4>();
     a.ctr = ctr.as<uint32_t>();
@@ -373,7 +397,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
         VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, st));
     }
     {
-        PhaseTimer t(kPhPeel, st);
+        PhaseTimer t(kPhPeel, st, 3);  // initial items, worklist peel, peeled count
         VF_CK(vf::launch_flow_peel(a, st));
     }
     std::vector<uint32_t> h(vf::kFlowWords);
@@ -381,7 +405,8 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     VF_CK(cudaStreamSynchronize(st));
     const uint32_t count = h[vf::kFlowPeeled], err = h[vf::kFlowErr];
     uint64_t slots = 0;
-    std::memcpy(&slots, &h[vf::kFlowRecs], 8);
+    std::memcpy(&slots, &h[vf::kFlowSlots], 8);
+    slots &= 0xFFFFFFFFull;  // record slots: low half
     *peeled = count;
     if (err & vf::kErrTimeout) return fail(VF_ETIMEOUT, "asynchronous peeling wait timed out");
     if (err & (vf::kErrDegOverflow | vf::kErrFrontier)) return VF_EBUILD;
@@ -389,7 +414,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     if (slots > V) return fail(VF_ECUDA, "asynchronous peeling took more record slots than items");
     a.nrec = slots;
     {
-        PhaseTimer t(kPhAssign, st);
+        PhaseTimer t(kPhAssign, st, slots ? 2 : 1);  // final flags + dataflow assignment
         VF_CK(vf::launch_flow_assign(a, st));
     }
     uint32_t e2 = 0;
@@ -683,7 +708,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
         }
         e = cudaGraphInstantiate(&exec, graph, 0);
         if (e == cudaSuccess) {
-            PhaseTimer t(kPhLge, st);
+            PhaseTimer t(kPhLge, st, 2);  // scatter + solver
             e = cudaGraphLaunch(exec, st);
         }
         if (exec) cudaGraphExecDestroy(exec);
@@ -693,7 +718,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
             return fail(VF_ECUDA, std::string("graph launch failed: ") + cudaGetErrorString(e));
         }
     } else {
-        PhaseTimer t(kPhLge, st);
+        PhaseTimer t(kPhLge, st, 2);  // scatter + solver
         cudaError_t e = enqueue(st);
         if (e != cudaSuccess) {
             free_data();
@@ -817,6 +842,7 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     VF_CK(cudaGetDevice(&dev));
+    keep_pool_warm(dev);
 
     Staged in_keys;
     vf_status rs = stage_keys(p.key_kind, keys, offsets, n, st, in_keys);
@@ -1077,7 +1103,7 @@ vf_status vf_timing_read(double* ms, uint64_t* launches) {
         if (e == cudaSuccess) e = cudaEventElapsedTime(&x, t.a, t.b);
         if (e != cudaSuccess) rs = fail(VF_ECUDA, std::string("timing: ") + cudaGetErrorString(e));
         ms[t.phase] += x;
-        launches[t.phase] += 1;
+        launches[t.phase] += uint64_t(t.kernels);
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
     }
@@ -1114,6 +1140,7 @@ vf_status vf_build_batch(const vf_batch_item* items, uint32_t count, const vf_pa
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     VF_CK(cudaGetDevice(&dev));
+    keep_pool_warm(dev);
     std::vector<Staged> staged(count);
     std::vector<const uint64_t*> kdev(count);
     std::vector<const void*> vdev(count, nullptr);

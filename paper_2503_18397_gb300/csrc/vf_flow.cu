@@ -9,8 +9,10 @@
 //
 // Peeling (the visit of Sec. 4.3 with many stacks at once): a lane follows one
 // chain: after peeling an edge it continues with a vertex that the edge brought
-// to degree one and publishes a second such vertex in a global queue. Idle
-// lanes reserve queue slots and take the item once it is written.
+// to degree one. A second such vertex goes to a free lane of the same warp
+// (a fork, by shuffle) or, when the warp has none, to a global queue. Lanes
+// of a warp with no work at all reserve queue slots and take the item once it
+// is written.
 //
 // Order: every item takes a record slot from one global counter together with
 // its claim, before it removes the edge from the other two vertices. A vertex
@@ -66,6 +68,24 @@ __device__ __forceinline__ unsigned long long reserve64(unsigned long long* ctr,
     return me ? base + __popc(mask & lanes_below()) : 0ull;
 }
 
+// Position of the r-th (from 0) set bit of m; m has more than r set bits.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const uint32_t low = (1u << w) - 1u;
+        const uint32_t c = __popc(m & low);
+        if (r >= c) {
+            r -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m &= low;
+        }
+    }
+    return pos;
+}
+
 __device__ __forceinline__ unsigned long long* ctr64(const FlowArgs& a, uint32_t word) {
     return reinterpret_cast<unsigned long long*>(a.ctr + word);
 }
@@ -90,23 +110,64 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
     }
 }
 
-// Initial items: every vertex of degree one with its edge.
+// Initial items: every vertex of degree one with its edge. A block takes
+// chunks of kSeedPer * kFT vertices and reserves the chunk's queue slots with
+// one atomic.
+constexpr int kSeedPer = 16;
+
 __global__ void __launch_bounds__(kFT) k_flow_seed(FlowArgs a) {
+    __shared__ uint32_t s_warp[kFT / 32];
+    __shared__ unsigned long long s_base;
     const uint64_t V = uint64_t(a.S) * a.g.cells;
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint32_t cells = uint32_t(a.g.cells);
-    for (uint64_t v0 = blockIdx.x * uint64_t(blockDim.x) + (threadIdx.x & ~31u); v0 < V; v0 += stride) {
-        const uint64_t v = v0 + lane32();
-        const uint32_t w = v < V ? a.W[v] : 0u;
-        const bool one = (w & 31u) == 1u;
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, one);
-        if (!m) continue;
-        const unsigned long long slot = reserve64(ctr64(a, kFlowTail), m, one);
-        if (one) {
-            const uint32_t s = uint32_t(v / cells);
-            a.queue[slot] = (v << 32) | (__ldg(a.start + s) + (w >> 5));
+    const uint64_t chunk = uint64_t(kFT) * kSeedPer;
+    const unsigned warp = threadIdx.x >> 5;
+    for (uint64_t c0 = blockIdx.x * chunk; c0 < V; c0 += uint64_t(gridDim.x) * chunk) {
+        uint32_t w[kSeedPer], cnt = 0;
+#pragma unroll
+        for (int j = 0; j < kSeedPer; j++) {
+            const uint64_t v = c0 + uint64_t(j) * kFT + threadIdx.x;
+            w[j] = v < V ? a.W[v] : 0u;
+            cnt += (w[j] & 31u) == 1u;
         }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane32() >= unsigned(d)) incl += y;
+        }
+        if (lane32() == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t total = 0;
+            for (int i = 0; i < kFT / 32; i++) {
+                const uint32_t t = s_warp[i];
+                s_warp[i] = total;
+                total += t;
+            }
+            s_base = total ? atomicAdd(ctr64(a, kFlowSlots), (unsigned long long)total << 32) >> 32 : 0ull;
+        }
+        __syncthreads();
+        unsigned long long slot = s_base + s_warp[warp] + incl - cnt;
+#pragma unroll
+        for (int j = 0; j < kSeedPer; j++) {
+            if ((w[j] & 31u) == 1u) {
+                const uint64_t v = c0 + uint64_t(j) * kFT + threadIdx.x;
+                a.queue[slot++] = (v << 32) | (__ldg(a.start + uint32_t(v / cells)) + (w[j] >> 5));
+            }
+        }
+        __syncthreads();
     }
+}
+
+// Peeled edges = set claim bits.
+__global__ void __launch_bounds__(kFT) k_count_claims(FlowArgs a, uint64_t words) {
+    uint32_t c = 0;
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < words; i += uint64_t(gridDim.x) * blockDim.x)
+        c += __popc(__ldg(a.claimed + i));
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, d);
+    if (lane32() == 0 && c) atomicAdd(a.ctr + kFlowPeeled, c);
 }
 
 // Worklist peeling; one chain per lane at a time. An iteration has two memory
@@ -114,15 +175,18 @@ __global__ void __launch_bounds__(kFT) k_flow_seed(FlowArgs a) {
 // iteration's results (queue slots for idle lanes, polls of reserved slots,
 // the item's signature, its claim, its record slot, the queue slot of an item
 // produced in the previous iteration), then the removals of the claimed edges.
-// Termination: every queue item (tail counter) eventually ends one chain (done
-// counter); reading done, then tail, and finding them equal means no chain was
-// running when done was read, so none can start again.
+// The record and queue-tail counters share one 64-bit word (record slots in
+// the low half, queue slots in the high half), so one fetch-and-add takes both.
+// Termination: chains start from queue items (tail counter) or forks. The done
+// counter holds chain ends minus forks, added once per iteration by lane 0 (so
+// a fork is subtracted before its chain's end is added); done == tail means no
+// chain is running. Reading done, then tail, and finding them equal means none
+// ran when done was read, so none can start again.
 __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
     const unsigned lane = lane32();
     const uint32_t cells = uint32_t(a.g.cells);
     unsigned long long* head = ctr64(a, kFlowHead);
-    unsigned long long* tail = ctr64(a, kFlowTail);
-    unsigned long long* recs = ctr64(a, kFlowRecs);
+    unsigned long long* slots = ctr64(a, kFlowSlots);
     unsigned long long* done = ctr64(a, kFlowDone);
     bool have = false;                   // holds an item (v, e)
     unsigned long long slot = ~0ull;     // reserved queue slot, not yet filled
@@ -131,15 +195,15 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
     uint32_t idle = 0;
     unsigned nap = 32;
     for (;;) {
-        const bool need = !have && slot == ~0ull;
-        const unsigned mneed = __ballot_sync(0xFFFFFFFFu, need);
         const unsigned mhave = __ballot_sync(0xFFFFFFFFu, have);
+        const bool need = !have && slot == ~0ull && mhave == 0;  // only an idle warp takes queue slots
+        const unsigned mneed = __ballot_sync(0xFFFFFFFFu, need);
         const unsigned mpend = __ballot_sync(0xFFFFFFFFu, pend);
         // ---- phase 1: independent requests, all in flight together
-        unsigned long long hb = 0, rb = 0, tb = 0;
+        unsigned long long hb = 0, rt = 0;  // rt: record slots (low half), queue slots (high half)
         if (mneed && int(lane) == __ffs(mneed) - 1) hb = atomicAdd(head, (unsigned long long)__popc(mneed));
-        if (mhave && int(lane) == __ffs(mhave) - 1) rb = atomicAdd(recs, (unsigned long long)__popc(mhave));
-        if (mpend && int(lane) == __ffs(mpend) - 1) tb = atomicAdd(tail, (unsigned long long)__popc(mpend));
+        if (mhave && int(lane) == __ffs(mhave) - 1)  // pend implies have
+            rt = atomicAdd(slots, ((unsigned long long)__popc(mpend) << 32) | (unsigned long long)__popc(mhave));
         unsigned long long it = kEmpty;
         if (!have && slot < a.queue_cap) it = dev_atomic64(a.queue[slot]).load(cuda::memory_order_relaxed);
         uint64_t local = 0;
@@ -154,10 +218,10 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
             hb = __shfl_sync(0xFFFFFFFFu, hb, __ffs(mneed) - 1);
             if (need) slot = hb + __popc(mneed & lanes_below());
         }
+        if (mhave) rt = __shfl_sync(0xFFFFFFFFu, rt, __ffs(mhave) - 1);
         if (mpend) {
-            tb = __shfl_sync(0xFFFFFFFFu, tb, __ffs(mpend) - 1);
             if (pend) {
-                const unsigned long long qs = tb + __popc(mpend & lanes_below());
+                const unsigned long long qs = (rt >> 32) + __popc(mpend & lanes_below());
                 if (qs < a.queue_cap)
                     dev_atomic64(a.queue[qs]).store((unsigned long long)pu << 32 | pe, cuda::memory_order_relaxed);
                 else
@@ -173,13 +237,12 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
         // ---- phase 2: removals of the claimed edges
         bool retire = false;
         if (mhave) {
-            rb = __shfl_sync(0xFFFFFFFFu, rb, __ffs(mhave) - 1);
             asm volatile("" ::: "memory");  // the record slot is taken before the removals below
             const bool peeled = have && !(cold & bit);
             bool next = false;
             uint32_t nv = 0, ne = 0;
             if (have) {
-                const unsigned long long rs = rb + __popc(mhave & lanes_below());
+                const unsigned long long rs = (rt & 0xFFFFFFFFull) + __popc(mhave & lanes_below());
                 if (peeled) {
                     atomicOr(a.pv + (v >> 5), 1u << (v & 31u));
                     const uint32_t s = v / cells;
@@ -222,12 +285,28 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
                     retire = true;
                 }
             }
-            const unsigned mpeeled = __ballot_sync(0xFFFFFFFFu, peeled);
-            if (mpeeled && lane == 0) atomicAdd(a.ctr + kFlowPeeled, uint32_t(__popc(mpeeled)));
         }
-        // a chain that ended had its produced items' slots taken in earlier iterations
+        // forks: second vertices go to lanes with neither an item nor a queue slot
+        const bool free_lane = !have && slot == ~0ull && !got;
+        const unsigned mfree = __ballot_sync(0xFFFFFFFFu, free_lane);
+        const unsigned mp = __ballot_sync(0xFFFFFFFFu, pend);
+        const uint32_t forks = min(__popc(mfree), __popc(mp));
+        if (forks) {
+            const uint32_t fr = __popc(mfree & lanes_below());
+            const uint32_t src = (free_lane && fr < forks) ? nth_set_bit(mp, fr) : lane;
+            const uint32_t xu = __shfl_sync(0xFFFFFFFFu, pu, src), xe = __shfl_sync(0xFFFFFFFFu, pe, src);
+            if (free_lane && fr < forks) {
+                have = true;
+                v = xu;
+                e = xe;
+            }
+            if (pend && uint32_t(__popc(mp & lanes_below())) < forks) pend = false;
+        }
+        // done += ended chains - forks (a chain that ended had its produced items
+        // counted in earlier iterations)
         const unsigned mret = __ballot_sync(0xFFFFFFFFu, retire);
-        if (mret && lane == 0) atomicAdd(done, (unsigned long long)__popc(mret));
+        if (lane == 0 && uint32_t(__popc(mret)) != forks)
+            atomicAdd(done, (unsigned long long)__popc(mret) - (unsigned long long)forks);
         if (got) {
             v = uint32_t(it >> 32);
             e = uint32_t(it);
@@ -244,7 +323,7 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
         uint32_t er = 0;
         if (lane == 0 && (idle & 7u) == 0) {
             f = dev_atomic64(*done).load(cuda::memory_order_acquire);
-            t = dev_atomic64(*tail).load(cuda::memory_order_relaxed);
+            t = dev_atomic64(*slots).load(cuda::memory_order_relaxed) >> 32;
             er = dev_atomic32(*a.err).load(cuda::memory_order_relaxed);
         }
         f = __shfl_sync(0xFFFFFFFFu, f, 0);
@@ -416,10 +495,12 @@ cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned l
 }
 
 cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st) {
-    k_flow_seed<<<grid_for(uint64_t(a.S) * a.g.cells), kFT, 0, st>>>(a);
+    k_flow_seed<<<grid_for((uint64_t(a.S) * a.g.cells + kSeedPer - 1) / kSeedPer), kFT, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_flow_peel<<<worker_grid(), kFT, 0, st>>>(a);
+    const uint64_t words = (uint64_t(a.claimed_bits) + 31) / 32;
+    k_count_claims<<<grid_for(words), kFT, 0, st>>>(a, words);
     return cudaGetLastError();
 }
 

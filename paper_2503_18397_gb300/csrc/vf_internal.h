@@ -29,6 +29,7 @@ struct FuseSolveArgs {
     Geom g;
     uint32_t* W;                      // S*cells vertex words
     uint32_t* claimed;                // one bit per edge
+    uint64_t claimed_bits;            // edges
     uint2* front[2];                  // frontier entries (vertex, edge)
     uint64_t front_cap;
     uint4* rec;                       // assignment records, one per peeled edge
@@ -60,8 +61,7 @@ cudaError_t launch_assign(FuseSolveArgs a, cudaStream_t st);
 // Counter words (u32 index into ctr), one 128-byte line each.
 enum : uint32_t {
     kFlowHead = 0,      // u64: queue slots taken by consumers
-    kFlowTail = 32,     // u64: queue slots filled
-    kFlowRecs = 64,     // u64: record slots taken
+    kFlowSlots = 32,    // u64: record slots taken (low half), queue slots filled (high half)
     kFlowDone = 96,     // u64: queue items whose chain has ended
     kFlowNext = 128,    // u64: assignment: next record position to take
     kFlowPeeled = 160,  // edges peeled
@@ -80,6 +80,7 @@ struct FlowArgs {
                                       // (the queue's memory, reused)
     uint64_t queue_cap;
     uint32_t* claimed;                // one bit per edge
+    uint64_t claimed_bits;            // edges
     uint32_t* pv;                     // one bit per vertex: an edge was peeled from it
     uint4* rec;                       // per slot {peeled vertex, other, other, value}; x = ~0: empty
     uint64_t nrec;                    // assignment: record slots taken by the peel
