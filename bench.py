@@ -58,7 +58,8 @@ WORKLOADS = {
 # Random accesses count one 32-byte sector each.
 ALGO_BYTES = {
     "hash_hist": lambda b, kind: 8.0,                                   # key read
-    "scatter": lambda b, kind: 8.0 + 8.0 + (0 if kind == "filter" else 1.0 + 4.0),  # key in, local sig out (+values)
+    # key in, local signature out (+ values); the fuse regime's tile sort is added in phase_table
+    "scatter": lambda b, kind: 8.0 + 8.0 + (0 if kind == "filter" else 1.0 + 4.0),
     "incidence": lambda b, kind: 8.0 + 3 * 32.0,                        # local sig + 3 vertex-word sectors
     # asynchronous fuse solver (the default): local signature (tile-ordered, streamed), value,
     # two vertex-word sectors (fetch-and-add), record written, queue item written + read
@@ -273,26 +274,9 @@ def run_gpu(args):
     d2h = 2 * n * outh.element_size()
 
     hbm, peak_kind = peaks()
-    nunits = {"hash_hist": n, "scatter": n, "incidence": n, "peel": n, "assign": n, "lge": n, "query": 2 * n}
-    per_phase = {}
-    for ph, (ms, cnt) in phases.items():
-        if cnt == 0:
-            continue
-        avg = ms / cnt
-        units_per_launch = nunits[ph] / (2 if ph == "query" else 1)
-        algo = ALGO_BYTES[ph](b, kind) * units_per_launch
-        per_phase[ph] = {"ms_per_launch": round(avg, 4), "launches": cnt,
-                         "share": round(ms / max(sum(v[0] for v in phases.values()), 1e-9), 4),
-                         "achieved_gbs": round(algo / (avg * 1e-3) / 1e9, 2)}
-    dom = max(per_phase, key=lambda k: per_phase[k]["share"]) if per_phase else None
+    per_phase, dom, roof = phase_table(phases, n, args.steps, b, kind, hbm, peak_kind, args.workload,
+                                       info.regime == vf.REGIME_FUSE)
     launches = sum(v[1] for v in phases.values())
-    roof = None
-    if dom:
-        d = per_phase[dom]
-        traffic = TRAFFIC.get((args.workload, dom))
-        roof = {"bound": "hbm", "kernel": dom, "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                "frac": round(d["achieved_gbs"] / hbm, 4), "traffic": traffic,
-                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_unit": ALGO_BYTES[dom](b, kind)}
     build_ns = b_ms * 1e6 / n
     qps = 2 * n / (q_ms * 1e-3)
     out = {
@@ -331,6 +315,37 @@ def run_gpu(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# Build attempts run hash+histogram once each; every attempt passes the keys
+# through scatter, incidence and peel (or the LGE solver); a successful one also
+# through assignment; every step queries 2n keys.
+def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse):
+    attempts = max(1, phases.get("hash_hist", (0, 0))[1])
+    units = {"hash_hist": n * attempts, "scatter": n * attempts, "incidence": n * attempts,
+             "peel": n * attempts, "lge": n * attempts, "assign": n * steps, "query": 2 * n * steps}
+    passes = {"hash_hist": attempts, "scatter": attempts, "incidence": attempts, "peel": attempts,
+              "lge": attempts, "assign": steps, "query": 2 * steps}
+    total = max(sum(v[0] for v in phases.values()), 1e-9)
+    per_phase = {}
+    for ph, (ms, cnt) in phases.items():
+        if cnt == 0:
+            continue
+        per_unit = ALGO_BYTES[ph](b, kind)
+        if ph == "scatter" and fuse:  # tile sort: signatures (and values) read and written once more
+            per_unit += 16.0 + (0 if kind == "filter" else 8.0)
+        algo = per_unit * units[ph]
+        per_phase[ph] = {"ms_total": round(ms, 3), "kernels": cnt, "passes": passes[ph],
+                         "ms_per_pass": round(ms / passes[ph], 4), "share": round(ms / total, 4),
+                         "achieved_gbs": round(algo / (ms * 1e-3) / 1e9, 2)}
+    dom = max(per_phase, key=lambda k: per_phase[k]["share"]) if per_phase else None
+    roof = None
+    if dom:
+        d = per_phase[dom]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": round(d["achieved_gbs"] / hbm, 4), "traffic": TRAFFIC.get((workload, dom)),
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_unit": ALGO_BYTES[dom](b, kind)}
+    return per_phase, dom, roof
 
 
 # Per-launch DRAM traffic (bytes) from ncu captures of the same kernels, scaled

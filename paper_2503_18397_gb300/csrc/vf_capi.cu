@@ -397,7 +397,8 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
         VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, st));
     }
     {
-        PhaseTimer t(kPhPeel, st, 3);  // initial items, worklist peel, peeled count
+        // per batch: (head rebase), initial items, worklist peel; then the peeled count
+        PhaseTimer t(kPhPeel, st, int(3 * vf::flow_batches(a)));
         VF_CK(vf::launch_flow_peel(a, st));
     }
     std::vector<uint32_t> h(vf::kFlowWords);
@@ -414,7 +415,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     if (slots > V) return fail(VF_ECUDA, "asynchronous peeling took more record slots than items");
     a.nrec = slots;
     {
-        PhaseTimer t(kPhAssign, st, slots ? 2 : 1);  // final flags + dataflow assignment
+        PhaseTimer t(kPhAssign, st, slots ? 2 : 1);  // final flags, dataflow assignment
         VF_CK(vf::launch_flow_assign(a, st));
     }
     uint32_t e2 = 0;

@@ -110,19 +110,19 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
     }
 }
 
-// Initial items: every vertex of degree one with its edge. A block takes
-// chunks of kSeedPer * kFT vertices and reserves the chunk's queue slots with
-// one atomic.
+// Initial items: every vertex of degree one with its edge, for the shards
+// [s_lo, s_hi) of one peeling batch. A block takes chunks of kSeedPer * kFT
+// vertices and reserves the chunk's queue slots with one atomic.
 constexpr int kSeedPer = 16;
 
-__global__ void __launch_bounds__(kFT) k_flow_seed(FlowArgs a) {
+__global__ void __launch_bounds__(kFT) k_flow_seed(FlowArgs a, uint32_t s_lo, uint32_t s_hi) {
     __shared__ uint32_t s_warp[kFT / 32];
     __shared__ unsigned long long s_base;
-    const uint64_t V = uint64_t(a.S) * a.g.cells;
     const uint32_t cells = uint32_t(a.g.cells);
+    const uint64_t V = uint64_t(s_hi) * cells;
     const uint64_t chunk = uint64_t(kFT) * kSeedPer;
     const unsigned warp = threadIdx.x >> 5;
-    for (uint64_t c0 = blockIdx.x * chunk; c0 < V; c0 += uint64_t(gridDim.x) * chunk) {
+    for (uint64_t c0 = uint64_t(s_lo) * cells + blockIdx.x * chunk; c0 < V; c0 += uint64_t(gridDim.x) * chunk) {
         uint32_t w[kSeedPer], cnt = 0;
 #pragma unroll
         for (int j = 0; j < kSeedPer; j++) {
@@ -158,6 +158,12 @@ __global__ void __launch_bounds__(kFT) k_flow_seed(FlowArgs a) {
         }
         __syncthreads();
     }
+}
+
+// Between peeling batches: consumers of the next batch start at the tail (the
+// lanes that reserved slots beyond it have left).
+__global__ void k_rebase_head(FlowArgs a) {
+    *ctr64(a, kFlowHead) = *ctr64(a, kFlowSlots) >> 32;
 }
 
 // Peeled edges = set claim bits.
@@ -494,11 +500,34 @@ cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned l
     return cudaGetLastError();
 }
 
+// Shards per peeling batch: the waves of a batch (two per shard, a few
+// segments of 4-byte vertex words each) should stay well inside L2. Larger
+// batches overlap more shards' waves but miss L2 once their working set grows
+// past a few tens of MB, which lengthens every step of the dependency chain.
+constexpr uint32_t kBatchHotMB = 16;
+
+static uint32_t shards_per_batch(const FlowArgs& a) {
+    const uint64_t seg = uint64_t(1) << a.g.lg_seg;
+    const uint64_t hot = 2 * 4 * seg * 4;  // bytes per shard
+    const uint64_t k = (uint64_t(kBatchHotMB) << 20) / hot;
+    return uint32_t(k < 1 ? 1 : (k > a.S ? a.S : k));
+}
+
+uint32_t flow_batches(const FlowArgs& a) {
+    const uint32_t per = shards_per_batch(a);
+    return (a.S + per - 1) / per;
+}
+
 cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st) {
-    k_flow_seed<<<grid_for((uint64_t(a.S) * a.g.cells + kSeedPer - 1) / kSeedPer), kFT, 0, st>>>(a);
+    const uint32_t per = shards_per_batch(a);
+    for (uint32_t s0 = 0; s0 < a.S; s0 += per) {
+        const uint32_t s1 = s0 + per < a.S ? s0 + per : a.S;
+        if (s0 > 0) k_rebase_head<<<1, 1, 0, st>>>(a);
+        k_flow_seed<<<grid_for((uint64_t(s1 - s0) * a.g.cells + kSeedPer - 1) / kSeedPer), kFT, 0, st>>>(a, s0, s1);
+        k_flow_peel<<<worker_grid(), kFT, 0, st>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_flow_peel<<<worker_grid(), kFT, 0, st>>>(a);
     const uint64_t words = (uint64_t(a.claimed_bits) + 31) / 32;
     k_count_claims<<<grid_for(words), kFT, 0, st>>>(a, words);
     return cudaGetLastError();

@@ -91,7 +91,10 @@ struct FlowArgs {
 };
 cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
                                const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st);
+// Peels the shards in batches whose waves fit in L2 (flow_batches launches
+// of initial items + worklist peel), then counts the peeled edges.
 cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st);
+uint32_t flow_batches(const FlowArgs& a);
 cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st);
 // Sorts each tile of consecutive edges by (shard, segment of the first vertex)
 // in place (fuse regime; locality of the peeling wave).
