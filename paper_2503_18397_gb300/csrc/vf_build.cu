@@ -173,9 +173,11 @@ __device__ __forceinline__ uint32_t shard_of_edge(const unsigned long long* __re
 // edge indices (Sec. 4.3, XOR trick). Degree overflow is reported, not wrapped.
 __global__ void __launch_bounds__(kThreads) k_accumulate(const uint64_t* __restrict__ loc, uint64_t n,
                                                          const unsigned long long* __restrict__ start, uint32_t S,
-                                                         Geom g, uint32_t* __restrict__ W, uint32_t* err) {
+                                                         Geom g, uint32_t* __restrict__ W, uint32_t* err,
+                                                         const uint32_t* __restrict__ drop) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t e = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; e < n; e += stride) {
+        if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;  // dropped duplicate
         uint32_t s = shard_of_edge(start, S, e);
         uint32_t el = uint32_t(e - start[s]);
         uint64_t v[3];
@@ -247,9 +249,9 @@ cudaError_t launch_sigs(int key_kind, const void* keys, const uint64_t* offs, ui
 }
 
 cudaError_t launch_accumulate(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
-                              const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st) {
+                              const Geom& g, uint32_t* W, uint32_t* err, const uint32_t* drop, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    k_accumulate<<<stream_grid(n), kThreads, 0, st>>>(loc, n, start, S, g, W, err);
+    k_accumulate<<<stream_grid(n), kThreads, 0, st>>>(loc, n, start, S, g, W, err, drop);
     return cudaGetLastError();
 }
 

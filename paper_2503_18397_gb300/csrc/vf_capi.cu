@@ -59,6 +59,15 @@ struct DevBuf {
     }
     template <class T>
     T* as() const { return static_cast<T*>(p); }
+    // Takes over o's memory (o is left empty).
+    void adopt(DevBuf& o) {
+        release();
+        p = o.p;
+        bytes = o.bytes;
+        st = o.st;
+        o.p = nullptr;
+        o.bytes = 0;
+    }
 };
 
 // Builds allocate their scratch (gigabytes for large fuse shards) from the
@@ -284,14 +293,18 @@ vf_status h2d(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
 // VF_EBUILD (peel failed: the attempt must be retried), or an error.
 vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
                        const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
-                       uint64_t* rounds_out, uint64_t cell_base) {
+                       uint64_t* rounds_out, uint64_t cell_base, const uint32_t* drop, uint64_t ndrop,
+                       DevBuf* claimed_out) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
     DevBuf W, claimed, f0, f1, rec, roff, ctr;
     VF_CK(W.alloc(V * 4, st));
     VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
     VF_CK(claimed.alloc(((n + 31) / 32) * 4, st));
-    VF_CK(cudaMemsetAsync(claimed.p, 0, ((n + 31) / 32) * 4, st));
+    if (drop)  // dropped duplicates count as claimed: they are never peeled
+        VF_CK(cudaMemcpyAsync(claimed.p, drop, ((n + 31) / 32) * 4, cudaMemcpyDeviceToDevice, st));
+    else
+        VF_CK(cudaMemsetAsync(claimed.p, 0, ((n + 31) / 32) * 4, st));
     VF_CK(f0.alloc(V * 8, st));
     VF_CK(f1.alloc(V * 8, st));
     VF_CK(rec.alloc(std::max<uint64_t>(n, 1) * 16, st));
@@ -325,7 +338,7 @@ vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc
     a.cell_base = cell_base;
     {
         PhaseTimer t(kPhAccum, st);
-        VF_CK(vf::launch_accumulate(loc, n, start, a.S, g, a.W, a.err, st));
+        VF_CK(vf::launch_accumulate(loc, n, start, a.S, g, a.W, a.err, drop, st));
     }
     {
         PhaseTimer t(kPhPeel, st);
@@ -339,7 +352,10 @@ vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc
     *rounds_out = rounds;
     if (err & vf::kErrTimeout) return fail(VF_ETIMEOUT, "peeling barrier timed out");
     if (err & (vf::kErrDegOverflow | vf::kErrFrontier)) return VF_EBUILD;
-    if (count != n) return VF_EBUILD;  // non-empty 2-core
+    if (count != n - ndrop) {  // non-empty 2-core
+        if (claimed_out) claimed_out->adopt(claimed);
+        return VF_EBUILD;
+    }
     VF_CK(cudaMemsetAsync(a.bar, 0, sizeof(vf::Bar2), st));
     a.rounds = rounds;
     {
@@ -357,7 +373,7 @@ vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc
 // (peel failed: retry), or an error.
 vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
                      const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
-                     uint64_t cell_base) {
+                     uint64_t cell_base, const uint32_t* drop, uint64_t ndrop, DevBuf* claimed_out) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
     DevBuf W, queue, claimed, pv, rec, ctr;
@@ -367,7 +383,10 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     VF_CK(cudaMemsetAsync(queue.p, 0xFF, V * 8, st));
     const uint64_t ewords = std::max<uint64_t>((n + 31) / 32, 1), vwords = std::max<uint64_t>((V + 31) / 32, 1);
     VF_CK(claimed.alloc(ewords * 4, st));
-    VF_CK(cudaMemsetAsync(claimed.p, 0, ewords * 4, st));
+    if (drop)  // dropped duplicates count as claimed: they are never peeled
+        VF_CK(cudaMemcpyAsync(claimed.p, drop, ewords * 4, cudaMemcpyDeviceToDevice, st));
+    else
+        VF_CK(cudaMemsetAsync(claimed.p, 0, ewords * 4, st));
     VF_CK(pv.alloc(vwords * 4, st));
     VF_CK(cudaMemsetAsync(pv.p, 0, vwords * 4, st));
     VF_CK(rec.alloc(std::max<uint64_t>(V, 1) * 16, st));  // one slot per item, at most one item per vertex
@@ -394,7 +413,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.cell_base = cell_base;
     {
         PhaseTimer t(kPhAccum, st);
-        VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, st));
+        VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, drop, st));
     }
     {
         // per batch: (head rebase), initial items, worklist peel; then the peeled count
@@ -408,10 +427,13 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     uint64_t slots = 0;
     std::memcpy(&slots, &h[vf::kFlowSlots], 8);
     slots &= 0xFFFFFFFFull;  // record slots: low half
-    *peeled = count;
+    *peeled = count - ndrop;  // claim bits include the dropped duplicates
     if (err & vf::kErrTimeout) return fail(VF_ETIMEOUT, "asynchronous peeling wait timed out");
     if (err & (vf::kErrDegOverflow | vf::kErrFrontier)) return VF_EBUILD;
-    if (count != n) return VF_EBUILD;  // non-empty 2-core
+    if (count != n) {  // non-empty 2-core
+        if (claimed_out) claimed_out->adopt(claimed);
+        return VF_EBUILD;
+    }
     if (slots > V) return fail(VF_ECUDA, "asynchronous peeling took more record slots than items");
     a.nrec = slots;
     {
@@ -426,21 +448,57 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
 }
 
 // One attempt of the fuse-regime solver: the asynchronous solver (default) or
-// the round-synchronous one. Reorders loc / val within each shard.
+// the round-synchronous one. Reorders loc / val within each shard. A filter
+// whose peel fails is checked for duplicate local signatures among the unpeeled
+// edges (identical edges never peel); if there are any, one copy of each is
+// kept and the same attempt is solved again without the others (Sec. 4.5),
+// which *dropped reports.
 vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32_t* val,
                      const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
-                     uint64_t* rounds_out, int solver, uint64_t cell_base = 0) {
+                     uint64_t* rounds_out, int solver, uint64_t* dropped, uint64_t cell_base = 0) {
     // edges of each tile in the order of their first vertex's segment (locality
     // of the peeling wave); the solvers only see edge indices within a shard
     {
         PhaseTimer t(kPhScatter, st);
         VF_CK(vf::launch_tile_order(loc, val, in.n_eff, start, uint32_t(in.shards), g, st));
     }
-    if (solver == VF_SOLVER_FLOW) {
-        *rounds_out = 0;
-        return solve_flow(in, g, loc, val, start, data, st, peeled, cell_base);
+    const uint64_t n = in.n_eff;
+    *dropped = 0;
+    DevBuf drop;
+    uint64_t ndrop = 0;
+    for (int pass = 0;; pass++) {
+        DevBuf claimed;
+        const bool dedup = g.kind == VF_FILTER && pass == 0;
+        vf_status rs;
+        if (solver == VF_SOLVER_FLOW) {
+            *rounds_out = 0;
+            rs = solve_flow(in, g, loc, val, start, data, st, peeled, cell_base,
+                            drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
+        } else {
+            rs = solve_rounds(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base,
+                              drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
+        }
+        if (rs != VF_EBUILD || !claimed.p) return rs;
+        // unpeeled edges of a failed filter attempt: any duplicates?
+        const uint64_t unpeeled = n - *peeled;
+        uint64_t cap = 1024;
+        while (cap < 2 * unpeeled) cap <<= 1;
+        const uint64_t words = std::max<uint64_t>((n + 31) / 32, 1);
+        DevBuf table, cnt;
+        VF_CK(table.alloc(cap * 8, st));
+        VF_CK(cudaMemsetAsync(table.p, 0, cap * 8, st));
+        VF_CK(drop.alloc(words * 4, st));
+        VF_CK(cudaMemsetAsync(drop.p, 0, words * 4, st));
+        VF_CK(cnt.alloc(8, st));
+        VF_CK(cudaMemsetAsync(cnt.p, 0, 8, st));
+        VF_CK(vf::launch_find_dups(loc, n, start, uint32_t(in.shards), claimed.as<uint32_t>(),
+                                   table.as<unsigned long long>(), cap, drop.as<uint32_t>(),
+                                   cnt.as<unsigned long long>(), nullptr, st));
+        VF_CK(cudaMemcpyAsync(&ndrop, cnt.p, 8, cudaMemcpyDeviceToHost, st));
+        VF_CK(cudaStreamSynchronize(st));
+        if (ndrop == 0) return VF_EBUILD;  // a genuine 2-core
+        *dropped = ndrop;
     }
-    return solve_rounds(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base);
 }
 
 // Tasks of the LGE solver for the shards of one or more structures, largest
@@ -465,8 +523,9 @@ void add_lge_tasks(std::vector<vf::LgeTask>& tasks, const std::vector<unsigned l
 // Runs the LGE solver over `tasks`; item_fail (device, one word per
 // structure) receives each structure's failure bits.
 vf_status run_lge_tasks(std::vector<vf::LgeTask>& tasks, bool lpt, const uint64_t* loc, const uint32_t* val,
-                        uint32_t* item_fail, cudaStream_t st, uint64_t* peeled, uint64_t* core, uint32_t* err_out) {
-    *peeled = *core = 0;
+                        uint32_t* item_fail, cudaStream_t st, uint64_t* peeled, uint64_t* core, uint32_t* err_out,
+                        uint64_t* dups) {
+    *peeled = *core = *dups = 0;
     *err_out = 0;
     if (tasks.empty()) return VF_OK;
     if (lpt)
@@ -508,17 +567,19 @@ vf_status run_lge_tasks(std::vector<vf::LgeTask>& tasks, bool lpt, const uint64_
     VF_CK(cudaStreamSynchronize(st));
     *peeled = h[4];
     *core = h[5];
+    *dups = h[7];
     *err_out = h[0];
     if (h[0] & vf::kErrTimeout) return fail(VF_ETIMEOUT, "LGE solver wait timed out");
     return VF_OK;
 }
 
 vf_status solve_lge(const vf_info& in, const std::vector<unsigned long long>& start, const uint64_t* loc,
-                    const uint32_t* val, uint8_t* data, cudaStream_t st, uint64_t* peeled, uint64_t* core) {
+                    const uint32_t* val, uint8_t* data, cudaStream_t st, uint64_t* peeled, uint64_t* core,
+                    uint64_t* dups) {
     std::vector<vf::LgeTask> tasks;
     add_lge_tasks(tasks, start, 0, in, data, 0);
     uint32_t err = 0;
-    vf_status rs = run_lge_tasks(tasks, true, loc, val, nullptr, st, peeled, core, &err);
+    vf_status rs = run_lge_tasks(tasks, true, loc, val, nullptr, st, peeled, core, &err, dups);
     if (rs != VF_OK) return rs;
     if (err & vf::kErrCapacity) return fail(VF_ECAPACITY, "LGE shard exceeds the per-CTA solver capacity");
     if (err & (vf::kErrUnsolvable | vf::kErrDegOverflow | vf::kErrLgeSize)) return VF_EBUILD;
@@ -644,7 +705,8 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     if (rs != VF_OK) return free_data(), rs;
     VF_CK(loc.alloc(std::max<uint64_t>(total, 1) * 8, st));
     VF_CK(val.alloc(std::max<uint64_t>(total, 1) * 4, st));
-    VF_CK(fails.alloc(std::max<uint64_t>(P, 1) * 4, st));
+    VF_CK(fails.alloc(std::max<uint64_t>(P, 1) * 8, st));  // failure bits, then dropped duplicates
+    uint32_t* dups_dev = fails.as<uint32_t>() + std::max<uint64_t>(P, 1);
     // LGE tasks of every LGE structure, one solver launch for all of them
     std::vector<vf::LgeTask> tasks;
     for (uint32_t j = 0; j < P; j++) {
@@ -676,6 +738,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     a.loc = loc.as<uint64_t>();
     a.val = val.as<uint32_t>();
     a.item_fail = fails.as<uint32_t>();
+    a.item_dup = dups_dev;
     a.scratch = scratch.as<uint32_t>();
     a.scratch_words_per_cta = per_cta;
     a.m_cap = m_cap;
@@ -684,7 +747,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     a.stats = misc.as<uint32_t>() + 4;
     // scatter + solver: one CUDA graph (or plain launches)
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
-        cudaError_t e = cudaMemsetAsync(fails.p, 0, std::max<uint64_t>(P, 1) * 4, q);
+        cudaError_t e = cudaMemsetAsync(fails.p, 0, std::max<uint64_t>(P, 1) * 8, q);
         if (e == cudaSuccess) e = cudaMemsetAsync(misc.p, 0, 64, q);
         if (e == cudaSuccess)
             e = vf::launch_batch_scatter(ddesc.as<vf::BatchItem>(), doff.as<uint64_t>(), P, total,
@@ -726,9 +789,12 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
             return fail(VF_ECUDA, std::string("batched solve launch failed: ") + cudaGetErrorString(e));
         }
     }
-    std::vector<uint32_t> fail_bits(P, 0);
+    std::vector<uint32_t> fail_bits(P, 0), dups(P, 0);
     VF_CK(cudaMemcpyAsync(fail_bits.data(), fails.p, P * 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaMemcpyAsync(dups.data(), dups_dev, P * 4, cudaMemcpyDeviceToHost, st));
     VF_CK(cudaStreamSynchronize(st));
+    for (uint32_t j = 0; j < P; j++)
+        if (info[j].regime == VF_REGIME_LGE) info[j].n_eff -= dups[j];
     // fuse-regime structures (above the threshold): one solver each
     for (uint32_t j = 0; j < P; j++) {
         if (info[j].regime != VF_REGIME_FUSE) continue;
@@ -737,14 +803,16 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
         DevBuf dstart;
         rs = h2d(dstart, start, st);
         if (rs != VF_OK) return free_data(), rs;
-        uint64_t peeled = 0, rounds = 0;
+        uint64_t peeled = 0, rounds = 0, dropped = 0;
         rs = solve_fuse(info[j], make_geom(info[j]), loc.as<uint64_t>() + key_off[j],
                         info[j].kind == VF_FUNC ? val.as<uint32_t>() + key_off[j] : nullptr,
-                        dstart.as<unsigned long long>(), data[j], st, &peeled, &rounds, common.fuse_solver);
+                        dstart.as<unsigned long long>(), data[j], st, &peeled, &rounds, common.fuse_solver,
+                        &dropped);
         if (rs == VF_EBUILD) fail_bits[j] |= vf::kErrUnsolvable;
         else if (rs != VF_OK) return free_data(), rs;
         info[j].peeled = peeled;
         info[j].rounds = rounds;
+        info[j].n_eff -= dropped;
     }
     VF_CK(cudaStreamSynchronize(st));
     for (uint32_t j = 0; j < P; j++) {
@@ -930,6 +998,7 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
         VF_CK(cursor.alloc(in.shards * 8, st));
         uint64_t peeled = 0, core = 0, rounds = 0;
         rs = VF_OK;
+        uint64_t dropped = 0;
         std::vector<unsigned long long> start;
         for (size_t k = 0; k + 1 < group.size() && rs == VF_OK; k++) {
             const uint32_t g0s = group[k], g1s = group[k + 1];
@@ -951,19 +1020,22 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
                                          g, cursor.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(),
                                          g0s, g1s, st));
             }
-            uint64_t pe = 0, co = 0, ro = 0;
+            uint64_t pe = 0, co = 0, ro = 0, dr = 0;
             if (in.regime == VF_REGIME_FUSE)
                 rs = solve_fuse(gi, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
                                 startb.as<unsigned long long>(), data.as<uint8_t>(), st, &pe, &ro,
-                                p.fuse_solver, uint64_t(g0s) * in.cells);
+                                p.fuse_solver, &dr, uint64_t(g0s) * in.cells);
             else
                 rs = solve_lge(in, start, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
-                               data.as<uint8_t>(), st, &pe, &co);
+                               data.as<uint8_t>(), st, &pe, &co, &dr);
             peeled += pe;
             core += co;
             rounds += ro;
+            dropped += dr;
         }
         in.peeled = peeled;
+        const uint64_t n_all = in.n_eff;
+        in.n_eff = n_all - dropped;
         in.core = in.regime == VF_REGIME_FUSE ? 0 : core;
         in.rounds = rounds;
         if (rs == VF_OK) {
@@ -977,6 +1049,7 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
             *out = s;
             return VF_OK;
         }
+        in.n_eff = n_all;
         last = rs;
         if (rs != VF_EBUILD) return rs;
     }

@@ -90,12 +90,15 @@ __device__ __forceinline__ unsigned long long* ctr64(const FlowArgs& a, uint32_t
     return reinterpret_cast<unsigned long long*>(a.ctr + word);
 }
 
-// Incidence: degree += 1 and sum += shard-local edge index, per vertex.
+// Incidence: degree += 1 and sum += shard-local edge index, per vertex. Edges
+// whose bit is set in `drop` (duplicate filter keys) are left out.
 __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict__ loc, uint64_t n,
                                                      const unsigned long long* __restrict__ start, uint32_t S, Geom g,
-                                                     uint32_t* __restrict__ W, uint32_t* err) {
+                                                     uint32_t* __restrict__ W, uint32_t* err,
+                                                     const uint32_t* __restrict__ drop) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t e = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; e < n; e += stride) {
+        if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
         const uint32_t s = flow_shard_of_edge(start, S, e);
         const uint32_t inc = 1u + (uint32_t(e - __ldg(start + s)) << 5);
         uint64_t v[3];
@@ -477,6 +480,42 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_order(uint64_t* __restric
     }
 }
 
+// ------------------------------------------------- filter de-duplication
+
+// Duplicate local signatures within a shard (a filter given repeated keys, or
+// a 64-bit collision) are identical edges, which never peel: a filter build
+// with duplicates always leaves them unpeeled. After a failed peel the
+// unpeeled edges are inserted into an open-addressing table keyed by (shard,
+// local signature); every edge that finds its key already present is marked in
+// `drop` (one copy of each group survives, Sec. 4.5) and counted, in total and
+// per shard. Without `claimed` every edge is inserted (duplicate count only).
+__global__ void __launch_bounds__(kFT) k_find_dups(const uint64_t* __restrict__ loc, uint64_t n,
+                                                   const unsigned long long* __restrict__ start, uint32_t S,
+                                                   const uint32_t* __restrict__ claimed,
+                                                   unsigned long long* __restrict__ table, uint64_t cap,
+                                                   uint32_t* __restrict__ drop, unsigned long long* ndrop,
+                                                   unsigned long long* __restrict__ per_shard) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t e = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; e < n; e += stride) {
+        if (claimed && ((__ldg(claimed + (e >> 5)) >> (e & 31u)) & 1u)) continue;
+        const uint64_t local = __ldg(loc + e);
+        const uint32_t s = flow_shard_of_edge(start, S, e);
+        uint64_t h = mix64(local + (uint64_t(s) + 1) * kGolden) & (cap - 1);
+        for (uint64_t probe = 0; probe < cap; probe++) {
+            const unsigned long long prev = atomicCAS(table + h, 0ull, (unsigned long long)e + 1);
+            if (prev == 0) break;  // first copy
+            const uint64_t o = prev - 1;
+            if (__ldg(loc + o) == local && flow_shard_of_edge(start, S, o) == s) {
+                if (drop) atomicOr(drop + (e >> 5), 1u << (e & 31u));
+                atomicAdd(ndrop, 1ull);
+                if (per_shard) atomicAdd(per_shard + s, 1ull);
+                break;
+            }
+            h = (h + 1) & (cap - 1);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launches
 
 static unsigned grid_for(uint64_t work) {
@@ -494,9 +533,9 @@ static unsigned worker_grid() { return unsigned(num_sms()); }
 static unsigned assign_grid() { return unsigned(num_sms()) * 2u; }
 
 cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
-                               const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st) {
+                               const Geom& g, uint32_t* W, uint32_t* err, const uint32_t* drop, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    k_incidence32<<<grid_for(n), kFT, 0, st>>>(loc, n, start, S, g, W, err);
+    k_incidence32<<<grid_for(n), kFT, 0, st>>>(loc, n, start, S, g, W, err, drop);
     return cudaGetLastError();
 }
 
@@ -564,6 +603,14 @@ cudaError_t launch_tile_order(uint64_t* loc, uint32_t* val, uint64_t n, const un
     const uint64_t cap = uint64_t(num_sms()) * 2;
     k_tile_order<<<unsigned(tiles < cap ? tiles : cap), kTileThreads, smem, st>>>(loc, val, n, start, S, g, nb,
                                                                                   sshift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_find_dups(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
+                             const uint32_t* claimed, unsigned long long* table, uint64_t cap, uint32_t* drop,
+                             unsigned long long* ndrop, unsigned long long* per_shard, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_find_dups<<<grid_for(n), kFT, 0, st>>>(loc, n, start, S, claimed, table, cap, drop, ndrop, per_shard);
     return cudaGetLastError();
 }
 

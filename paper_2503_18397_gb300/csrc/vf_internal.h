@@ -51,8 +51,9 @@ cudaError_t launch_scatter(const uint64_t* keys_u64, const Sig* sig_in, const vo
                            uint32_t s_lo, uint32_t s_hi, cudaStream_t st);
 cudaError_t launch_sigs(int key_kind, const void* keys, const uint64_t* offs, uint64_t n, uint64_t kh,
                         uint64_t kl, Sig* out, cudaStream_t st);
+// drop: optional bitmap of edges to leave out (duplicate filter keys).
 cudaError_t launch_accumulate(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
-                              const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st);
+                              const Geom& g, uint32_t* W, uint32_t* err, const uint32_t* drop, cudaStream_t st);
 cudaError_t launch_peel(FuseSolveArgs a, cudaStream_t st);
 cudaError_t launch_assign(FuseSolveArgs a, cudaStream_t st);
 
@@ -90,7 +91,14 @@ struct FlowArgs {
     uint64_t cell_base;               // cell of the first vertex (shard groups)
 };
 cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
-                               const Geom& g, uint32_t* W, uint32_t* err, cudaStream_t st);
+                               const Geom& g, uint32_t* W, uint32_t* err, const uint32_t* drop, cudaStream_t st);
+// Marks in `drop` (if given) every edge not set in `claimed` (if given) whose
+// (shard, local signature) an earlier such edge already has; table: cap (a
+// power of two, >= 2x the edges inserted) zeroed words; *ndrop counts the
+// marks, per_shard[s] (if given) those of shard s.
+cudaError_t launch_find_dups(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
+                             const uint32_t* claimed, unsigned long long* table, uint64_t cap, uint32_t* drop,
+                             unsigned long long* ndrop, unsigned long long* per_shard, cudaStream_t st);
 // Peels the shards in batches whose waves fit in L2 (flow_batches launches
 // of initial items + worklist peel), then counts the peeled edges.
 cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st);
@@ -125,7 +133,8 @@ struct LgeArgs {
     uint64_t scratch_words_per_cta;
     uint32_t m_cap, v_cap;            // largest shard / cell count the scratch layout holds
     uint32_t* err;                    // OR of all failure bits
-    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] task counter
+    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] task counter, [3] dropped duplicates
+    uint32_t* item_dup;               // per-structure dropped duplicate filter keys, or NULL
 };
 // Layout (in 32-bit words) of one CTA's LGE scratch slab for shards of at most
 // m keys and V cells.

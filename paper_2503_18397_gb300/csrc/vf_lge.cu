@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ uint32_t s_shard, s_fail;
     __shared__ uint32_t s_cnt[4];
-    __shared__ uint32_t s_C, s_rem, s_A, s_S, s_D, s_r, s_apos, s_nact, s_nbatch, s_piv, s_lo;
+    __shared__ uint32_t s_C, s_rem, s_A, s_S, s_D, s_r, s_apos, s_nact, s_nbatch, s_piv, s_lo, s_dup;
     __shared__ uint32_t s_hist[256];
     __shared__ uint32_t s_batch[kMaxBatch];
     __shared__ uint32_t s_part[kLT];
@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             s_skip = s_shard < a.ntasks &&
                      (*reinterpret_cast<volatile uint32_t*>(a.item_fail + a.tasks[s_shard].item) & kBad) != 0;
             s_fail = 0;
+            s_dup = 0;
         }
         __syncthreads();
         const uint32_t s = s_shard;
@@ -276,8 +277,29 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 inc_list[atomicAdd(&inc_cur[ev[1]], 1u)] = j;
                 inc_list[atomicAdd(&inc_cur[ev[2]], 1u)] = j;
             }
+            __syncthreads();
+            // Filters drop duplicate local signatures (Sec. 4.5). Identical edges never
+            // peel, so every duplicate is in the core, next to its copies in the
+            // incidence list of its first vertex; the copy of smallest index stays.
+            if (task.kind == 1) {
+                for (uint32_t j = tid; j < C; j += T) {
+                    const uint32_t e = __ldcg(&core[j]);
+                    const uint64_t x = __ldg(a.loc + e0 + e);
+                    const uint32_t v = __ldcg(&cev[3 * e]);
+                    const uint32_t q1 = __ldcg(&inc_off[v + 1]);
+                    for (uint32_t q = __ldcg(&inc_off[v]); q < q1; q++) {
+                        const uint32_t e2 = __ldcg(&core[__ldcg(&inc_list[q])]);
+                        if (e2 < e && __ldg(a.loc + e0 + e2) == x) {
+                            est[j] |= 4u;  // done: no equation of its own
+                            atomicAdd(&s_dup, 1u);
+                            break;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
             if (tid == 0) {
-                s_rem = C;
+                s_rem = C - s_dup;
                 s_A = s_S = s_D = s_r = s_apos = s_lo = 0;
                 s_cnt[0] = s_cnt[1] = 0;
                 soff[0] = 0;
@@ -560,7 +582,11 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
         }
         if (tid == 0) {
             atomicAdd(&a.stats[0], peeled);
-            atomicAdd(&a.stats[1], C);
+            atomicAdd(&a.stats[1], C - s_dup);
+            if (s_dup) {
+                atomicAdd(&a.stats[3], s_dup);
+                if (a.item_dup) atomicAdd(a.item_dup + task.item, s_dup);
+            }
         }
         __syncthreads();
     }

@@ -175,6 +175,7 @@ extern "C" vf_status vf_build_static(const uint64_t* keys, const void* values, u
         in.peeled = h[4];
         in.core = h[5];
         in.rounds = 0;
+        in.n_eff = n - h[7];  // a filter drops duplicate local signatures
         *info = in;
         return VF_OK;
     }

@@ -110,3 +110,26 @@ def test_batch_all_lge_threshold_and_tuner(vf, orc):
     _check_against_single(vf, orc, items, host, structs, opts_like_default=False)
     best2, ms2 = vf.vf_tune_batch(items)
     assert ms2 == -1.0 and best2.as_dict() == best.as_dict()  # cached per batch shape
+
+
+def test_batch_filter_duplicate_keys(vf, orc):
+    # filters with repeated keys inside a batch: copies are dropped per shard in the
+    # LGE solver (Sec. 4.5); n_eff and every query equal the oracle's build
+    rng = np.random.default_rng(31)
+    items, host = [], []
+    for i, n in enumerate([3000, 40_000, 250_000]):
+        keys = synth.u64_keys(i * 10_000_000, n, 31)
+        rep = keys[rng.choice(n, size=n // 20, replace=False)]
+        allk = np.concatenate([keys, rep, rep[: len(rep) // 3]])
+        allk = allk[rng.permutation(len(allk))]
+        items.append((_dev(allk), None, 1, 8, 500 + i))
+        host.append((allk, n))
+    structs = vf.vf_build_batch(items)
+    for s, (allk, n) in zip(structs, host):
+        info = s.info
+        st, oi, _ = orc.build(orc.default_params(kind=orc.FILTER, b=8, seed=info.seed - info.retries), allk)
+        assert st == orc.OK
+        assert info.n_eff == oi.n_eff == n
+        assert (info.seed, info.retries) == (oi.seed, oi.retries)
+        assert _host(s.query(_dev(allk))).all()
+        s.free()

@@ -72,10 +72,10 @@ def check_build(vf, orc, keys, vals, offsets=None, n_other=20_000, **kw):
     st, oi, odata = orc.build(op, keys, vals, offsets=offsets)
     assert st == orc.OK
     for f in ("regime", "h", "h_bb", "h_dup", "shards", "M", "c", "lg_seg", "seg", "l", "T", "cells",
-              "total_cells", "data_bytes", "seed", "retries"):
+              "total_cells", "data_bytes", "seed", "retries", "n_eff"):
         assert getattr(info, f) == getattr(oi, f), f
     if info.regime == vf.REGIME_FUSE:
-        assert info.peeled == oi.peeled == n
+        assert info.peeled == oi.peeled == info.n_eff
     out = host(s.query(dev(keys), offsets=None if offsets is None else dev(offsets)))
     if kind == vf.FUNC:
         assert (out == vals).all()
@@ -213,6 +213,40 @@ def test_retries_match_oracle(vf, orc, solver):
                                   fuse_solver=solver)
         retried += info.retries > 0
     assert retried > 0
+
+
+def with_repeats(n, frac, seed, triples=False):
+    """n distinct keys plus copies of a random subset (a few in triplicate), shuffled."""
+    keys = synth.u64_keys(0, n, seed)
+    rng = np.random.default_rng(seed)
+    rep = keys[rng.choice(n, size=int(n * frac), replace=False)]
+    parts = [keys, rep] + ([rep[: len(rep) // 4]] if triples else [])
+    allk = np.concatenate(parts)
+    return allk[rng.permutation(len(allk))]
+
+
+@SOLVERS
+def test_filter_duplicate_keys_fuse(vf, orc, solver):
+    # repeated keys give identical edges, which never peel: the GPU drops the
+    # copies found among the unpeeled edges and solves again (Sec. 4.5)
+    keys = with_repeats(1_000_000, 0.02, 21, triples=True)
+    s, info, oi = check_build(vf, orc, keys, None, seed=3, n_other=100_000, fuse_solver=solver)
+    assert info.regime == vf.REGIME_FUSE
+    assert info.n_eff == oi.n_eff == 1_000_000 < len(keys)
+
+
+def test_filter_duplicate_keys_lge(vf, orc):
+    keys = with_repeats(60_000, 0.05, 22, triples=True)
+    s, info, oi = check_build(vf, orc, keys, None, b=16, seed=4, n_other=20_000)
+    assert info.regime == vf.REGIME_LGE
+    assert info.n_eff == oi.n_eff == 60_000
+
+
+def test_filter_duplicate_keys_sharded_fuse(vf, orc):
+    # sharded fuse regime (eps forced up): duplicates are per shard
+    keys = with_repeats(2_000_000, 0.01, 23)
+    s, info, oi = check_build(vf, orc, keys, None, mode=vf.MODE_FUSE, eps=0.01, seed=6, n_other=50_000)
+    assert info.h >= 1 and info.n_eff == oi.n_eff == 2_000_000
 
 
 def test_query_stream_async_and_reuse(vf, orc):
