@@ -19,8 +19,8 @@ SRC = os.path.join(HERE, "vf_oracle.c")
 
 FUNC, FILTER = 0, 1
 KEYS_U64, KEYS_BYTES = 0, 1
-MODE_AUTO, MODE_FUSE, MODE_LGE = 0, 1, 2
-REGIME_FUSE, REGIME_LGE = 1, 2
+MODE_AUTO, MODE_FUSE, MODE_LGE, MODE_MWHC = 0, 1, 2, 3
+REGIME_FUSE, REGIME_LGE, REGIME_MWHC = 1, 2, 3
 OK, EINVAL, ENOMEM, EBUILD = 0, 1, 2, 3
 
 

@@ -7,7 +7,8 @@
  *
  * The build follows the paper step by step, one key and one shard at a time:
  *   hash -> shard on the top signature bits (Sec. 4, eq. logballsbins) ->
- *   per-shard 3-hypergraph (fuse graph, Sec. 4.2) -> degree and XOR-of-edge
+ *   per-shard 3-hypergraph (fuse graph, Sec. 4.2; or a 3-partite random
+ *   3-hypergraph for the MWHC construction, Sec. 4.1) -> degree and XOR-of-edge
  *   incidence (Sec. 4.3, XOR trick) -> stack-based peeling visit (Sec. 4.3) ->
  *   [LGE regime: solve the 2-core over GF(2), here by plain Gaussian
  *   elimination since any solution is acceptable, Sec. 3.3 / 4.2] ->
@@ -17,8 +18,12 @@
  * Parity status:
  *   mix64              pinned (published SplitMix64 test vector)
  *   signatures         pinned by uniformity / collision tests (repo-defined hash)
- *   shard bits         pinned (Table 1 shard counts; eq. dupmwhc worked example)
- *   geometry           pinned (space overhead of Sec. 5; closed forms)
+ *   shard bits         pinned (Table 1 shard counts; eq. dupmwhc worked example,
+ *                      through the planner in MWHC mode)
+ *   geometry           pinned (space overhead of Sec. 5; closed forms; MWHC's
+ *                      23% overhead and 3-partite cells)
+ *   MWHC edges         pinned (one vertex per part, uniform; duplicate rate
+ *                      against m^2 / (2 (cm/3)^3) of Sec. 4.1)
  *   peel               pinned (brute-force 2-core on tiny hypergraphs)
  *   GF(2) solve        pinned (brute force over all assignments on tiny systems)
  *   build / query      pinned (Problem 1: every key decodes to its value;
@@ -149,9 +154,16 @@ int orc_plan_h(const orc_params *p, uint64_t n, int *regime, int *h_bb, int *h_d
     int reg;
     if (p->mode == ORC_MODE_LGE) reg = ORC_REGIME_LGE;
     else if (p->mode == ORC_MODE_FUSE) reg = ORC_REGIME_FUSE;
+    else if (p->mode == ORC_MODE_MWHC) reg = ORC_REGIME_MWHC;
     else reg = n < p->lge_threshold ? ORC_REGIME_LGE : ORC_REGIME_FUSE;
     int h;
-    if (reg == ORC_REGIME_FUSE) {
+    if (reg == ORC_REGIME_MWHC) {
+        /* Sec. 4.1: random 3-hypergraphs with c = 1.23; eq. (dupmwhc) is
+         * combined with eq. (logballsbins) by taking the smaller bound. */
+        *h_bb = orc_h_ballsbins(n, p->eps);
+        *h_dup = orc_h_dupmwhc(n, p->eta, 1.23);
+        h = *h_bb < *h_dup ? *h_bb : *h_dup;
+    } else if (reg == ORC_REGIME_FUSE) {
         /* Sec. 4.2: the number of shards is the smaller of the two bounds. */
         *h_bb = orc_h_ballsbins(n, p->eps);
         *h_dup = orc_h_dupfuse(n, p->eta, 1.105);
@@ -170,7 +182,17 @@ int orc_plan_h(const orc_params *p, uint64_t n, int *regime, int *h_bb, int *h_d
 
 void orc_geometry(orc_info *in) {
     double Mf = (double)(in->M > 0 ? in->M : 1);
-    if (in->regime == ORC_REGIME_LGE) {
+    if (in->regime == ORC_REGIME_MWHC) {
+        /* k-partite 3-hypergraph (Sec. 4.1): three parts of ceil(c M / 3)
+         * vertices, at least 16 each so that tiny shards rarely repeat an edge. */
+        in->c = 1.23;
+        in->lg_seg = 0;
+        in->seg = 0;
+        in->l = 0;
+        in->T = 0;
+        uint64_t part = (uint64_t)ceil(in->c * Mf / 3.0);
+        in->cells = 3 * (part < 16 ? 16 : part);
+    } else if (in->regime == ORC_REGIME_LGE) {
         in->c = 1.12;
         in->lg_seg = 0;
         in->seg = 0;
@@ -229,6 +251,13 @@ void orc_edge(const orc_info *in, uint64_t local, uint64_t v[3]) {
         v[0] = v0;
         v[1] = (s + 1) * in->seg + (r % in->seg);
         v[2] = (s + 2) * in->seg + ((r >> 32) % in->seg);
+    } else if (in->regime == ORC_REGIME_MWHC) {
+        /* MWHC (Sec. 4.1, k-partite construction): one vertex drawn uniformly
+         * from each third of the shard's cells. */
+        uint64_t P = in->cells / 3;
+        v[0] = orc_mulhi(local, P);
+        v[1] = P + orc_mulhi(orc_mix64(local ^ ORC_C_EDGE), P);
+        v[2] = 2 * P + orc_mulhi(orc_mix64(local ^ ORC_C_EDGE2), P);
     } else {
         /* LGE regime: three distinct vertices drawn uniformly over the shard. */
         uint64_t V = in->cells;

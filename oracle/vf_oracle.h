@@ -24,8 +24,8 @@ extern "C" {
 
 enum { ORC_FUNC = 0, ORC_FILTER = 1 };
 enum { ORC_KEYS_U64 = 0, ORC_KEYS_BYTES = 1 };
-enum { ORC_MODE_AUTO = 0, ORC_MODE_FUSE = 1, ORC_MODE_LGE = 2 };
-enum { ORC_REGIME_FUSE = 1, ORC_REGIME_LGE = 2 };
+enum { ORC_MODE_AUTO = 0, ORC_MODE_FUSE = 1, ORC_MODE_LGE = 2, ORC_MODE_MWHC = 3 };
+enum { ORC_REGIME_FUSE = 1, ORC_REGIME_LGE = 2, ORC_REGIME_MWHC = 3 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EBUILD = 3 };
 
 typedef struct {
@@ -36,7 +36,7 @@ typedef struct {
     int max_retries;      /* extra attempts with seed+1, seed+2, ... */
     uint64_t seed;
     double eps;           /* epsilon of epsilon-cost sharding */
-    double eta;           /* duplicate-edge failure budget of eq. (dupfuse) */
+    double eta;           /* duplicate-edge failure budget of eq. (logdupfuse) / eq. (dupmwhc) */
     uint64_t lge_threshold;  /* auto mode: n below this -> LGE regime */
     uint64_t lge_target;     /* LGE regime: wanted mean keys per shard */
     uint64_t lge_max_shard;  /* LGE regime: largest allowed shard */
@@ -47,7 +47,7 @@ typedef struct {
     uint64_t n_eff;       /* keys after filter de-duplication */
     int kind, b, regime;
     int h;                /* shard bits; shards = 2^h */
-    int h_bb, h_dup;      /* the two bounds h is the minimum of (fuse regime) */
+    int h_bb, h_dup;      /* the two bounds h is the minimum of (fuse and MWHC regimes) */
     uint64_t shards;
     uint64_t M;           /* largest shard */
     double c;             /* expansion factor */

@@ -437,3 +437,94 @@ def test_small_structure_overhead(orc):
     for n in (50_000, 500_000):
         info = orc.geometry(orc.REGIME_LGE, 0, n)
         assert lo - 0.01 <= info.total_cells / n - 1 <= hi + 0.001
+
+
+# ------------------------------------------------------------------ MWHC (Sec. 4.1)
+
+def test_mwhc_planner_reproduces_paper_example(orc):
+    # the planner in MWHC mode combines eq. (dupmwhc) with eq. (logballsbins): at
+    # 10^12 keys, eps = 0.01, eta = 10^-3 the duplicate bound wins with 8192 shards
+    for keys, c, eta, shards in golden("mwhc_shard_example.txt"):
+        p = orc.default_params(mode=orc.MODE_MWHC, eps=0.01, eta=float(eta))
+        h, regime, h_bb, h_dup = orc.plan_h(p, int(keys))
+        assert regime == orc.REGIME_MWHC and 1 << h == int(shards) and h == h_dup < h_bb
+        # eq. (logballsbins) directly: x = n eps^2 / 2, h_bb = floor(lg x - lg ln x)
+        x = int(keys) * 0.01**2 / 2
+        assert h_bb == math.floor(math.log2(x) - math.log2(math.log(x)))
+    # small n: the balls-and-bins bound is the smaller one (no sharding below e)
+    p = orc.default_params(mode=orc.MODE_MWHC, eps=0.01, eta=1e-3)
+    h, regime, h_bb, h_dup = orc.plan_h(p, 20_000)
+    assert regime == orc.REGIME_MWHC and h == h_bb == 0
+
+
+def test_mwhc_geometry_three_parts_23_percent(orc):
+    # Sec. 4.1: 3-partite hypergraph with c = 1.23 -> ~23% space overhead
+    for M in (10_000, 1_000_003, 123_456_789):
+        info = _info(orc, orc.REGIME_MWHC, 0, M)
+        assert info.c == 1.23 and info.cells % 3 == 0
+        assert info.cells == 3 * math.ceil(1.23 * M / 3)
+        assert 0.23 - 1e-12 <= info.cells / M - 1 < 0.23 + 3.0 / M
+    # tiny shards: at least 16 vertices per part
+    assert _info(orc, orc.REGIME_MWHC, 0, 2).cells == 48
+
+
+def test_mwhc_edges_one_per_part_uniform(orc):
+    info = _info(orc, orc.REGIME_MWHC, 0, 3000)
+    P = info.cells // 3
+    loc = synth.u64_keys(0, 60_000, 12)
+    e = orc.edges_of(info, loc).astype(np.int64)
+    for k in range(3):
+        assert ((e[:, k] >= k * P) & (e[:, k] < (k + 1) * P)).all()
+        cnt = np.bincount(e[:, k] - k * P, minlength=P)
+        exp_ = len(loc) / P
+        dof = P - 1
+        assert ((cnt - exp_) ** 2 / exp_).sum() < dof + 6 * math.sqrt(2 * dof)
+    # the three coordinates are independent: the pair (v0, v1) is uniform over
+    # B x B bins of (nearly) equal size; expected counts from the exact bin sizes
+    B = 30
+    b0 = e[:, 0] * B // P
+    b1 = (e[:, 1] - P) * B // P
+    cnt = np.bincount(b0 * B + b1, minlength=B * B).astype(float)
+    size = np.bincount(np.arange(P) * B // P, minlength=B) / P
+    exp_ = len(loc) * np.outer(size, size).ravel()
+    dof = B * B - 1
+    assert ((cnt - exp_) ** 2 / exp_).sum() < dof + 6 * math.sqrt(2 * dof)
+
+
+def test_mwhc_duplicate_rate_matches_paper_estimate(orc):
+    # Sec. 4.1: (cm/3)^3 possible edges; expected duplicate pairs m(m-1)/2 / P^3,
+    # no-duplicate probability ~ exp(-1 / (2 (c/3)^3 m)). Monte Carlo, small parts.
+    m = 200
+    info = _info(orc, orc.REGIME_MWHC, 0, m)
+    info.cells = 3 * 20  # P = 20 (forced) -> lambda ~ 2.5
+    P = 20
+    trials, dups = 200, []
+    for t in range(trials):
+        e = orc.edges_of(info, synth.u64_keys(t * m, m, 13))
+        _, c = np.unique(e, axis=0, return_counts=True)
+        dups.append(int((c * (c - 1) // 2).sum()))
+    lam = m * (m - 1) / 2 / P**3
+    mean = np.mean(dups)
+    assert abs(mean - lam) < 5 * math.sqrt(lam / trials), (mean, lam)
+    # the paper's closed form with c = 3P/m
+    cc = 3 * P / m
+    assert abs(lam - 1 / (2 * (cc / 3) ** 3 * m) * (m - 1) / m) / lam < 1e-9
+
+
+@pytest.mark.parametrize("kind,b", [(0, 8), (0, 13), (1, 8), (1, 16)])
+def test_mwhc_build_decodes_sharded(orc, kind, b):
+    # eps forced up so that 200k keys shard; every key decodes (Problem 1) or is
+    # accepted (Problem 2), and the structure is 3-partite with c = 1.23
+    n = 200_000
+    keys = synth.u64_keys(0, n, 14)
+    vals = synth.values(n, b, 14) if kind == 0 else None
+    p = orc.default_params(kind=kind, b=b, mode=orc.MODE_MWHC, eps=0.05, eta=1e-3, seed=3)
+    st, info, data = orc.build(p, keys, vals)
+    assert st == orc.OK and info.regime == orc.REGIME_MWHC and info.h >= 1
+    assert info.peeled == info.n_eff == n and info.core == 0
+    q = orc.query(info, data, keys)
+    assert (q == vals).all() if kind == 0 else q.all()
+    if kind == 1:
+        other = orc.query(info, data, synth.u64_keys(n, 200_000, 14))
+        pr = 2.0 ** -b
+        assert abs(other.mean() - pr) < 5 * math.sqrt(pr * (1 - pr) / 200_000) + 1e-9
