@@ -35,7 +35,7 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 
 WORKLOADS = {
-    # name: (kind, b, n, key kind, description[, forced mode])
+    # name: (kind, b, n, key kind, description[, parameter overrides])
     "c2": ("filter", 8, 100_000_000, "u64",
            "VFilter n=1e8 uniform 64-bit keys, b=8, fuse graphs (eps-cost sharding h=3); "
            "query 1e8 members + 1e8 disjoint keys"),
@@ -51,7 +51,11 @@ WORKLOADS = {
            "uniform 64-bit keys (b=8) generated on the device in chunks and built by shard group"),
     "c3": ("func", 16, 10_000_000, "bytes",
            "VFunc n=1e7 byte strings (length 8..64), 16-bit values, LGE regime shards; "
-           "query 1e7 members + 1e7 disjoint strings", "lge"),
+           "query 1e7 members + 1e7 disjoint strings", {"mode": "lge"}),
+    "mwhc": ("filter", 8, 100_000_000, "u64",
+             "VFilter n=1e8 uniform 64-bit keys, b=8, MWHC construction (3-partite random 3-hypergraphs, "
+             "c=1.23, eps=0.01, eta=1e-3: 64 shards); query 1e8 members + 1e8 disjoint keys",
+             {"mode": "mwhc", "eps": 0.01, "eta": 1e-3}),
 }
 
 # Algorithmic DRAM bytes per unit for each phase kernel (unit: key, edge or query).
@@ -69,6 +73,16 @@ ALGO_BYTES = {
     "lge": lambda b, kind: 8.0 + 8.0 * 3,                               # per key, shard state on chip (lower bound)
     "query": lambda b, kind: 8.0 + 3 * 32.0 + 1.0,                      # key, 3 cell sectors, output
 }
+
+
+def apply_overrides(p, workload, mod):
+    """Parameter overrides of a workload (mode by name, eps, eta) on a params struct."""
+    ov = WORKLOADS[workload][5] if len(WORKLOADS[workload]) > 5 else {}
+    for k, v in ov.items():
+        if k == "mode":
+            p.mode = {"lge": mod.MODE_LGE, "fuse": mod.MODE_FUSE, "mwhc": mod.MODE_MWHC}[v]
+        else:
+            setattr(p, k, v)
 
 
 def peaks():
@@ -184,8 +198,7 @@ def run_gpu(args):
     kind, b, n, keys, offs, vals, other, ooffs = make_inputs(args.workload, 0x5EED + rank, args.n)
     p = vf.vf_params_default(kind=vf.FILTER if kind == "filter" else vf.FUNC, b=b,
                              key_kind=vf.KEYS_BYTES if offs is not None else vf.KEYS_U64, seed=1 + rank)
-    if len(WORKLOADS[args.workload]) > 5:
-        p.mode = vf.MODE_LGE
+    apply_overrides(p, args.workload, vf)
     kd, vd, od, xd, xo = (to_dev(a, torch) for a in (keys, vals, offs, other, ooffs))
     stream = torch.cuda.current_stream()
 
@@ -359,7 +372,7 @@ TRAFFIC = {("c2", "query"): round(198.56e6 / 2e7 * 1e8)}
 def oracle_sample(workload: str, quick: bool):
     """Bounded sample of the workload for the single-thread oracle."""
     kind, b, n, kk = WORKLOADS[workload][:4]
-    if len(WORKLOADS[workload]) > 5:
+    if len(WORKLOADS[workload]) > 5 and WORKLOADS[workload][5].get("mode") == "lge":
         # plain Gaussian elimination of every 2-core is cubic: a few shards only
         return kind, b, min(n, 40_000), kk
     ns = min(n, 4_000_000 if quick else 8_000_000)
@@ -380,8 +393,7 @@ def cpu_baseline(workload: str, quick: bool = True):
     vals = synth.values(ns, b, 3) if kind == "func" else None
     p = O.default_params(kind=O.FILTER if kind == "filter" else O.FUNC, b=b,
                          key_kind=O.KEYS_BYTES if offs is not None else O.KEYS_U64, seed=1)
-    if len(WORKLOADS[workload]) > 5:
-        p.mode = O.MODE_LGE
+    apply_overrides(p, workload, O)
     t0 = time.perf_counter()
     st, info, data = O.build(p, keys, vals, offsets=offs)
     t1 = time.perf_counter()

@@ -47,8 +47,8 @@ typedef enum {
 
 enum { VF_FUNC = 0, VF_FILTER = 1 };
 enum { VF_KEYS_U64 = 0, VF_KEYS_BYTES = 1 };
-enum { VF_MODE_AUTO = 0, VF_MODE_FUSE = 1, VF_MODE_LGE = 2 };
-enum { VF_REGIME_FUSE = 1, VF_REGIME_LGE = 2 };
+enum { VF_MODE_AUTO = 0, VF_MODE_FUSE = 1, VF_MODE_LGE = 2, VF_MODE_MWHC = 3 };
+enum { VF_REGIME_FUSE = 1, VF_REGIME_LGE = 2, VF_REGIME_MWHC = 3 };
 /* Fuse-regime solver. Both peel the same hypergraph (Sec. 4.3) and give the
  * same query results; they differ in how the work is scheduled on the GPU.
  * VF_SOLVER_FLOW: asynchronous worklist peeling that records peeled edges in
@@ -64,11 +64,16 @@ typedef struct {
                                 a filter's false-positive rate is 2^-b (Sec. 3.1) */
     int key_kind;            /* VF_KEYS_U64 or VF_KEYS_BYTES */
     int mode;                /* VF_MODE_AUTO: LGE regime below lge_threshold keys, fuse
-                                regime above (Sec. 4.2); or force one regime */
+                                regime above (Sec. 4.2); or force one regime.
+                                VF_MODE_MWHC: the MWHC construction (Sec. 4.1):
+                                3-partite random 3-hypergraphs, c = 1.23, shard bits
+                                min(eq. logballsbins, eq. dupmwhc); the paper's
+                                configuration uses eps = 0.01, eta = 0.001 */
     int max_retries;         /* a failed attempt restarts everything with seed+1 (Sec. 4) */
     uint64_t seed;           /* global seed; there is no per-shard seed (Sec. 4) */
     double eps;              /* epsilon of epsilon-cost sharding, eq. (ballsbins); 0.001 */
-    double eta;              /* duplicate-edge budget of eq. (logdupfuse); 0.1 */
+    double eta;              /* duplicate-edge budget of eq. (logdupfuse) (0.1) or of
+                                eq. (dupmwhc) in MWHC mode */
     uint64_t lge_threshold;  /* 800000 keys (Sec. 4.2) */
     uint64_t lge_target;     /* LGE regime: shard bits chosen so mean shard <= this (16384) */
     uint64_t lge_max_shard;  /* LGE regime: shard bits grow until no shard exceeds this
@@ -82,10 +87,12 @@ typedef struct {
     uint64_t n_eff;          /* keys solved (a filter drops duplicate local signatures) */
     int kind, b, regime;     /* regime: VF_REGIME_FUSE or VF_REGIME_LGE */
     int h;                   /* shard bits: 2^h shards on the top signature bits (Sec. 4) */
-    int h_bb, h_dup;         /* eq. (logballsbins) and eq. (logdupfuse); -1 in LGE regime */
+    int h_bb, h_dup;         /* eq. (logballsbins) and eq. (logdupfuse) / eq. (dupmwhc);
+                                -1 in LGE regime */
     uint64_t shards;
     uint64_t M;              /* keys in the largest shard; every shard gets cells for M */
-    double c;                /* expansion factor: 1.105 (large sharded fuse) or 1.12 */
+    double c;                /* expansion factor: 1.105 (large sharded fuse), 1.12, or
+                                1.23 (MWHC: cells = 3 parts of cells / 3) */
     int lg_seg;              /* fuse: log2 of the segment size (eq. nln or eq. ln) */
     uint64_t seg, l, T;      /* fuse: segment size, start segments, segments (l = T - 2) */
     uint64_t cells;          /* cells per shard; shard s owns cells [s*cells, (s+1)*cells) */

@@ -23,8 +23,8 @@ lib_path = os.path.join(HERE, "libvfunc.so")
 
 FUNC, FILTER = 0, 1
 KEYS_U64, KEYS_BYTES = 0, 1
-MODE_AUTO, MODE_FUSE, MODE_LGE = 0, 1, 2
-REGIME_FUSE, REGIME_LGE = 1, 2
+MODE_AUTO, MODE_FUSE, MODE_LGE, MODE_MWHC = 0, 1, 2, 3
+REGIME_FUSE, REGIME_LGE, REGIME_MWHC = 1, 2, 3
 SOLVER_FLOW, SOLVER_ROUNDS = 0, 1
 STATUS = {0: "VF_OK", 1: "VF_EINVAL", 2: "VF_ENOMEM", 3: "VF_EBUILD", 4: "VF_EDUP", 5: "VF_ETIMEOUT",
           6: "VF_ECUDA", 7: "VF_ECAPACITY"}

@@ -167,7 +167,23 @@ int h_dupfuse(uint64_t n, double eta, double c) {
     return h > 0 ? int(h) : 0;
 }
 
+// eq. (dupmwhc): S <= sqrt(-2 n (c/3)^3 ln(1 - eta)), S = 2^h.
+int h_dupmwhc(uint64_t n, double eta, double c) {
+    const double s = std::sqrt(-2.0 * double(n) * std::pow(c / 3.0, 3.0) * std::log(1.0 - eta));
+    if (!(s >= 1.0)) return 0;
+    return int(std::floor(std::log2(s)));
+}
+
 void plan_h(const vf_params& p, uint64_t n, vf_info& in) {
+    if (p.mode == VF_MODE_MWHC) {
+        // Sec. 4.1: random 3-hypergraphs, c = 1.23; eq. (dupmwhc) combined with
+        // eq. (logballsbins) by taking the smaller bound
+        in.regime = VF_REGIME_MWHC;
+        in.h_bb = h_ballsbins(n, p.eps);
+        in.h_dup = h_dupmwhc(n, p.eta, 1.23);
+        in.h = std::min(in.h_bb, in.h_dup);
+        return;
+    }
     const bool lge = p.mode == VF_MODE_LGE || (p.mode == VF_MODE_AUTO && n < p.lge_threshold);
     in.regime = lge ? VF_REGIME_LGE : VF_REGIME_FUSE;
     if (!lge) {
@@ -186,7 +202,14 @@ void plan_h(const vf_params& p, uint64_t n, vf_info& in) {
 // 10^7 keys; otherwise c = 1.12 (eq. (ln) segments in the fuse regime).
 void geometry(vf_info& in) {
     const double Mf = double(in.M > 0 ? in.M : 1);
-    if (in.regime == VF_REGIME_LGE) {
+    if (in.regime == VF_REGIME_MWHC) {
+        // k-partite 3-hypergraph: three parts of ceil(c M / 3) cells, at least 16
+        in.c = 1.23;
+        in.lg_seg = 0;
+        in.seg = in.l = in.T = 0;
+        const uint64_t part = uint64_t(std::ceil(in.c * Mf / 3.0));
+        in.cells = 3 * std::max<uint64_t>(part, 16);
+    } else if (in.regime == VF_REGIME_LGE) {
         in.c = 1.12;
         in.lg_seg = 0;
         in.seg = in.l = in.T = 0;
@@ -222,7 +245,7 @@ vf::Geom make_geom(const vf_info& in) {
     g.kh = vf::mix64(in.seed ^ vf::kLaneHi);
     g.kl = vf::mix64(in.seed ^ vf::kLaneLo);
     g.cells = in.cells;
-    g.span = in.l * in.seg;
+    g.span = in.regime == VF_REGIME_MWHC ? in.cells / 3 : in.l * in.seg;
     g.lg_seg = in.lg_seg;
     g.h = in.h;
     g.regime = in.regime;
@@ -685,7 +708,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     for (uint32_t j = 0; j < P; j++) {
         vf_info& in = info[j];
         geometry(in);
-        if ((in.regime == VF_REGIME_FUSE && in.M >= (uint64_t(1) << 27)) || in.total_cells >= (uint64_t(1) << 32)) {
+        if ((in.regime != VF_REGIME_LGE && in.M >= (uint64_t(1) << 27)) || in.total_cells >= (uint64_t(1) << 32)) {
             free_data();
             return fail(VF_ECAPACITY, "batched structure exceeds a size limit");
         }
@@ -797,7 +820,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
         if (info[j].regime == VF_REGIME_LGE) info[j].n_eff -= dups[j];
     // fuse-regime structures (above the threshold): one solver each
     for (uint32_t j = 0; j < P; j++) {
-        if (info[j].regime != VF_REGIME_FUSE) continue;
+        if (info[j].regime == VF_REGIME_LGE) continue;  // fuse and MWHC: the peeling solvers
         std::vector<unsigned long long> start(info[j].shards + 1, 0);
         for (uint64_t s2 = 0; s2 < info[j].shards; s2++) start[s2 + 1] = start[s2] + counts[hist_off[j] + s2];
         DevBuf dstart;
@@ -874,6 +897,7 @@ const char* vf_last_error(void) { return g_last_error.c_str(); }
 
 vf_status vf_plan(const vf_params* p, uint64_t n, uint64_t M, vf_info* out) {
     if (!p || !out) return fail(VF_EINVAL, "vf_plan: NULL argument");
+    if (p->mode < VF_MODE_AUTO || p->mode > VF_MODE_MWHC) return fail(VF_EINVAL, "vf_plan: bad mode");
     vf_info in;
     std::memset(&in, 0, sizeof in);
     in.n = in.n_eff = n;
@@ -901,13 +925,13 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
     if (p.key_kind == VF_KEYS_BYTES && !offsets) return fail(VF_EINVAL, "offsets is NULL");
     if (p.kind == VF_FUNC && n > 0 && !values) return fail(VF_EINVAL, "a function needs values");
     if (!(p.eps > 0.0) || !(p.eta > 0.0 && p.eta < 1.0) || p.max_retries < 0 || p.lge_target == 0 ||
-        p.lge_max_shard < 2)
-        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes");
-    // More than 2^30 keys: only 64-bit keys in the fuse regime, built one shard
-    // group (<= 2^30 keys) at a time.
+        p.lge_max_shard < 2 || p.mode < VF_MODE_AUTO || p.mode > VF_MODE_MWHC)
+        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes / mode");
+    // More than 2^30 keys: only 64-bit keys in the fuse or MWHC regime, built
+    // one shard group (<= 2^30 keys) at a time.
     const bool big = n > (uint64_t(1) << 30);
     if (big && (p.key_kind != VF_KEYS_U64 || p.mode == VF_MODE_LGE || n < p.lge_threshold || n > (uint64_t(1) << 36)))
-        return fail(VF_ECAPACITY, "above 2^30 keys: 64-bit keys, fuse regime, at most 2^36 keys");
+        return fail(VF_ECAPACITY, "above 2^30 keys: 64-bit keys, fuse or MWHC regime, at most 2^36 keys");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     VF_CK(cudaGetDevice(&dev));
@@ -962,8 +986,8 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
             break;
         }
         geometry(in);
-        if (in.regime == VF_REGIME_FUSE && in.M >= (uint64_t(1) << 27))
-            return fail(VF_ECAPACITY, "fuse shard above 2^27 keys");
+        if (in.regime != VF_REGIME_LGE && in.M >= (uint64_t(1) << 27))
+            return fail(VF_ECAPACITY, "fuse / MWHC shard above 2^27 keys");
         if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard)
             return fail(VF_ECAPACITY, "LGE shard above lge_max_shard");
         const vf::Geom g = make_geom(in);
@@ -982,7 +1006,7 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
             }
             group.push_back(uint32_t(in.shards));
         }
-        if (group.size() > 2 && in.regime != VF_REGIME_FUSE)
+        if (group.size() > 2 && in.regime == VF_REGIME_LGE)
             return fail(VF_ECAPACITY, "more than 2^30 keys or 2^32 cells in the LGE regime");
         uint64_t group_max = 0;
         for (size_t k = 0; k + 1 < group.size(); k++) {
@@ -1021,7 +1045,7 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
                                          g0s, g1s, st));
             }
             uint64_t pe = 0, co = 0, ro = 0, dr = 0;
-            if (in.regime == VF_REGIME_FUSE)
+            if (in.regime != VF_REGIME_LGE)  // fuse graphs and MWHC hypergraphs peel the same way
                 rs = solve_fuse(gi, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
                                 startb.as<unsigned long long>(), data.as<uint8_t>(), st, &pe, &ro,
                                 p.fuse_solver, &dr, uint64_t(g0s) * in.cells);
@@ -1036,7 +1060,7 @@ vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values
         in.peeled = peeled;
         const uint64_t n_all = in.n_eff;
         in.n_eff = n_all - dropped;
-        in.core = in.regime == VF_REGIME_FUSE ? 0 : core;
+        in.core = in.regime == VF_REGIME_LGE ? core : 0;
         in.rounds = rounds;
         if (rs == VF_OK) {
             VF_CK(cudaStreamSynchronize(st));
@@ -1199,6 +1223,8 @@ vf_status vf_build_batch(const vf_batch_item* items, uint32_t count, const vf_pa
                          const vf_batch_opts* opts, void* stream, vf_struct** out) {
     g_last_error.clear();
     if (!common || !out || (count > 0 && !items)) return fail(VF_EINVAL, "vf_build_batch: NULL argument");
+    if (common->mode < VF_MODE_AUTO || common->mode > VF_MODE_MWHC)
+        return fail(VF_EINVAL, "vf_build_batch: bad mode");
     vf_batch_opts o;
     if (opts) o = *opts; else vf_batch_opts_default(&o);
     if (o.lge_target == 0) return fail(VF_EINVAL, "vf_build_batch: lge_target must be positive");

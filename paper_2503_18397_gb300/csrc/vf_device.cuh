@@ -18,6 +18,7 @@ constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 
 constexpr int kRegimeFuse = 1;
 constexpr int kRegimeLge = 2;
+constexpr int kRegimeMwhc = 3;
 
 // Status bits written by kernels into a device word.
 constexpr uint32_t kErrDegOverflow = 1u << 0;   // a vertex exceeded 31 incident edges
@@ -41,7 +42,7 @@ __device__ __forceinline__ uint64_t mulhi(uint64_t a, uint64_t b) { return __umu
 struct Geom {
     uint64_t kh, kl;      // lane keys: mix64(seed ^ kLaneHi), mix64(seed ^ kLaneLo)
     uint64_t cells;       // cells per shard
-    uint64_t span;        // fuse: l * seg (range of the first vertex)
+    uint64_t span;        // fuse: l * seg (range of the first vertex); MWHC: vertices per part
     int32_t lg_seg;       // fuse: log2 segment size
     int32_t h;            // shard bits
     int32_t regime;
@@ -122,6 +123,12 @@ __device__ __forceinline__ void edge_of(const Geom& g, uint64_t local, uint64_t 
         v[0] = v0;
         v[1] = ((s + 1) << g.lg_seg) + (r & mask);
         v[2] = ((s + 2) << g.lg_seg) + ((r >> 32) & mask);
+    } else if (g.regime == kRegimeMwhc) {
+        // MWHC (Sec. 4.1, k-partite): one uniform vertex in each third of the shard
+        const uint64_t P = g.span;
+        v[0] = mulhi(local, P);
+        v[1] = P + mulhi(mix64(local ^ kEdgeSalt), P);
+        v[2] = 2 * P + mulhi(mix64(local ^ kEdgeSalt2), P);
     } else {
         uint64_t V = g.cells;
         uint64_t r = mix64(local ^ kEdgeSalt);

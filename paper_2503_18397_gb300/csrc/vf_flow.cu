@@ -546,6 +546,7 @@ cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned l
 constexpr uint32_t kBatchHotMB = 16;
 
 static uint32_t shards_per_batch(const FlowArgs& a) {
+    if (a.g.regime != kRegimeFuse) return a.S;  // random hypergraphs peel in a few levels, no wave
     const uint64_t seg = uint64_t(1) << a.g.lg_seg;
     const uint64_t hot = 2 * 4 * seg * 4;  // bytes per shard
     const uint64_t k = (uint64_t(kBatchHotMB) << 20) / hot;
@@ -582,7 +583,7 @@ cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st) {
 
 cudaError_t launch_tile_order(uint64_t* loc, uint32_t* val, uint64_t n, const unsigned long long* start,
                               uint32_t S, const Geom& g, cudaStream_t st) {
-    if (n == 0) return cudaSuccess;
+    if (n == 0 || g.regime != kRegimeFuse) return cudaSuccess;  // only fuse graphs have segments
     const uint32_t l = uint32_t(g.span >> g.lg_seg);
     uint32_t sshift = 0;
     while (((l - 1) >> sshift) + 1 > kTileBins / 2) sshift++;

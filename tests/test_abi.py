@@ -85,3 +85,22 @@ def test_plan_forced_regimes(vf, orc):
             assert info.h == h and info.regime == regime
             for f in FIELDS:
                 assert getattr(info, f) == getattr(g, f)
+
+
+def test_plan_matches_oracle_mwhc(vf, orc):
+    # MWHC mode (Sec. 4.1): shard bits from eq. (logballsbins) and eq. (dupmwhc),
+    # 3-partite geometry with c = 1.23, for the paper's eps/eta and the defaults
+    rng = np.random.default_rng(1)
+    ns = sorted(set([0, 1, 2, 3, 47, 1000, 10**6, 10**8, 10**12] + [int(10 ** x) for x in rng.uniform(0, 13, 200)]))
+    for eps, eta in ((0.01, 1e-3), (0.001, 0.1), (0.05, 0.5)):
+        for n in ns:
+            info, (h, regime, h_bb, h_dup), _ = _plan_pair(vf, orc, n, 1, mode=vf.MODE_MWHC, eps=eps, eta=eta)
+            assert info.regime == regime == vf.REGIME_MWHC
+            assert (info.h, info.h_bb, info.h_dup) == (h, h_bb, h_dup), (n, eps, eta)
+            M = int(n / (1 << h) + math.sqrt(max(n / (1 << h), 1)) * 3)
+            info, _, g = _plan_pair(vf, orc, n, M, mode=vf.MODE_MWHC, eps=eps, eta=eta)
+            for f in FIELDS:
+                assert getattr(info, f) == getattr(g, f), (n, f)
+    p = vf.vf_params_default(mode=7)
+    with pytest.raises(vf.VFError):
+        vf.vf_plan(10, 10, p)

@@ -215,6 +215,57 @@ def test_retries_match_oracle(vf, orc, solver):
     assert retried > 0
 
 
+# ---------------------------------------------------------------- MWHC (Sec. 4.1)
+
+@SOLVERS
+@pytest.mark.parametrize("b", [1, 8, 13, 32])
+def test_mwhc_function(vf, orc, b, solver):
+    n = 300_000
+    keys = synth.u64_keys(0, n, 41)
+    vals = synth.values(n, b, 41)
+    s, info, _ = check_build(vf, orc, keys, vals, b=b, mode=vf.MODE_MWHC, eps=0.01, eta=1e-3, seed=2,
+                             n_other=50_000, fuse_solver=solver)
+    assert info.regime == vf.REGIME_MWHC and info.c == 1.23 and info.cells % 3 == 0
+
+
+@SOLVERS
+def test_mwhc_filter_sharded(vf, orc, solver):
+    n = 2_000_000
+    keys = synth.u64_keys(0, n, 42)
+    s, info, _ = check_build(vf, orc, keys, None, b=8, mode=vf.MODE_MWHC, eps=0.01, eta=1e-3, seed=9,
+                             n_other=200_000, fuse_solver=solver)
+    assert info.h == 4 and info.regime == vf.REGIME_MWHC
+    other = synth.u64_keys(n, 400_000, 42)
+    fpr = host(s.query(dev(other))).mean()
+    assert abs(fpr - 2.0**-8) < 5 * math.sqrt(2.0**-8 / len(other))
+
+
+def test_mwhc_byte_strings_and_duplicates(vf, orc):
+    data, offs = synth.byte_strings(0, 400_000, 43)
+    vals = synth.values(400_000, 16, 43)
+    check_build(vf, orc, data, vals, offsets=offs, b=16, mode=vf.MODE_MWHC, eps=0.05, eta=1e-3, seed=1,
+                n_other=30_000)
+    keys = with_repeats(200_000, 0.02, 44)
+    s, info, oi = check_build(vf, orc, keys, None, mode=vf.MODE_MWHC, eps=0.05, eta=1e-3, seed=5, n_other=0)
+    assert info.n_eff == oi.n_eff == 200_000
+
+
+@SOLVERS
+def test_mwhc_retries_match_oracle(vf, orc, solver):
+    # 256 shards of ~1560 keys: at this size c = 1.23 leaves a 2-core or a
+    # duplicate edge in some shard most of the time, so attempts are retried; the
+    # GPU fails exactly when the oracle does (every seed here needs 3..8 retries)
+    keys = synth.u64_keys(0, 400_000, 45)
+    vals = synth.values(400_000, 8, 45)
+    retried = 0
+    for seed in range(4):
+        s, info, oi = check_build(vf, orc, keys, vals, mode=vf.MODE_MWHC, eps=0.5, eta=0.9, seed=seed,
+                                  max_retries=30, n_other=0, fuse_solver=solver)
+        assert info.h == 8
+        retried += info.retries > 0
+    assert retried > 0
+
+
 def with_repeats(n, frac, seed, triples=False):
     """n distinct keys plus copies of a random subset (a few in triplicate), shuffled."""
     keys = synth.u64_keys(0, n, seed)
