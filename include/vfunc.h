@@ -42,7 +42,9 @@ typedef enum {
     VF_EDUP = 4,      /* duplicate keys with different values make a function impossible */
     VF_ETIMEOUT = 5,  /* a bounded device-side wait gave up; results are invalid */
     VF_ECUDA = 6,     /* a CUDA runtime call failed */
-    VF_ECAPACITY = 7  /* a size exceeds a documented limit of this implementation */
+    VF_ECAPACITY = 7, /* a size exceeds a documented limit of this implementation */
+    VF_EAGAIN = 8,    /* vf_build_resumable stopped after max_groups shard groups; call again */
+    VF_EIO = 9        /* a file could not be read or written, or is not a valid serialized form */
 } vf_status;
 
 enum { VF_FUNC = 0, VF_FILTER = 1 };
@@ -124,6 +126,35 @@ void vf_params_default(vf_params *p);
  * the LGE regime). */
 vf_status vf_build(const void *keys, const uint64_t *offsets, const void *values, uint64_t n,
                    const vf_params *params, void *stream, vf_struct **out);
+
+/* Resumable build (Sec. 6: shards are built one group of consecutive shards
+ * at a time). Builds exactly what vf_build builds from the same arguments, in
+ * shard groups of at most group_keys keys (0: 2^30), writing every finished
+ * group into the file `checkpoint` (the serialized form below, with a header
+ * field counting the groups written). With max_groups > 0 a call returns
+ * VF_EAGAIN after writing that many groups; a later call with the same keys,
+ * values and parameters continues from the file (same seed, same shard
+ * histogram, same parameters; anything else starts the file afresh). On
+ * VF_OK the file holds the complete structure (vf_load reads it) and *out is
+ * the structure. A failed attempt (seed) restarts the file with seed+1.
+ * Errors: those of vf_build, VF_EAGAIN, VF_EIO. */
+vf_status vf_build_resumable(const void *keys, const uint64_t *offsets, const void *values, uint64_t n,
+                             const vf_params *params, const char *checkpoint, uint64_t group_keys,
+                             uint32_t max_groups, void *stream, vf_struct **out);
+
+/* Serialized form: a 4096-byte header of little-endian fields (magic
+ * "VFSTORE1", version 1, the vf_info of the build, group progress, digests)
+ * followed at byte 4096 by the data array in its device layout (shard s owns
+ * cells [s*cells, (s+1)*cells); b in {8,16,32} native, else a bit array plus
+ * one pad word), so a file can be mapped and its cells read in place.
+ * vf_serialize writes 4096 + data_bytes bytes into host memory `buf` (with
+ * buf == NULL only *size is set; a smaller capacity is VF_EINVAL).
+ * vf_deserialize / vf_load validate the header (VF_EIO if corrupt, foreign or
+ * incomplete) and copy the cells to a new structure on the current device. */
+vf_status vf_serialize(const vf_struct *s, void *buf, uint64_t capacity, uint64_t *size);
+vf_status vf_deserialize(const void *buf, uint64_t size, void *stream, vf_struct **out);
+vf_status vf_save(const vf_struct *s, const char *path);
+vf_status vf_load(const char *path, void *stream, vf_struct **out);
 
 /* Query m keys (eq. MWHC with k = 3): shard from the top signature bits, cell
  * offset shard*cells with no offset array (Sec. 4), XOR of three cells; a

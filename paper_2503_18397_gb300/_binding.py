@@ -27,7 +27,8 @@ MODE_AUTO, MODE_FUSE, MODE_LGE, MODE_MWHC = 0, 1, 2, 3
 REGIME_FUSE, REGIME_LGE, REGIME_MWHC = 1, 2, 3
 SOLVER_FLOW, SOLVER_ROUNDS = 0, 1
 STATUS = {0: "VF_OK", 1: "VF_EINVAL", 2: "VF_ENOMEM", 3: "VF_EBUILD", 4: "VF_EDUP", 5: "VF_ETIMEOUT",
-          6: "VF_ECUDA", 7: "VF_ECAPACITY"}
+          6: "VF_ECUDA", 7: "VF_ECAPACITY", 8: "VF_EAGAIN", 9: "VF_EIO"}
+EAGAIN, EIO = 8, 9
 
 
 class VFError(RuntimeError):
@@ -113,6 +114,14 @@ def lib():
         L.vf_query_batch.restype = C.c_int
         L.vf_timing_enable.argtypes = [i32]
         L.vf_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(u64)]
+        L.vf_build_resumable.argtypes = [vp, vp, vp, u64, C.POINTER(VfParams), C.c_char_p, u64, C.c_uint32, vp,
+                                         C.POINTER(vp)]
+        L.vf_serialize.argtypes = [vp, vp, u64, C.POINTER(u64)]
+        L.vf_deserialize.argtypes = [vp, u64, vp, C.POINTER(vp)]
+        L.vf_save.argtypes = [vp, C.c_char_p]
+        L.vf_load.argtypes = [C.c_char_p, vp, C.POINTER(vp)]
+        for name in ("vf_build_resumable", "vf_serialize", "vf_deserialize", "vf_save", "vf_load"):
+            getattr(L, name).restype = C.c_int
         L.vf_last_error.argtypes = []
         L.vf_last_error.restype = C.c_char_p
         for name in ("vf_build", "vf_query", "vf_get_info", "vf_plan", "vf_data", "vf_export", "vf_signatures",
@@ -208,6 +217,54 @@ def vf_build(keys, values=None, *, offsets=None, params: VfParams | None = None,
     out = C.c_void_p()
     _check(lib().vf_build(_ptr(keys), _ptr(offsets), _ptr(values), n, C.byref(params),
                           _stream(stream, keys, values, offsets), C.byref(out)))
+    return Structure(out.value)
+
+
+def vf_build_resumable(keys, values=None, *, checkpoint: str, offsets=None, params: VfParams | None = None,
+                       group_keys: int = 0, max_groups: int = 0, stream=None, **overrides):
+    """vf_build in shard groups checkpointed to `checkpoint`. Returns the Structure
+    when complete, or None when max_groups groups were written and the build is
+    to be resumed by calling again with the same arguments."""
+    if params is None:
+        params = vf_params_default()
+        params.kind = FUNC if values is not None else FILTER
+        params.key_kind = KEYS_BYTES if offsets is not None else KEYS_U64
+    for k, v in overrides.items():
+        setattr(params, k, v)
+    n = _len(keys, offsets)
+    out = C.c_void_p()
+    st = lib().vf_build_resumable(_ptr(keys), _ptr(offsets), _ptr(values), n, C.byref(params),
+                                  os.fsencode(checkpoint), group_keys, max_groups,
+                                  _stream(stream, keys, values, offsets), C.byref(out))
+    if st == EAGAIN:
+        return None
+    _check(st)
+    return Structure(out.value)
+
+
+def vf_serialize(s) -> bytes:
+    """The serialized form (4096-byte header + data array) as bytes."""
+    size = C.c_uint64()
+    _check(lib().vf_serialize(s.handle, None, 0, C.byref(size)))
+    buf = (C.c_uint8 * size.value)()
+    _check(lib().vf_serialize(s.handle, buf, size.value, C.byref(size)))
+    return bytes(buf)
+
+
+def vf_deserialize(data: bytes, stream=None):
+    out = C.c_void_p()
+    buf = (C.c_uint8 * len(data)).from_buffer_copy(data)
+    _check(lib().vf_deserialize(buf, len(data), _stream(stream), C.byref(out)))
+    return Structure(out.value)
+
+
+def vf_save(s, path: str):
+    _check(lib().vf_save(s.handle, os.fsencode(path)))
+
+
+def vf_load(path: str, stream=None):
+    out = C.c_void_p()
+    _check(lib().vf_load(os.fsencode(path), _stream(stream), C.byref(out)))
     return Structure(out.value)
 
 

@@ -14,13 +14,6 @@
 
 #include "vf_internal.h"
 
-struct vf_struct {
-    vf_info info;
-    vf::Geom geom;
-    uint8_t* data;  // device, info.data_bytes (+ padding)
-    int device;
-};
-
 namespace {
 
 thread_local std::string g_last_error;
@@ -870,7 +863,341 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, vf_batch_opts> g_tune_cache;
 
+struct ResumeOpts {
+    const char* path;
+    uint64_t group_keys;
+    uint32_t max_groups;
+};
+
+uint64_t digest_words(const uint64_t* w, size_t n) {
+    uint64_t h = 0x6A09E667F3BCC908ull;
+    for (size_t i = 0; i < n; i++) h = vf::mix64(h ^ w[i]) + uint64_t(i);
+    return h;
+}
+
+// Parameters that shape the structure (the solver choice does not).
+uint64_t params_digest(const vf_params& p, uint64_t group_keys) {
+    uint64_t e, t;
+    std::memcpy(&e, &p.eps, 8);
+    std::memcpy(&t, &p.eta, 8);
+    const uint64_t w[] = {uint64_t(p.kind), uint64_t(p.b), uint64_t(p.key_kind), uint64_t(p.mode), e, t,
+                          p.lge_threshold, p.lge_target, p.lge_max_shard, group_keys};
+    return digest_words(w, sizeof w / sizeof w[0]);
+}
+
+// Byte range of the data array holding cells [c0, c1) (bit arrays: rounded
+// outward; the last group also takes the pad word).
+void cell_bytes(const vf_info& in, uint64_t c0, uint64_t c1, bool last, uint64_t* lo, uint64_t* hi) {
+    const uint64_t b = uint64_t(in.b);
+    *lo = c0 * b / 8;
+    *hi = last ? in.data_bytes : (c1 * b + 7) / 8;
+}
+
+// Checkpoint file of a resumable build: the serialized form with
+// groups_done < groups_total until the last shard group is written.
+struct Checkpoint {
+    std::FILE* f = nullptr;
+    vf::StoreHeader h{};
+    ~Checkpoint() {
+        if (f) std::fclose(f);
+    }
+    vf_status write_header() {
+        std::vector<uint8_t> buf(vf::kStoreHeaderBytes);
+        vf::store_encode(h, buf.data());
+        if (!vf::file_write_at(f, 0, buf.data(), buf.size()) || std::fflush(f) != 0)
+            return fail(VF_EIO, "checkpoint: writing the header failed");
+        return VF_OK;
+    }
+    uint64_t group_keys = 0;
+    vf_status open(const char* path, const vf_info& in, const vf_params& p, const std::vector<uint32_t>& counts,
+                   const std::vector<uint32_t>& group, uint8_t* data, cudaStream_t st, size_t* k0) {
+        std::vector<uint64_t> cw(counts.begin(), counts.end());
+        const uint64_t cd = digest_words(cw.data(), cw.size());
+        const uint64_t pd = params_digest(p, group_keys);
+        *k0 = 0;
+        f = std::fopen(path, "r+b");
+        if (f) {
+            std::vector<uint8_t> buf(vf::kStoreHeaderBytes);
+            vf::StoreHeader old;
+            const bool same = vf::file_read_at(f, 0, buf.data(), buf.size()) &&
+                              vf::store_decode(buf.data(), buf.size(), old) && old.info.seed == in.seed &&
+                              old.info.n == in.n && old.info.kind == in.kind && old.info.b == in.b &&
+                              old.info.regime == in.regime && old.info.h == in.h && old.info.M == in.M &&
+                              old.info.cells == in.cells && old.info.data_bytes == in.data_bytes &&
+                              old.counts_digest == cd && old.params_digest == pd &&
+                              old.groups_total == group.size() - 1 && old.key_kind == p.key_kind &&
+                              old.groups_done < old.groups_total;
+            if (same) {
+                h = old;
+                *k0 = size_t(h.groups_done);
+                if (*k0 > 0) {
+                    uint64_t lo, hi;
+                    cell_bytes(in, 0, uint64_t(group[*k0]) * in.cells, false, &lo, &hi);
+                    VF_CK(cudaStreamSynchronize(st));  // the data array was zeroed on `st`
+                    bool io = true;
+                    VF_CK(vf::file_to_device(f, vf::kStoreHeaderBytes, data, hi, &io));
+                    if (!io) return fail(VF_EIO, "checkpoint: reading completed shard groups failed");
+                }
+                return VF_OK;
+            }
+            std::fclose(f);
+            f = nullptr;
+        }
+        f = std::fopen(path, "w+b");
+        if (!f) return fail(VF_EIO, std::string("checkpoint: cannot create ") + path);
+        std::memset(&h, 0, sizeof h);
+        h.info = in;
+        h.info.peeled = h.info.core = h.info.rounds = 0;
+        h.groups_total = group.size() - 1;
+        h.groups_done = 0;
+        h.counts_digest = cd;
+        h.params_digest = pd;
+        h.key_kind = p.key_kind;
+        const uint8_t zero = 0;
+        if (in.data_bytes > 0 &&
+            !vf::file_write_at(f, vf::kStoreHeaderBytes + in.data_bytes - 1, &zero, 1))  // size the file
+            return fail(VF_EIO, "checkpoint: sizing the file failed");
+        return write_header();
+    }
+    vf_status save_group(const vf_info& in, const std::vector<uint32_t>& group, size_t k, const uint8_t* data,
+                         uint64_t peeled, uint64_t core, uint64_t rounds, uint64_t dropped) {
+        uint64_t lo, hi;
+        cell_bytes(in, uint64_t(group[k]) * in.cells, uint64_t(group[k + 1]) * in.cells, k + 2 == group.size(), &lo,
+                   &hi);
+        bool io = true;
+        VF_CK(vf::device_to_file(f, vf::kStoreHeaderBytes + lo, data + lo, hi - lo, &io));
+        if (!io) return fail(VF_EIO, "checkpoint: writing a shard group failed");
+        h.groups_done = k + 1;
+        h.info.peeled = peeled, h.info.core = core, h.info.rounds = rounds;
+        h.dropped = dropped;
+        return write_header();
+    }
+    vf_status finish(const vf_info& in) {
+        h.info = in;
+        return write_header();
+    }
+};
+
+// The attempt (seed - params.seed) an unfinished checkpoint of this build was
+// written by, or 0: every call of a resumable build starts there, so the
+// progress of a retried attempt is not lost.
+int checkpoint_attempt(const ResumeOpts* ro, const vf_params& p, uint64_t n) {
+    std::FILE* f = std::fopen(ro->path, "rb");
+    if (!f) return 0;
+    std::vector<uint8_t> buf(vf::kStoreHeaderBytes);
+    vf::StoreHeader h;
+    int a = 0;
+    if (vf::file_read_at(f, 0, buf.data(), buf.size()) && vf::store_decode(buf.data(), buf.size(), h) &&
+        h.groups_done < h.groups_total && h.info.n == n && h.key_kind == p.key_kind &&
+        h.params_digest == params_digest(p, ro->group_keys) && h.info.seed >= p.seed &&
+        h.info.seed - p.seed <= uint64_t(p.max_retries))
+        a = int(h.info.seed - p.seed);
+    std::fclose(f);
+    return a;
+}
+
+vf_status build_impl(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
+                     const vf_params* params, void* stream, vf_struct** out, const ResumeOpts* ro);
+
+vf_status build_impl(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
+                     const vf_params* params, void* stream, vf_struct** out, const ResumeOpts* ro) {
+    g_last_error.clear();
+    if (!params || !out) return fail(VF_EINVAL, "vf_build: NULL params or out");
+    *out = nullptr;
+    const vf_params p = *params;
+    if (p.b < 1 || p.b > 32) return fail(VF_EINVAL, "b must be in 1..32");
+    if (p.kind != VF_FUNC && p.kind != VF_FILTER) return fail(VF_EINVAL, "bad kind");
+    if (p.key_kind != VF_KEYS_U64 && p.key_kind != VF_KEYS_BYTES) return fail(VF_EINVAL, "bad key_kind");
+    if (n > 0 && !keys) return fail(VF_EINVAL, "keys is NULL");
+    if (p.key_kind == VF_KEYS_BYTES && !offsets) return fail(VF_EINVAL, "offsets is NULL");
+    if (p.kind == VF_FUNC && n > 0 && !values) return fail(VF_EINVAL, "a function needs values");
+    if (!(p.eps > 0.0) || !(p.eta > 0.0 && p.eta < 1.0) || p.max_retries < 0 || p.lge_target == 0 ||
+        p.lge_max_shard < 2 || p.mode < VF_MODE_AUTO || p.mode > VF_MODE_MWHC)
+        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes / mode");
+    // More than 2^30 keys: only 64-bit keys in the fuse or MWHC regime, built
+    // one shard group (<= 2^30 keys) at a time.
+    const bool big = n > (uint64_t(1) << 30);
+    if (big && (p.key_kind != VF_KEYS_U64 || p.mode == VF_MODE_LGE || n < p.lge_threshold || n > (uint64_t(1) << 36)))
+        return fail(VF_ECAPACITY, "above 2^30 keys: 64-bit keys, fuse or MWHC regime, at most 2^36 keys");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    VF_CK(cudaGetDevice(&dev));
+    keep_pool_warm(dev);
+
+    Staged in_keys;
+    vf_status rs = stage_keys(p.key_kind, keys, offsets, n, st, in_keys);
+    if (rs != VF_OK) return rs;
+    const void* vals_dev = nullptr;
+    if (p.kind == VF_FUNC && n > 0) {
+        if (on_device(values)) {
+            vals_dev = values;
+        } else {
+            VF_CK(in_keys.vbuf.alloc(n * value_bytes(p.b), st));
+            VF_CK(cudaMemcpyAsync(in_keys.vbuf.p, values, n * value_bytes(p.b), cudaMemcpyHostToDevice, st));
+            vals_dev = in_keys.vbuf.p;
+        }
+    }
+
+    DevBuf hist, sigs, loc, val, startb, cursor, data;
+    if (p.key_kind == VF_KEYS_BYTES) VF_CK(sigs.alloc(n * sizeof(vf::Sig), st));
+
+    vf_status last = VF_EBUILD;
+    const int first_attempt = ro ? checkpoint_attempt(ro, p, n) : 0;
+    for (int attempt = first_attempt; attempt <= p.max_retries; attempt++) {
+        vf_info in;
+        std::memset(&in, 0, sizeof in);
+        in.n = in.n_eff = n;
+        in.kind = p.kind;
+        in.b = p.b;
+        in.seed = p.seed + uint64_t(attempt);
+        in.retries = attempt;
+        plan_h(p, n, in);
+        std::vector<uint32_t> counts;
+        for (;;) {
+            in.shards = uint64_t(1) << in.h;
+            vf::Geom g0 = make_geom(in);
+            VF_CK(hist.alloc(in.shards * 4, st));
+            VF_CK(cudaMemsetAsync(hist.p, 0, in.shards * 4, st));
+            {
+                PhaseTimer t(kPhHist, st);
+                VF_CK(vf::launch_hist(p.key_kind, in_keys.keys, in_keys.offs, n, g0, hist.as<uint32_t>(),
+                                      sigs.as<vf::Sig>(), st));
+            }
+            counts.assign(in.shards, 0);
+            VF_CK(cudaMemcpyAsync(counts.data(), hist.p, in.shards * 4, cudaMemcpyDeviceToHost, st));
+            VF_CK(cudaStreamSynchronize(st));
+            in.M = *std::max_element(counts.begin(), counts.end());
+            if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard && in.h < 40) {
+                in.h++;
+                continue;
+            }
+            break;
+        }
+        geometry(in);
+        if (in.regime != VF_REGIME_LGE && in.M >= (uint64_t(1) << 27))
+            return fail(VF_ECAPACITY, "fuse / MWHC shard above 2^27 keys");
+        if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard)
+            return fail(VF_ECAPACITY, "LGE shard above lge_max_shard");
+        const vf::Geom g = make_geom(in);
+        // shard groups: consecutive shards with at most 2^30 keys (or the resumable
+        // build's group size) and 2^32 cells each
+        const uint64_t group_cap =
+            ro && ro->group_keys ? std::min<uint64_t>(ro->group_keys, uint64_t(1) << 30) : uint64_t(1) << 30;
+        std::vector<uint32_t> group{0};
+        {
+            uint64_t keys_in = 0, cells_in = 0;
+            for (uint32_t s = 0; s < in.shards; s++) {
+                if (s > group.back() && (keys_in + counts[s] > group_cap ||
+                                         cells_in + in.cells >= (uint64_t(1) << 32))) {
+                    group.push_back(s);
+                    keys_in = cells_in = 0;
+                }
+                keys_in += counts[s];
+                cells_in += in.cells;
+            }
+            group.push_back(uint32_t(in.shards));
+        }
+        if (group.size() > 2 && in.regime == VF_REGIME_LGE)
+            return fail(VF_ECAPACITY, "more than 2^30 keys or 2^32 cells in the LGE regime");
+        uint64_t group_max = 0;
+        for (size_t k = 0; k + 1 < group.size(); k++) {
+            uint64_t sum = 0;
+            for (uint32_t s = group[k]; s < group[k + 1]; s++) sum += counts[s];
+            group_max = std::max(group_max, sum);
+        }
+        if (loc.bytes < std::max<uint64_t>(group_max, 1) * 8) VF_CK(loc.alloc(std::max<uint64_t>(group_max, 1) * 8, st));
+        if (p.kind == VF_FUNC && val.bytes < std::max<uint64_t>(group_max, 1) * 4)
+            VF_CK(val.alloc(std::max<uint64_t>(group_max, 1) * 4, st));
+        VF_CK(data.alloc(in.data_bytes + 16, st));
+        VF_CK(cudaMemsetAsync(data.p, 0, in.data_bytes + 16, st));
+        VF_CK(cursor.alloc(in.shards * 8, st));
+        uint64_t peeled = 0, core = 0, rounds = 0;
+        rs = VF_OK;
+        uint64_t dropped = 0;
+        std::vector<unsigned long long> start;
+        // resumable build: continue from this attempt's checkpoint, or start one
+        Checkpoint ck;
+        size_t k0 = 0;
+        if (ro) {
+            ck.group_keys = ro->group_keys;
+            rs = ck.open(ro->path, in, p, counts, group, data.as<uint8_t>(), st, &k0);
+            if (rs != VF_OK) return rs;
+            peeled = ck.h.info.peeled, core = ck.h.info.core, rounds = ck.h.info.rounds, dropped = ck.h.dropped;
+        }
+        uint32_t groups_here = 0;
+        for (size_t k = k0; k + 1 < group.size() && rs == VF_OK; k++) {
+            const uint32_t g0s = group[k], g1s = group[k + 1];
+            vf_info gi = in;
+            gi.shards = g1s - g0s;
+            start.assign(gi.shards + 1, 0);
+            for (uint32_t s = g0s; s < g1s; s++) start[s - g0s + 1] = start[s - g0s] + counts[s];
+            gi.n_eff = start[gi.shards];
+            gi.total_cells = gi.shards * in.cells;
+            // cursors of the group's shards start at the group-local shard starts
+            std::vector<unsigned long long> cur(in.shards, 0);
+            for (uint32_t s = g0s; s < g1s; s++) cur[s] = start[s - g0s];
+            VF_CK(cudaMemcpyAsync(cursor.p, cur.data(), in.shards * 8, cudaMemcpyHostToDevice, st));
+            rs = h2d(startb, start, st);
+            if (rs != VF_OK) return rs;
+            {
+                PhaseTimer t(kPhScatter, st);
+                VF_CK(vf::launch_scatter(static_cast<const uint64_t*>(in_keys.keys), sigs.as<vf::Sig>(), vals_dev, n,
+                                         g, cursor.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(),
+                                         g0s, g1s, st));
+            }
+            uint64_t pe = 0, co = 0, rn = 0, dr = 0;
+            if (in.regime != VF_REGIME_LGE)  // fuse graphs and MWHC hypergraphs peel the same way
+                rs = solve_fuse(gi, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
+                                startb.as<unsigned long long>(), data.as<uint8_t>(), st, &pe, &rn,
+                                p.fuse_solver, &dr, uint64_t(g0s) * in.cells);
+            else
+                rs = solve_lge(in, start, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
+                               data.as<uint8_t>(), st, &pe, &co, &dr);
+            peeled += pe;
+            core += co;
+            rounds += rn;
+            dropped += dr;
+            if (rs == VF_OK && ck.f) {
+                rs = ck.save_group(in, group, k, data.as<uint8_t>(), peeled, core, rounds, dropped);
+                if (rs != VF_OK) return rs;
+                if (ro->max_groups && ++groups_here == ro->max_groups && k + 2 < group.size()) {
+                    char msg[96];
+                    std::snprintf(msg, sizeof msg, "checkpoint holds %zu of %zu shard groups", k + 1,
+                                  group.size() - 1);
+                    return fail(VF_EAGAIN, msg);
+                }
+            }
+        }
+        in.peeled = peeled;
+        const uint64_t n_all = in.n_eff;
+        in.n_eff = n_all - dropped;
+        in.core = in.regime == VF_REGIME_LGE ? core : 0;
+        in.rounds = rounds;
+        if (rs == VF_OK) {
+            VF_CK(cudaStreamSynchronize(st));
+            if (ck.f) {
+                rs = ck.finish(in);
+                if (rs != VF_OK) return rs;
+            }
+            vf_struct* s = new vf_struct;
+            s->info = in;
+            s->geom = g;
+            s->data = data.as<uint8_t>();
+            s->device = dev;
+            data.p = nullptr;  // ownership moves to the structure
+            *out = s;
+            return VF_OK;
+        }
+        in.n_eff = n_all;
+        last = rs;
+        if (rs != VF_EBUILD) return rs;
+    }
+    return fail(last, "all attempts failed (seed .. seed+max_retries)");
+}
+
 }  // namespace
+
+vf::Geom vf::geom_of(const vf_info& in) { return make_geom(in); }
 
 void vf::set_last_error(const char* msg) { g_last_error = msg; }
 
@@ -914,170 +1241,15 @@ vf_status vf_plan(const vf_params* p, uint64_t n, uint64_t M, vf_info* out) {
 
 vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
                    const vf_params* params, void* stream, vf_struct** out) {
-    g_last_error.clear();
-    if (!params || !out) return fail(VF_EINVAL, "vf_build: NULL params or out");
-    *out = nullptr;
-    const vf_params p = *params;
-    if (p.b < 1 || p.b > 32) return fail(VF_EINVAL, "b must be in 1..32");
-    if (p.kind != VF_FUNC && p.kind != VF_FILTER) return fail(VF_EINVAL, "bad kind");
-    if (p.key_kind != VF_KEYS_U64 && p.key_kind != VF_KEYS_BYTES) return fail(VF_EINVAL, "bad key_kind");
-    if (n > 0 && !keys) return fail(VF_EINVAL, "keys is NULL");
-    if (p.key_kind == VF_KEYS_BYTES && !offsets) return fail(VF_EINVAL, "offsets is NULL");
-    if (p.kind == VF_FUNC && n > 0 && !values) return fail(VF_EINVAL, "a function needs values");
-    if (!(p.eps > 0.0) || !(p.eta > 0.0 && p.eta < 1.0) || p.max_retries < 0 || p.lge_target == 0 ||
-        p.lge_max_shard < 2 || p.mode < VF_MODE_AUTO || p.mode > VF_MODE_MWHC)
-        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes / mode");
-    // More than 2^30 keys: only 64-bit keys in the fuse or MWHC regime, built
-    // one shard group (<= 2^30 keys) at a time.
-    const bool big = n > (uint64_t(1) << 30);
-    if (big && (p.key_kind != VF_KEYS_U64 || p.mode == VF_MODE_LGE || n < p.lge_threshold || n > (uint64_t(1) << 36)))
-        return fail(VF_ECAPACITY, "above 2^30 keys: 64-bit keys, fuse or MWHC regime, at most 2^36 keys");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int dev = 0;
-    VF_CK(cudaGetDevice(&dev));
-    keep_pool_warm(dev);
+    return build_impl(keys, offsets, values, n, params, stream, out, nullptr);
+}
 
-    Staged in_keys;
-    vf_status rs = stage_keys(p.key_kind, keys, offsets, n, st, in_keys);
-    if (rs != VF_OK) return rs;
-    const void* vals_dev = nullptr;
-    if (p.kind == VF_FUNC && n > 0) {
-        if (on_device(values)) {
-            vals_dev = values;
-        } else {
-            VF_CK(in_keys.vbuf.alloc(n * value_bytes(p.b), st));
-            VF_CK(cudaMemcpyAsync(in_keys.vbuf.p, values, n * value_bytes(p.b), cudaMemcpyHostToDevice, st));
-            vals_dev = in_keys.vbuf.p;
-        }
-    }
-
-    DevBuf hist, sigs, loc, val, startb, cursor, data;
-    if (p.key_kind == VF_KEYS_BYTES) VF_CK(sigs.alloc(n * sizeof(vf::Sig), st));
-
-    vf_status last = VF_EBUILD;
-    for (int attempt = 0; attempt <= p.max_retries; attempt++) {
-        vf_info in;
-        std::memset(&in, 0, sizeof in);
-        in.n = in.n_eff = n;
-        in.kind = p.kind;
-        in.b = p.b;
-        in.seed = p.seed + uint64_t(attempt);
-        in.retries = attempt;
-        plan_h(p, n, in);
-        std::vector<uint32_t> counts;
-        for (;;) {
-            in.shards = uint64_t(1) << in.h;
-            vf::Geom g0 = make_geom(in);
-            VF_CK(hist.alloc(in.shards * 4, st));
-            VF_CK(cudaMemsetAsync(hist.p, 0, in.shards * 4, st));
-            {
-                PhaseTimer t(kPhHist, st);
-                VF_CK(vf::launch_hist(p.key_kind, in_keys.keys, in_keys.offs, n, g0, hist.as<uint32_t>(),
-                                      sigs.as<vf::Sig>(), st));
-            }
-            counts.assign(in.shards, 0);
-            VF_CK(cudaMemcpyAsync(counts.data(), hist.p, in.shards * 4, cudaMemcpyDeviceToHost, st));
-            VF_CK(cudaStreamSynchronize(st));
-            in.M = *std::max_element(counts.begin(), counts.end());
-            if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard && in.h < 40) {
-                in.h++;
-                continue;
-            }
-            break;
-        }
-        geometry(in);
-        if (in.regime != VF_REGIME_LGE && in.M >= (uint64_t(1) << 27))
-            return fail(VF_ECAPACITY, "fuse / MWHC shard above 2^27 keys");
-        if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard)
-            return fail(VF_ECAPACITY, "LGE shard above lge_max_shard");
-        const vf::Geom g = make_geom(in);
-        // shard groups: consecutive shards with at most 2^30 keys and 2^32 cells each
-        std::vector<uint32_t> group{0};
-        {
-            uint64_t keys_in = 0, cells_in = 0;
-            for (uint32_t s = 0; s < in.shards; s++) {
-                if (s > group.back() && (keys_in + counts[s] > (uint64_t(1) << 30) ||
-                                         cells_in + in.cells >= (uint64_t(1) << 32))) {
-                    group.push_back(s);
-                    keys_in = cells_in = 0;
-                }
-                keys_in += counts[s];
-                cells_in += in.cells;
-            }
-            group.push_back(uint32_t(in.shards));
-        }
-        if (group.size() > 2 && in.regime == VF_REGIME_LGE)
-            return fail(VF_ECAPACITY, "more than 2^30 keys or 2^32 cells in the LGE regime");
-        uint64_t group_max = 0;
-        for (size_t k = 0; k + 1 < group.size(); k++) {
-            uint64_t sum = 0;
-            for (uint32_t s = group[k]; s < group[k + 1]; s++) sum += counts[s];
-            group_max = std::max(group_max, sum);
-        }
-        if (loc.bytes < std::max<uint64_t>(group_max, 1) * 8) VF_CK(loc.alloc(std::max<uint64_t>(group_max, 1) * 8, st));
-        if (p.kind == VF_FUNC && val.bytes < std::max<uint64_t>(group_max, 1) * 4)
-            VF_CK(val.alloc(std::max<uint64_t>(group_max, 1) * 4, st));
-        VF_CK(data.alloc(in.data_bytes + 16, st));
-        VF_CK(cudaMemsetAsync(data.p, 0, in.data_bytes + 16, st));
-        VF_CK(cursor.alloc(in.shards * 8, st));
-        uint64_t peeled = 0, core = 0, rounds = 0;
-        rs = VF_OK;
-        uint64_t dropped = 0;
-        std::vector<unsigned long long> start;
-        for (size_t k = 0; k + 1 < group.size() && rs == VF_OK; k++) {
-            const uint32_t g0s = group[k], g1s = group[k + 1];
-            vf_info gi = in;
-            gi.shards = g1s - g0s;
-            start.assign(gi.shards + 1, 0);
-            for (uint32_t s = g0s; s < g1s; s++) start[s - g0s + 1] = start[s - g0s] + counts[s];
-            gi.n_eff = start[gi.shards];
-            gi.total_cells = gi.shards * in.cells;
-            // cursors of the group's shards start at the group-local shard starts
-            std::vector<unsigned long long> cur(in.shards, 0);
-            for (uint32_t s = g0s; s < g1s; s++) cur[s] = start[s - g0s];
-            VF_CK(cudaMemcpyAsync(cursor.p, cur.data(), in.shards * 8, cudaMemcpyHostToDevice, st));
-            rs = h2d(startb, start, st);
-            if (rs != VF_OK) return rs;
-            {
-                PhaseTimer t(kPhScatter, st);
-                VF_CK(vf::launch_scatter(static_cast<const uint64_t*>(in_keys.keys), sigs.as<vf::Sig>(), vals_dev, n,
-                                         g, cursor.as<unsigned long long>(), loc.as<uint64_t>(), val.as<uint32_t>(),
-                                         g0s, g1s, st));
-            }
-            uint64_t pe = 0, co = 0, ro = 0, dr = 0;
-            if (in.regime != VF_REGIME_LGE)  // fuse graphs and MWHC hypergraphs peel the same way
-                rs = solve_fuse(gi, g, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
-                                startb.as<unsigned long long>(), data.as<uint8_t>(), st, &pe, &ro,
-                                p.fuse_solver, &dr, uint64_t(g0s) * in.cells);
-            else
-                rs = solve_lge(in, start, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
-                               data.as<uint8_t>(), st, &pe, &co, &dr);
-            peeled += pe;
-            core += co;
-            rounds += ro;
-            dropped += dr;
-        }
-        in.peeled = peeled;
-        const uint64_t n_all = in.n_eff;
-        in.n_eff = n_all - dropped;
-        in.core = in.regime == VF_REGIME_LGE ? core : 0;
-        in.rounds = rounds;
-        if (rs == VF_OK) {
-            VF_CK(cudaStreamSynchronize(st));
-            vf_struct* s = new vf_struct;
-            s->info = in;
-            s->geom = g;
-            s->data = data.as<uint8_t>();
-            s->device = dev;
-            data.p = nullptr;  // ownership moves to the structure
-            *out = s;
-            return VF_OK;
-        }
-        in.n_eff = n_all;
-        last = rs;
-        if (rs != VF_EBUILD) return rs;
-    }
-    return fail(last, "all attempts failed (seed .. seed+max_retries)");
+vf_status vf_build_resumable(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
+                             const vf_params* params, const char* checkpoint, uint64_t group_keys,
+                             uint32_t max_groups, void* stream, vf_struct** out) {
+    if (!checkpoint) return fail(VF_EINVAL, "vf_build_resumable: NULL checkpoint path");
+    ResumeOpts ro{checkpoint, group_keys, max_groups};
+    return build_impl(keys, offsets, values, n, params, stream, out, &ro);
 }
 
 vf_status vf_query(const vf_struct* s, const void* keys, const uint64_t* offsets, uint64_t m, void* out,
@@ -1353,6 +1525,99 @@ vf_status vf_tune_batch(const vf_batch_item* items, uint32_t count, const vf_par
     *best = bo;
     if (best_ms) *best_ms = bms;
     return VF_OK;
+}
+
+// ------------------------------------------------------------ serialized form
+
+static vf_status new_struct_from(const vf::StoreHeader& h, const uint8_t* host_or_dev_data, std::FILE* f,
+                                 vf_struct** out) {
+    int dev = 0;
+    VF_CK(cudaGetDevice(&dev));
+    uint8_t* d = nullptr;
+    VF_CK(cudaMalloc(&d, h.info.data_bytes + 16));
+    cudaError_t e = cudaMemset(d, 0, h.info.data_bytes + 16);
+    bool io = true;
+    if (e == cudaSuccess) {
+        if (f) e = vf::file_to_device(f, vf::kStoreHeaderBytes, d, h.info.data_bytes, &io);
+        else e = cudaMemcpy(d, host_or_dev_data, h.info.data_bytes, cudaMemcpyDefault);
+    }
+    if (e != cudaSuccess || !io) {
+        cudaFree(d);
+        if (!io) return fail(VF_EIO, "reading the data array failed");
+        return fail(VF_ECUDA, std::string("loading the data array: ") + cudaGetErrorString(e));
+    }
+    vf_struct* s = new vf_struct;
+    s->info = h.info;
+    s->geom = vf::geom_of(h.info);
+    s->data = d;
+    s->device = dev;
+    *out = s;
+    return VF_OK;
+}
+
+static vf::StoreHeader header_of(const vf_struct* s) {
+    vf::StoreHeader h;
+    std::memset(&h, 0, sizeof h);
+    h.info = s->info;
+    h.groups_total = h.groups_done = 1;
+    h.dropped = s->info.n - s->info.n_eff;
+    h.key_kind = -1;  // queries say which key kind they pass
+    return h;
+}
+
+vf_status vf_serialize(const vf_struct* s, void* buf, uint64_t capacity, uint64_t* size) {
+    if (!s || !size) return fail(VF_EINVAL, "vf_serialize: NULL argument");
+    *size = vf::kStoreHeaderBytes + s->info.data_bytes;
+    if (!buf) return VF_OK;
+    if (capacity < *size) return fail(VF_EINVAL, "vf_serialize: buffer too small");
+    vf::store_encode(header_of(s), static_cast<uint8_t*>(buf));
+    VF_CK(cudaMemcpy(static_cast<uint8_t*>(buf) + vf::kStoreHeaderBytes, s->data, s->info.data_bytes,
+                     cudaMemcpyDeviceToHost));
+    return VF_OK;
+}
+
+vf_status vf_deserialize(const void* buf, uint64_t size, void* stream, vf_struct** out) {
+    (void)stream;
+    if (!buf || !out) return fail(VF_EINVAL, "vf_deserialize: NULL argument");
+    *out = nullptr;
+    vf::StoreHeader h;
+    if (!vf::store_decode(static_cast<const uint8_t*>(buf), size, h) || h.groups_done != h.groups_total ||
+        size < vf::kStoreHeaderBytes + h.info.data_bytes)
+        return fail(VF_EIO, "vf_deserialize: not a complete serialized structure");
+    return new_struct_from(h, static_cast<const uint8_t*>(buf) + vf::kStoreHeaderBytes, nullptr, out);
+}
+
+vf_status vf_save(const vf_struct* s, const char* path) {
+    if (!s || !path) return fail(VF_EINVAL, "vf_save: NULL argument");
+    std::FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(VF_EIO, std::string("vf_save: cannot create ") + path);
+    std::vector<uint8_t> hb(vf::kStoreHeaderBytes);
+    vf::store_encode(header_of(s), hb.data());
+    bool io = vf::file_write_at(f, 0, hb.data(), hb.size());
+    cudaError_t e = cudaSuccess;
+    if (io) e = vf::device_to_file(f, vf::kStoreHeaderBytes, s->data, s->info.data_bytes, &io);
+    if (std::fclose(f) != 0) io = false;
+    if (e != cudaSuccess) return fail(VF_ECUDA, std::string("vf_save: ") + cudaGetErrorString(e));
+    if (!io) return fail(VF_EIO, "vf_save: writing failed");
+    return VF_OK;
+}
+
+vf_status vf_load(const char* path, void* stream, vf_struct** out) {
+    (void)stream;
+    if (!path || !out) return fail(VF_EINVAL, "vf_load: NULL argument");
+    *out = nullptr;
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(VF_EIO, std::string("vf_load: cannot open ") + path);
+    std::vector<uint8_t> hb(vf::kStoreHeaderBytes);
+    vf::StoreHeader h;
+    vf_status rs;
+    if (!vf::file_read_at(f, 0, hb.data(), hb.size()) || !vf::store_decode(hb.data(), hb.size(), h) ||
+        h.groups_done != h.groups_total)
+        rs = fail(VF_EIO, "vf_load: not a complete serialized structure");
+    else
+        rs = new_struct_from(h, nullptr, f, out);
+    std::fclose(f);
+    return rs;
 }
 
 vf_status vf_free(vf_struct* s) {

@@ -4,9 +4,40 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <cstdio>
+
 #include "vf_device.cuh"
+#include "vfunc.h"
+
+// A built structure (opaque in the C ABI).
+struct vf_struct {
+    vf_info info;
+    vf::Geom geom;
+    uint8_t* data;  // device, info.data_bytes (+ padding)
+    int device;
+};
 
 namespace vf {
+
+// Geometry kernels need for a structure described by `in`.
+Geom geom_of(const vf_info& in);
+
+// ---- serialized form (csrc/vf_store.cu)
+constexpr uint64_t kStoreHeaderBytes = 4096;
+struct StoreHeader {
+    vf_info info;
+    uint64_t groups_total, groups_done;  // shard groups of the build; done == total: complete
+    uint64_t counts_digest;              // digest of the per-shard key counts
+    uint64_t params_digest;              // digest of the parameters that shape the structure
+    uint64_t dropped;                    // duplicate filter keys dropped so far
+    int32_t key_kind;
+};
+void store_encode(const StoreHeader& h, uint8_t* out);  // out: kStoreHeaderBytes
+bool store_decode(const uint8_t* in, uint64_t avail, StoreHeader& h);
+bool file_read_at(std::FILE* f, uint64_t off, void* dst, uint64_t bytes);
+bool file_write_at(std::FILE* f, uint64_t off, const void* src, uint64_t bytes);
+cudaError_t file_to_device(std::FILE* f, uint64_t off, uint8_t* dev, uint64_t bytes, bool* io_ok);
+cudaError_t device_to_file(std::FILE* f, uint64_t off, const uint8_t* dev, uint64_t bytes, bool* io_ok);
 
 int num_sms();
 

@@ -104,3 +104,20 @@ def test_plan_matches_oracle_mwhc(vf, orc):
     p = vf.vf_params_default(mode=7)
     with pytest.raises(vf.VFError):
         vf.vf_plan(10, 10, p)
+
+
+def test_serialized_form_rejects_foreign_bytes(vf, tmp_path):
+    # header validation happens before any device work: garbage, a truncated
+    # header and a missing file are VF_EIO, never a half-built structure
+    for blob in (b"", b"VFSTORE1", b"\0" * 4096, b"VFSTORE1" + b"\xff" * 5000):
+        with pytest.raises(vf.VFError) as e:
+            vf.vf_deserialize(blob)
+        assert e.value.status == vf.EIO
+    with pytest.raises(vf.VFError) as e:
+        vf.vf_load(str(tmp_path / "missing.vf"))
+    assert e.value.status == vf.EIO
+    bad = tmp_path / "bad.vf"
+    bad.write_bytes(b"not a structure" * 400)
+    with pytest.raises(vf.VFError) as e:
+        vf.vf_load(str(bad))
+    assert e.value.status == vf.EIO
