@@ -75,6 +75,25 @@ ALGO_BYTES = {
 }
 
 
+def reduce_max(vals, dist, device):
+    """Element-wise maximum over ranks: the slowest replica sets the job's time."""
+    vals = [float(v) for v in vals]
+    if dist is None:
+        return vals
+    import torch
+
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rates(b_ms, q_ms, n, world):
+    """Whole-job rates of `world` replicas that each built n keys in b_ms and
+    queried 2n keys in q_ms (max-over-ranks times): build ns per key over all
+    world*n keys, and Gqueries/s over all 2*n*world queries."""
+    return b_ms * 1e6 / (n * world), 2 * n * world / (q_ms * 1e-3) / 1e9
+
+
 def apply_overrides(p, workload, mod):
     """Parameter overrides of a workload (mode by name, eps, eta) on a params struct."""
     ov = WORKLOADS[workload][5] if len(WORKLOADS[workload]) > 5 else {}
@@ -259,12 +278,7 @@ def run_gpu(args):
     phases = vf.vf_timing_read()
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([total_ms, statistics.mean(build_ms), statistics.mean(query_ms)], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, b_ms, q_ms = t.tolist()
-    else:
-        b_ms, q_ms = statistics.mean(build_ms), statistics.mean(query_ms)
+    total_ms, b_ms, q_ms = reduce_max([total_ms, statistics.mean(build_ms), statistics.mean(query_ms)], dist, "cuda")
 
     # end to end: the same build and queries from pinned host buffers, host output
     kh, vh, oh, xh, xoh = (None if a is None else to_dev(a, torch, pin=True) for a in (keys, vals, offs, other, ooffs))
@@ -285,13 +299,14 @@ def run_gpu(args):
     other_bytes = other.nbytes + (ooffs.nbytes if ooffs is not None else 0)
     h2d = key_bytes + (vals.nbytes if vals is not None else 0) + key_bytes + other_bytes
     d2h = 2 * n * outh.element_size()
+    e2e_b_ms, e2e_q_ms = reduce_max([statistics.mean(e2e_b), statistics.mean(e2e_q)], dist, "cuda")
 
     hbm, peak_kind = peaks()
     per_phase, dom, roof = phase_table(phases, n, args.steps, b, kind, hbm, peak_kind, args.workload,
                                        info.regime == vf.REGIME_FUSE)
     launches = sum(v[1] for v in phases.values())
-    build_ns = b_ms * 1e6 / n
-    qps = 2 * n / (q_ms * 1e-3)
+    build_ns, qgps = job_rates(b_ms, q_ms, n, world)
+    e2e_ns, e2e_qgps = job_rates(e2e_b_ms, e2e_q_ms, n, world)
     out = {
         "metric": METRIC,
         "value": round(build_ns, 4),
@@ -311,9 +326,8 @@ def run_gpu(args):
                    "shards": int(info.shards), "cells_per_shard": int(info.cells), "lg_seg": int(info.lg_seg),
                    "c": info.c, "space_overhead": round(info.total_cells / n - 1, 4)},
         "build_ms": round(b_ms, 3),
-        "query": {"gqps": round(qps / 1e9, 3), "ms_per_2n": round(q_ms, 3)},
-        "e2e": {"value": round(statistics.mean(e2e_b) * 1e6 / n, 4), "unit": "ns/key",
-                "query_gqps": round(2 * n / (statistics.mean(e2e_q) * 1e-3) / 1e9, 3),
+        "query": {"gqps": round(qgps, 3), "ms_per_2n": round(q_ms, 3)},
+        "e2e": {"value": round(e2e_ns, 4), "unit": "ns/key", "query_gqps": round(e2e_qgps, 3),
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "phases": per_phase,
