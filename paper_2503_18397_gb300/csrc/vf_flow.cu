@@ -42,6 +42,7 @@ constexpr uint32_t kHole = 0xFFFFFFFFu;     // record of an item whose claim fai
 constexpr uint32_t kIdleLimit = 1u << 23;  // polls of ~1 us: a wait gives up after ~8 s
 constexpr unsigned kNapMax = 256;          // ns, peeling
 constexpr unsigned kAssignNapMax = 256;    // ns, assignment
+constexpr uint32_t kWavePrefetch = 5;      // segments ahead of a peeling step whose vertex words are prefetched
 
 using dev_atomic32 = cuda::atomic_ref<unsigned int, cuda::thread_scope_device>;
 using dev_atomic64 = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
@@ -264,6 +265,16 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
                     const uint32_t c0 = uint32_t(vv[0]), c1 = uint32_t(vv[1]), c2 = uint32_t(vv[2]);
                     const uint32_t o0 = base + (c0 == lv ? c1 : c0);             // the two vertices other
                     const uint32_t o1 = base + (c0 != lv && c1 != lv ? c1 : c2);  // than v, in edge order
+                    if (a.g.regime == kRegimeFuse) {
+                        // the waves sweep the segments: warm L2 with a line of vertex
+                        // words kWavePrefetch segments ahead, in either direction
+                        const uint32_t sv = lv >> a.g.lg_seg, T = cells >> a.g.lg_seg;
+                        const uint32_t off = uint32_t(mix64(e) & ((1ull << a.g.lg_seg) - 1)) & ~31u;
+                        if (sv + kWavePrefetch < T)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.W + base + ((sv + kWavePrefetch) << a.g.lg_seg) + off));
+                        if (sv >= kWavePrefetch)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.W + base + ((sv - kWavePrefetch) << a.g.lg_seg) + off));
+                    }
                     const uint32_t w0 = atomicAdd(a.W + o0, 0u - dec) - dec;
                     const uint32_t w1 = atomicAdd(a.W + o1, 0u - dec) - dec;
                     if ((w0 & 31u) == 1u) {
@@ -529,8 +540,9 @@ static unsigned grid_for(uint64_t work) {
 // turns at the shared queue and record counters, whose queueing sets the
 // latency of a peeling step.
 static unsigned worker_grid() { return unsigned(num_sms()); }
-// Assignment polls without hot counters on its path: two blocks per SM.
-static unsigned assign_grid() { return unsigned(num_sms()) * 2u; }
+// Assignment polls without hot counters on its path: two blocks per SM for fuse
+// graphs (a deep, narrow dataflow); four for random hypergraphs (shallow, wide).
+static unsigned assign_grid(const Geom& g) { return unsigned(num_sms()) * (g.regime == kRegimeFuse ? 2u : 4u); }
 
 cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
                                const Geom& g, uint32_t* W, uint32_t* err, const uint32_t* drop, cudaStream_t st) {
@@ -577,7 +589,7 @@ cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st) {
     k_final_init<<<grid_for(uint64_t(a.S) * a.g.cells), kFT, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.nrec == 0) return e;
-    k_flow_assign<<<assign_grid(), kFT, 0, st>>>(a);
+    k_flow_assign<<<assign_grid(a.g), kFT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
