@@ -78,12 +78,12 @@ def lib():
         L.orc_plan_h.argtypes = [C.POINTER(Params), u64, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.orc_geometry.argtypes = [C.POINTER(Info)]
         L.orc_edge.argtypes = [C.POINTER(Info), u64, C.POINTER(u64)]
-        L.orc_fingerprint.restype = C.c_uint32
+        L.orc_fingerprint.restype = C.c_uint64
         L.orc_fingerprint.argtypes = [u64, i32]
         L.orc_build.argtypes = [C.POINTER(Params), vp, vp, vp, u64, C.POINTER(Info), C.POINTER(C.c_void_p)]
         L.orc_free.argtypes = [vp]
         L.orc_query.argtypes = [C.POINTER(Info), vp, i32, vp, vp, u64, vp]
-        L.orc_cell_get.restype = C.c_uint32
+        L.orc_cell_get.restype = C.c_uint64
         L.orc_cell_get.argtypes = [vp, i32, u64]
         L.orc_peel.restype = u64
         L.orc_peel.argtypes = [u64, u64, vp, vp, vp]
@@ -176,7 +176,7 @@ def build(params: Params, keys, values=None, offsets=None):
 def out_dtype(kind: int, b: int):
     if kind == FILTER:
         return np.uint8
-    return np.uint8 if b <= 8 else np.uint16 if b <= 16 else np.uint32
+    return np.uint8 if b <= 8 else np.uint16 if b <= 16 else np.uint32 if b <= 32 else np.uint64
 
 
 def query(info: Info, data: np.ndarray, keys, offsets=None) -> np.ndarray:
@@ -203,7 +203,7 @@ def peel(V: int, edges: np.ndarray):
 
 def gf2_solve(V: int, edges: np.ndarray, rhs: np.ndarray):
     edges = np.ascontiguousarray(edges, dtype=np.uint32)
-    rhs = np.ascontiguousarray(rhs, dtype=np.uint32)
-    w = np.zeros(max(V, 1), dtype=np.uint32)
+    rhs = np.ascontiguousarray(rhs, dtype=np.uint64)
+    w = np.zeros(max(V, 1), dtype=np.uint64)
     ok = lib().orc_gf2_solve(V, len(edges), _ptr(edges), _ptr(rhs), _ptr(w))
     return bool(ok), w[:V]

@@ -221,7 +221,7 @@ void orc_geometry(orc_info *in) {
         in->cells = in->T * in->seg;
     }
     in->total_cells = in->shards * in->cells;
-    if (in->b == 8 || in->b == 16 || in->b == 32)
+    if (in->b == 8 || in->b == 16 || in->b == 32 || in->b == 64)
         in->data_bytes = in->total_cells * (uint64_t)(in->b / 8);
     else
         in->data_bytes = ((in->total_cells * (uint64_t)in->b + 63) / 64 + 1) * 8;
@@ -273,29 +273,31 @@ void orc_edge(const orc_info *in, uint64_t local, uint64_t v[3]) {
 }
 
 /* Filters derive the b-bit hash from the signature (Sec. 4.5). */
-uint32_t orc_fingerprint(uint64_t local, int b) {
-    return (uint32_t)(orc_mix64(local ^ ORC_C_FP) >> (64 - b));
+uint64_t orc_fingerprint(uint64_t local, int b) {
+    return orc_mix64(local ^ ORC_C_FP) >> (64 - b);
 }
 
 /* ------------------------------------------------------------------ cells */
 
-uint32_t orc_cell_get(const uint8_t *data, int b, uint64_t i) {
+uint64_t orc_cell_get(const uint8_t *data, int b, uint64_t i) {
     if (b == 8) return data[i];
     if (b == 16) { uint16_t x; memcpy(&x, data + 2 * i, 2); return x; }
     if (b == 32) { uint32_t x; memcpy(&x, data + 4 * i, 4); return x; }
+    if (b == 64) { uint64_t x; memcpy(&x, data + 8 * i, 8); return x; }
     uint64_t bit = i * (uint64_t)b;
-    uint32_t v = 0;
+    uint64_t v = 0;
     for (int j = 0; j < b; j++) {
         uint64_t q = bit + (uint64_t)j;
-        v |= (uint32_t)((data[q / 8] >> (q % 8)) & 1u) << j;
+        v |= (uint64_t)((data[q / 8] >> (q % 8)) & 1u) << j;
     }
     return v;
 }
 
-static void cell_set(uint8_t *data, int b, uint64_t i, uint32_t v) {
+static void cell_set(uint8_t *data, int b, uint64_t i, uint64_t v) {
     if (b == 8) { data[i] = (uint8_t)v; return; }
     if (b == 16) { uint16_t x = (uint16_t)v; memcpy(data + 2 * i, &x, 2); return; }
-    if (b == 32) { memcpy(data + 4 * i, &v, 4); return; }
+    if (b == 32) { uint32_t x = (uint32_t)v; memcpy(data + 4 * i, &x, 4); return; }
+    if (b == 64) { memcpy(data + 8 * i, &v, 8); return; }
     uint64_t bit = i * (uint64_t)b;
     for (int j = 0; j < b; j++) {
         uint64_t q = bit + (uint64_t)j;
@@ -354,11 +356,11 @@ uint64_t orc_peel(uint64_t V, uint64_t m, const uint32_t *edges, uint32_t *order
  * zero row with a non-zero right-hand side makes the system inconsistent.
  * Back-substitution runs over pivot columns from the highest down; variables
  * without a pivot are set to 0. */
-int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint32_t *rhs, uint32_t *w) {
+int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint64_t *rhs, uint64_t *w) {
     uint64_t W = (V + 63) / 64;
     if (W == 0) W = 1;
     uint64_t *rows = calloc((m ? m : 1) * W, sizeof(uint64_t));
-    uint32_t *rr = calloc(m ? m : 1, sizeof(uint32_t));
+    uint64_t *rr = calloc(m ? m : 1, sizeof(uint64_t));
     int64_t *pivot = malloc((V ? V : 1) * sizeof(int64_t));
     uint64_t *cur = malloc(W * sizeof(uint64_t));
     int ok = 1;
@@ -370,7 +372,7 @@ int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint32_t 
             uint32_t v = edges[3 * e + k];
             cur[v / 64] ^= 1ULL << (v % 64);
         }
-        uint32_t cr = rhs[e];
+        uint64_t cr = rhs[e];
         for (;;) {
             uint64_t c = 0;
             int found = 0;
@@ -395,7 +397,7 @@ int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint32_t 
         for (uint64_t cc = V; cc-- > 0;) {
             if (pivot[cc] < 0) continue;
             const uint64_t *pr = rows + (uint64_t)pivot[cc] * W;
-            uint32_t val = rr[pivot[cc]];
+            uint64_t val = rr[pivot[cc]];
             for (uint64_t j = cc + 1; j < V; j++)
                 if ((pr[j / 64] >> (j % 64)) & 1ULL) val ^= w[j];
             w[cc] = val;
@@ -415,17 +417,18 @@ static int u64_cmp(const void *a, const void *b) {
     return x < y ? -1 : x > y;
 }
 
-static uint32_t value_at(const void *values, int b, uint64_t i) {
-    uint32_t v;
+static uint64_t value_at(const void *values, int b, uint64_t i) {
+    uint64_t v;
     if (b <= 8) v = ((const uint8_t *)values)[i];
     else if (b <= 16) v = ((const uint16_t *)values)[i];
-    else v = ((const uint32_t *)values)[i];
-    return b == 32 ? v : (v & ((1u << b) - 1u));
+    else if (b <= 32) v = ((const uint32_t *)values)[i];
+    else v = ((const uint64_t *)values)[i];
+    return b == 64 ? v : (v & ((1ULL << b) - 1ULL));
 }
 
 /* Solve one shard: edges from local signatures, peel, optional GE on the
  * 2-core, reverse assignment. Returns 1 on success. */
-static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, const uint32_t *val,
+static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, const uint64_t *val,
                        uint8_t *data, uint64_t base, uint64_t *peeled_out) {
     uint64_t V = in->cells;
     uint32_t *edges = malloc((m ? m : 1) * 3 * sizeof(uint32_t));
@@ -438,7 +441,7 @@ static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, cons
     }
     uint64_t ne = orc_peel(V, m, edges, order, side);
     *peeled_out = ne;
-    uint32_t *w = calloc(V, sizeof(uint32_t));
+    uint64_t *w = calloc(V, sizeof(uint64_t));
     int ok = 1;
     if (ne < m) {
         if (in->regime != ORC_REGIME_LGE) {
@@ -448,7 +451,7 @@ static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, cons
             for (uint64_t i = 0; i < ne; i++) is_peeled[order[i]] = 1;
             uint64_t nc = 0;
             uint32_t *ce = malloc((m - ne) * 3 * sizeof(uint32_t));
-            uint32_t *cr = malloc((m - ne) * sizeof(uint32_t));
+            uint64_t *cr = malloc((m - ne) * sizeof(uint64_t));
             for (uint64_t e = 0; e < m; e++) {
                 if (is_peeled[e]) continue;
                 memcpy(ce + 3 * nc, edges + 3 * e, 3 * sizeof(uint32_t));
@@ -466,7 +469,7 @@ static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, cons
         for (uint64_t i = ne; i-- > 0;) {
             uint32_t e = order[i];
             int sd = side[i];
-            uint32_t x = val[e];
+            uint64_t x = val[e];
             for (int k = 0; k < 3; k++)
                 if (k != sd) x ^= w[edges[3 * e + k]];
             w[edges[3 * e + sd]] = x;
@@ -482,7 +485,7 @@ static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, cons
 
 int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
               const void *values, uint64_t n, orc_info *info, uint8_t **data_out) {
-    if (p->b < 1 || p->b > 32 || (p->kind != ORC_FUNC && p->kind != ORC_FILTER)) return ORC_EINVAL;
+    if (p->b < 1 || p->b > 64 || (p->kind != ORC_FUNC && p->kind != ORC_FILTER)) return ORC_EINVAL;
     if (p->key_kind != ORC_KEYS_U64 && p->key_kind != ORC_KEYS_BYTES) return ORC_EINVAL;
     if (n > 0 && keys == NULL) return ORC_EINVAL;
     if (p->key_kind == ORC_KEYS_BYTES && offsets == NULL) return ORC_EINVAL;
@@ -490,7 +493,7 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
     *data_out = NULL;
     uint64_t *sig = malloc((n ? n : 1) * 2 * sizeof(uint64_t));
     uint64_t *loc = malloc((n ? n : 1) * sizeof(uint64_t));
-    uint32_t *val = malloc((n ? n : 1) * sizeof(uint32_t));
+    uint64_t *val = malloc((n ? n : 1) * sizeof(uint64_t));
     if (!sig || !loc || !val) return ORC_ENOMEM;
 
     for (int attempt = 0; attempt <= p->max_retries; attempt++) {
@@ -539,7 +542,7 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
         for (uint64_t s = 0; s < in.shards && ok; s++) {
             uint64_t m = cnt[s];
             uint64_t *L = loc + start[s];
-            uint32_t *Vv = val + start[s];
+            uint64_t *Vv = val + start[s];
             if (p->kind == ORC_FILTER) {
                 /* Sec. 4.5: duplicate local signatures are dropped; the
                  * fingerprint is a function of the local signature. */
@@ -595,7 +598,7 @@ void orc_query(const orc_info *in, const uint8_t *data, int key_kind, const void
         uint64_t v[3];
         orc_edge(in, local, v);
         uint64_t base = s * in->cells;
-        uint32_t x = orc_cell_get(data, in->b, base + v[0]) ^ orc_cell_get(data, in->b, base + v[1]) ^
+        uint64_t x = orc_cell_get(data, in->b, base + v[0]) ^ orc_cell_get(data, in->b, base + v[1]) ^
                      orc_cell_get(data, in->b, base + v[2]);
         if (in->kind == ORC_FILTER) {
             ((uint8_t *)out)[i] = x == orc_fingerprint(local, in->b);
@@ -603,8 +606,10 @@ void orc_query(const orc_info *in, const uint8_t *data, int key_kind, const void
             ((uint8_t *)out)[i] = (uint8_t)x;
         } else if (in->b <= 16) {
             ((uint16_t *)out)[i] = (uint16_t)x;
+        } else if (in->b <= 32) {
+            ((uint32_t *)out)[i] = (uint32_t)x;
         } else {
-            ((uint32_t *)out)[i] = x;
+            ((uint64_t *)out)[i] = x;
         }
     }
 }

@@ -30,7 +30,7 @@ enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EBUILD = 3 };
 
 typedef struct {
     int kind;             /* ORC_FUNC or ORC_FILTER */
-    int b;                /* value / fingerprint bits, 1..32 */
+    int b;                /* value / fingerprint bits, 1..64 */
     int key_kind;         /* ORC_KEYS_U64 or ORC_KEYS_BYTES */
     int mode;             /* ORC_MODE_* */
     int max_retries;      /* extra attempts with seed+1, seed+2, ... */
@@ -94,10 +94,10 @@ void orc_geometry(orc_info *info);
 uint64_t orc_shard(const uint64_t sig[2], int h);
 uint64_t orc_local(const uint64_t sig[2], int h);
 void orc_edge(const orc_info *info, uint64_t local, uint64_t v[3]);
-uint32_t orc_fingerprint(uint64_t local, int b);
+uint64_t orc_fingerprint(uint64_t local, int b);
 
 /* Build. keys: uint64 array (ORC_KEYS_U64) or packed bytes with offsets[n+1].
- * values: func only, uint8/16/32 per b (<=8, <=16, <=32 bits); low b bits used.
+ * values: func only, uint8/16/32/64 per b (<=8, <=16, <=32, <=64 bits); low b bits used.
  * On success *data is a malloc'ed array of info->data_bytes bytes. */
 int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
               const void *values, uint64_t n, orc_info *info, uint8_t **data);
@@ -107,15 +107,15 @@ void orc_free(void *ptr);
 void orc_query(const orc_info *info, const uint8_t *data, int key_kind, const void *keys,
                const uint64_t *offsets, uint64_t m, void *out);
 
-/* Cell access (Sec. 5 layout: native array for b in {8,16,32}, else a bit array). */
-uint32_t orc_cell_get(const uint8_t *data, int b, uint64_t i);
+/* Cell access (Sec. 5 layout: native array for b in {8,16,32,64}, else a bit array). */
+uint64_t orc_cell_get(const uint8_t *data, int b, uint64_t i);
 
 /* Helpers exposed for pin tests on explicit tiny hypergraphs.
  * orc_peel: stack peel of m 3-edges on V vertices; returns number peeled and
  * writes per-edge peel order/side when non-NULL.
  * orc_gf2_solve: plain GE; returns 1 if solvable and writes w[V]. */
 uint64_t orc_peel(uint64_t V, uint64_t m, const uint32_t *edges, uint32_t *order, uint8_t *side);
-int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint32_t *rhs, uint32_t *w);
+int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint64_t *rhs, uint64_t *w);
 
 /* Batch forms of orc_sig_* and orc_edge used by the tests. */
 void orc_sigs(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t seed,

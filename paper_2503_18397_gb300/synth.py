@@ -55,9 +55,9 @@ def u64_keys(start: int, count: int, seed: int) -> np.ndarray:
 
 
 def values(count: int, b: int, seed: int) -> np.ndarray:
-    """Uniform b-bit values in the narrowest unsigned type holding b bits."""
+    """Uniform b-bit values (b <= 64) in the narrowest unsigned type holding b bits."""
     rng = np.random.Generator(np.random.PCG64(seed ^ 0xA11CE))
-    dt = np.uint8 if b <= 8 else np.uint16 if b <= 16 else np.uint32
+    dt = np.uint8 if b <= 8 else np.uint16 if b <= 16 else np.uint32 if b <= 32 else np.uint64
     hi = 1 << b
     return rng.integers(0, hi, size=count, dtype=np.uint64).astype(dt)
 
@@ -115,6 +115,10 @@ def values_torch(count: int, b: int, seed: int, device="cuda"):
 
     g = torch.Generator(device=device)
     g.manual_seed(seed ^ 0xA11CE)
+    if b > 32:  # int64 tensor holding the 64-bit patterns
+        lo = torch.randint(0, 1 << 32, (count,), dtype=torch.int64, device=device, generator=g)
+        hi = torch.randint(0, 1 << (b - 32), (count,), dtype=torch.int64, device=device, generator=g)
+        return lo | (hi << 32)
     v = torch.randint(0, 1 << b, (count,), dtype=torch.int64, device=device, generator=g)
     if b <= 8:
         return v.to(torch.uint8)

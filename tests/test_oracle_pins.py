@@ -328,13 +328,18 @@ def test_gf2_solve_matches_bruteforce(orc):
         V = int(rng.integers(3, 9))
         m = int(rng.integers(1, 12))
         edges = _random_hypergraph(rng, V, m)
+        # value widths of 1..3 bits, and 64-bit values whose planes are checked
+        # on a few bit positions (a high plane is solved like a low one)
         bits = int(rng.integers(1, 4))
-        rhs = rng.integers(0, 1 << bits, size=m).astype(np.uint32)
+        rhs = rng.integers(0, 1 << bits, size=m).astype(np.uint64)
+        if trial % 3 == 0:
+            rhs = rhs | (rng.integers(0, 1 << 62, size=m, dtype=np.uint64) << np.uint64(2) & np.uint64(~7 & (2**64 - 1)))
         ok, w = orc.gf2_solve(V, edges, rhs)
         # brute force: each bit plane independently
         solvable = True
-        for j in range(bits):
-            plane = (rhs >> j) & 1
+        planes = list(range(bits)) + ([3, 31, 32, 63] if trial % 3 == 0 else [])
+        for j in planes:
+            plane = (rhs >> np.uint64(j)) & np.uint64(1)
             found = False
             for assign in itertools.product((0, 1), repeat=V):
                 if all((assign[a] ^ assign[b] ^ assign[c]) == plane[i] for i, (a, b, c) in enumerate(edges)):
@@ -350,7 +355,7 @@ def test_gf2_solve_matches_bruteforce(orc):
 # ------------------------------------------------------------------ builds
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 97, 5000, 40_000])
-@pytest.mark.parametrize("b", [1, 5, 8, 16, 32])
+@pytest.mark.parametrize("b", [1, 5, 8, 16, 32, 33, 64])
 def test_build_function_decodes_every_key(orc, n, b):
     keys = synth.u64_keys(0, n, 21)
     vals = synth.values(n, b, 21)
@@ -528,3 +533,38 @@ def test_mwhc_build_decodes_sharded(orc, kind, b):
         other = orc.query(info, data, synth.u64_keys(n, 200_000, 14))
         pr = 2.0 ** -b
         assert abs(other.mean() - pr) < 5 * math.sqrt(pr * (1 - pr) / 200_000) + 1e-9
+
+
+
+# ------------------------------------------------------------- wide values (b > 32)
+
+@pytest.mark.parametrize("b", [33, 40, 63])
+def test_bit_array_cells_wider_than_a_word(orc, b):
+    # Sec. 5 bit array: cell i holds bits [i*b, (i+1)*b); b > 32 cells straddle
+    # 32- and 64-bit words. Reading back a build's cells one bit at a time
+    # (independently of orc_cell_get) gives the same values.
+    n = 3000
+    keys = synth.u64_keys(0, n, 61)
+    vals = synth.values(n, b, 61)
+    st, info, data = orc.build(orc.default_params(b=b, seed=2), keys, vals)
+    assert st == orc.OK and info.data_bytes == ((info.total_cells * b + 63) // 64 + 1) * 8
+    bits = np.unpackbits(data, bitorder="little")
+    for i in range(0, info.total_cells, 97):
+        want = 0
+        for j in range(b):
+            want |= int(bits[i * b + j]) << j
+        assert orc.lib().orc_cell_get(data.ctypes.data, b, i) == want
+
+
+def test_wide_filter_fingerprints_and_no_false_negatives(orc):
+    # Problem 2 with b = 33 and 64: fingerprints are the top b bits of the remix;
+    # members always pass, non-members almost never (FPR 2^-33 / 2^-64)
+    n = 50_000
+    keys = synth.u64_keys(0, n, 62)
+    other = synth.u64_keys(n, 200_000, 62)
+    for b in (33, 64):
+        st, info, data = orc.build(orc.default_params(kind=orc.FILTER, b=b, seed=1), keys)
+        assert st == orc.OK
+        assert orc.query(info, data, keys).all() and orc.query(info, data, other).sum() == 0
+        f = orc.fingerprint(int(keys[0]), b)
+        assert f >> b == 0 and orc.fingerprint(int(keys[0]), 32) == f >> (b - 32)
