@@ -62,8 +62,13 @@ enum { VF_SOLVER_FLOW = 0, VF_SOLVER_ROUNDS = 1 };
 /* Build parameters. vf_params_default() fills the paper's defaults. */
 typedef struct {
     int kind;                /* VF_FUNC (Problem 1) or VF_FILTER (Problem 2) */
-    int b;                   /* value bits (function) or fingerprint bits (filter), 1..32;
-                                a filter's false-positive rate is 2^-b (Sec. 3.1) */
+    int b;                   /* value bits (function) or fingerprint bits (filter), 1..64;
+                                a filter's false-positive rate is 2^-b (Sec. 3.1). Values
+                                and outputs are u8/u16/u32/u64 for b <= 8/16/32/64. Above
+                                32 bits vf_build solves the low 32 and the high b-32 bit
+                                planes as two slices on one hypergraph (same seed) and
+                                packs them; batched, resumable and allocation-free
+                                builds take b <= 32 */
     int key_kind;            /* VF_KEYS_U64 or VF_KEYS_BYTES */
     int mode;                /* VF_MODE_AUTO: LGE regime below lge_threshold keys, fuse
                                 regime above (Sec. 4.2); or force one regime.
@@ -99,7 +104,7 @@ typedef struct {
     uint64_t seg, l, T;      /* fuse: segment size, start segments, segments (l = T - 2) */
     uint64_t cells;          /* cells per shard; shard s owns cells [s*cells, (s+1)*cells) */
     uint64_t total_cells;
-    uint64_t data_bytes;     /* size of the data array (b in {8,16,32}: native; else bits) */
+    uint64_t data_bytes;     /* size of the data array (b in {8,16,32,64}: native; else bits) */
     uint64_t seed;           /* seed of the successful attempt */
     int retries;             /* failed attempts before it */
     uint64_t peeled, core;   /* edges peeled / edges solved by elimination (last attempt) */

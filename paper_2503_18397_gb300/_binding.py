@@ -269,9 +269,15 @@ def vf_load(path: str, stream=None):
 
 
 def _out_dtype(info: VfInfo):
+    """Output element type: u8 for filters, else the narrowest type holding b bits."""
     if info.kind == FILTER or info.b <= 8:
         return np.uint8
-    return np.uint16 if info.b <= 16 else np.uint32
+    return np.uint16 if info.b <= 16 else np.uint32 if info.b <= 32 else np.uint64
+
+
+def _torch_dtype(dt):
+    # 64-bit results come back as int64 tensors holding the bit patterns
+    return {np.uint8: torch.uint8, np.uint16: torch.uint16, np.uint32: torch.uint32, np.uint64: torch.int64}[dt]
 
 
 def vf_query(s: Structure, keys, offsets=None, out=None, stream=None):
@@ -280,7 +286,7 @@ def vf_query(s: Structure, keys, offsets=None, out=None, stream=None):
     if out is None:
         dt = _out_dtype(vf_get_info(s))
         if _is_tensor(keys):
-            tdt = {np.uint8: torch.uint8, np.uint16: torch.uint16, np.uint32: torch.uint32}[dt]
+            tdt = _torch_dtype(dt)
             out = torch.empty(m, dtype=tdt, device=keys.device)
         else:
             out = np.empty(m, dtype=dt)
@@ -296,7 +302,7 @@ def vf_query_batch(requests, stream=None):
     for i, (s, keys, out) in enumerate(requests):
         if out is None:
             dt = _out_dtype(vf_get_info(s))
-            tdt = {np.uint8: torch.uint8, np.uint16: torch.uint16, np.uint32: torch.uint32}[dt]
+            tdt = _torch_dtype(dt)
             out = torch.empty(len(keys), dtype=tdt, device=keys.device)
         outs.append(out)
         arr[i].s = s.handle

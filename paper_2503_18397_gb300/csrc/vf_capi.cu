@@ -226,13 +226,14 @@ void geometry(vf_info& in) {
         in.cells = in.T * in.seg;
     }
     in.total_cells = in.shards * in.cells;
-    if (in.b == 8 || in.b == 16 || in.b == 32)
+    if (in.b == 8 || in.b == 16 || in.b == 32 || in.b == 64)
         in.data_bytes = in.total_cells * uint64_t(in.b / 8);
     else
         in.data_bytes = ((in.total_cells * uint64_t(in.b) + 63) / 64 + 1) * 8;
 }
 
-vf::Geom make_geom(const vf_info& in) {
+// fpb / fps: the fingerprint slice of a 32-bit slice of a wider filter.
+vf::Geom make_geom(const vf_info& in, int fpb = 0, int fps = 0) {
     vf::Geom g;
     std::memset(&g, 0, sizeof g);
     g.kh = vf::mix64(in.seed ^ vf::kLaneHi);
@@ -244,10 +245,12 @@ vf::Geom make_geom(const vf_info& in) {
     g.regime = in.regime;
     g.b = in.b;
     g.kind = in.kind;
+    g.fpb = fpb;
+    g.fps = fps;
     return g;
 }
 
-size_t value_bytes(int b) { return b <= 8 ? 1 : b <= 16 ? 2 : 4; }
+size_t value_bytes(int b) { return b <= 8 ? 1 : b <= 16 ? 2 : b <= 32 ? 4 : 8; }
 
 // Input staged on the device (a copy when the caller passed host memory).
 struct Staged {
@@ -520,7 +523,7 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32
 // Tasks of the LGE solver for the shards of one or more structures, largest
 // shard first when `lpt` (longest-processing-time order balances the CTAs).
 void add_lge_tasks(std::vector<vf::LgeTask>& tasks, const std::vector<unsigned long long>& start, uint64_t base_key,
-                   const vf_info& in, uint8_t* data, uint32_t item) {
+                   const vf_info& in, uint8_t* data, uint32_t item, int fpb = 0, int fps = 0) {
     for (uint64_t s = 0; s < in.shards; s++) {
         vf::LgeTask t;
         std::memset(&t, 0, sizeof t);
@@ -532,6 +535,8 @@ void add_lge_tasks(std::vector<vf::LgeTask>& tasks, const std::vector<unsigned l
         t.b = in.b;
         t.kind = in.kind;
         t.item = item;
+        t.fpb = uint8_t(fpb);
+        t.fps = uint8_t(fps);
         if (t.m > 0) tasks.push_back(t);
     }
 }
@@ -591,9 +596,9 @@ vf_status run_lge_tasks(std::vector<vf::LgeTask>& tasks, bool lpt, const uint64_
 
 vf_status solve_lge(const vf_info& in, const std::vector<unsigned long long>& start, const uint64_t* loc,
                     const uint32_t* val, uint8_t* data, cudaStream_t st, uint64_t* peeled, uint64_t* core,
-                    uint64_t* dups) {
+                    uint64_t* dups, int fpb = 0, int fps = 0) {
     std::vector<vf::LgeTask> tasks;
-    add_lge_tasks(tasks, start, 0, in, data, 0);
+    add_lge_tasks(tasks, start, 0, in, data, 0, fpb, fps);
     uint32_t err = 0;
     vf_status rs = run_lge_tasks(tasks, true, loc, val, nullptr, st, peeled, core, &err, dups);
     if (rs != VF_OK) return rs;
@@ -996,16 +1001,24 @@ int checkpoint_attempt(const ResumeOpts* ro, const vf_params& p, uint64_t n) {
     return a;
 }
 
-vf_status build_impl(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
-                     const vf_params* params, void* stream, vf_struct** out, const ResumeOpts* ro);
+// One 32-bit slice of a structure wider than 32 bits: the fingerprint bits
+// it holds (filters).
+struct SliceOpts {
+    int fpb, fps;
+};
 
 vf_status build_impl(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
-                     const vf_params* params, void* stream, vf_struct** out, const ResumeOpts* ro) {
+                     const vf_params* params, void* stream, vf_struct** out, const ResumeOpts* ro,
+                     const SliceOpts* so = nullptr);
+
+vf_status build_impl(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
+                     const vf_params* params, void* stream, vf_struct** out, const ResumeOpts* ro,
+                     const SliceOpts* so) {
     g_last_error.clear();
     if (!params || !out) return fail(VF_EINVAL, "vf_build: NULL params or out");
     *out = nullptr;
     const vf_params p = *params;
-    if (p.b < 1 || p.b > 32) return fail(VF_EINVAL, "b must be in 1..32");
+    if (p.b < 1 || p.b > 32) return fail(VF_EINVAL, "b must be in 1..64 (above 32 only through vf_build)");
     if (p.kind != VF_FUNC && p.kind != VF_FILTER) return fail(VF_EINVAL, "bad kind");
     if (p.key_kind != VF_KEYS_U64 && p.key_kind != VF_KEYS_BYTES) return fail(VF_EINVAL, "bad key_kind");
     if (n > 0 && !keys) return fail(VF_EINVAL, "keys is NULL");
@@ -1078,7 +1091,7 @@ vf_status build_impl(const void* keys, const uint64_t* offsets, const void* valu
             return fail(VF_ECAPACITY, "fuse / MWHC shard above 2^27 keys");
         if (in.regime == VF_REGIME_LGE && in.M > p.lge_max_shard)
             return fail(VF_ECAPACITY, "LGE shard above lge_max_shard");
-        const vf::Geom g = make_geom(in);
+        const vf::Geom g = make_geom(in, so ? so->fpb : 0, so ? so->fps : 0);
         // shard groups: consecutive shards with at most 2^30 keys (or the resumable
         // build's group size) and 2^32 cells each
         const uint64_t group_cap =
@@ -1152,7 +1165,7 @@ vf_status build_impl(const void* keys, const uint64_t* offsets, const void* valu
                                 p.fuse_solver, &dr, uint64_t(g0s) * in.cells);
             else
                 rs = solve_lge(in, start, loc.as<uint64_t>(), p.kind == VF_FUNC ? val.as<uint32_t>() : nullptr,
-                               data.as<uint8_t>(), st, &pe, &co, &dr);
+                               data.as<uint8_t>(), st, &pe, &co, &dr, so ? so->fpb : 0, so ? so->fps : 0);
             peeled += pe;
             core += co;
             rounds += rn;
@@ -1189,6 +1202,83 @@ vf_status build_impl(const void* keys, const uint64_t* offsets, const void* valu
             return VF_OK;
         }
         in.n_eff = n_all;
+        last = rs;
+        if (rs != VF_EBUILD) return rs;
+    }
+    return fail(last, "all attempts failed (seed .. seed+max_retries)");
+}
+
+// Values wider than 32 bits (b = 33..64): the system is linear over GF(2)^b,
+// so an attempt solves the low 32 bit planes and the high b-32 bit planes as
+// two slices on the same hypergraph and seed; it fails (next seed) if either
+// does, as the full system would. The slices' cells are then packed into one
+// b-bit array.
+vf_status build_wide(const void* keys, const uint64_t* offsets, const void* values, uint64_t n, const vf_params& p,
+                     void* stream, vf_struct** out) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int b = p.b, hb = b - 32;
+    DevBuf v64, vlo, vhi;
+    if (p.kind == VF_FUNC && n > 0) {
+        const uint64_t* vdev = static_cast<const uint64_t*>(values);
+        if (!on_device(values)) {
+            VF_CK(v64.alloc(n * 8, st));
+            VF_CK(cudaMemcpyAsync(v64.p, values, n * 8, cudaMemcpyHostToDevice, st));
+            vdev = v64.as<uint64_t>();
+        }
+        VF_CK(vlo.alloc(n * 4, st));
+        VF_CK(vhi.alloc(n * value_bytes(hb), st));
+        VF_CK(vf::launch_split64(vdev, n, b, vlo.as<uint32_t>(), vhi.p, st));
+    }
+    int dev = 0;
+    VF_CK(cudaGetDevice(&dev));
+    vf_status last = VF_EBUILD;
+    for (int attempt = 0; attempt <= p.max_retries; attempt++) {
+        vf_params ps = p;
+        ps.seed = p.seed + uint64_t(attempt);
+        ps.max_retries = 0;
+        ps.b = 32;
+        vf_struct* lo = nullptr;
+        vf_struct* hi = nullptr;
+        const SliceOpts slo{b, 0}, shi{b, 32};
+        vf_status rs = build_impl(keys, offsets, vlo.p, n, &ps, stream, &lo, nullptr, &slo);
+        if (rs == VF_OK) {
+            ps.b = hb;
+            rs = build_impl(keys, offsets, vhi.p, n, &ps, stream, &hi, nullptr, &shi);
+        }
+        if (rs == VF_OK && (lo->info.total_cells != hi->info.total_cells || lo->info.h != hi->info.h)) {
+            vf_free(lo);
+            vf_free(hi);
+            return fail(VF_ECUDA, "wide build: the two slices disagree on the geometry");
+        }
+        if (rs == VF_OK) {
+            vf_info in = lo->info;
+            in.b = b;
+            in.seed = ps.seed;
+            in.retries = attempt;
+            in.data_bytes = b == 64 ? in.total_cells * 8 : ((in.total_cells * uint64_t(b) + 63) / 64 + 1) * 8;
+            uint8_t* d = nullptr;
+            cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), in.data_bytes + 16, st);
+            if (e == cudaSuccess)
+                e = vf::launch_pack_wide(reinterpret_cast<const uint32_t*>(lo->data), hi->data, in.total_cells, b,
+                                         in.data_bytes / 8, reinterpret_cast<uint64_t*>(d), st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d + in.data_bytes, 0, 16, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            vf_free(lo);
+            vf_free(hi);
+            if (e != cudaSuccess) {
+                if (d) cudaFree(d);
+                return fail(VF_ECUDA, std::string("wide build: packing failed: ") + cudaGetErrorString(e));
+            }
+            vf_struct* s = new vf_struct;
+            s->info = in;
+            s->geom = make_geom(in);
+            s->data = d;
+            s->device = dev;
+            *out = s;
+            return VF_OK;
+        }
+        if (lo) vf_free(lo);
+        if (hi) vf_free(hi);
         last = rs;
         if (rs != VF_EBUILD) return rs;
     }
@@ -1241,6 +1331,12 @@ vf_status vf_plan(const vf_params* p, uint64_t n, uint64_t M, vf_info* out) {
 
 vf_status vf_build(const void* keys, const uint64_t* offsets, const void* values, uint64_t n,
                    const vf_params* params, void* stream, vf_struct** out) {
+    if (params && out && params->b > 32 && params->b <= 64) {
+        g_last_error.clear();
+        *out = nullptr;
+        if (params->kind == VF_FUNC && n > 0 && !values) return fail(VF_EINVAL, "a function needs values");
+        return build_wide(keys, offsets, values, n, *params, stream, out);
+    }
     return build_impl(keys, offsets, values, n, params, stream, out, nullptr);
 }
 
@@ -1248,6 +1344,7 @@ vf_status vf_build_resumable(const void* keys, const uint64_t* offsets, const vo
                              const vf_params* params, const char* checkpoint, uint64_t group_keys,
                              uint32_t max_groups, void* stream, vf_struct** out) {
     if (!checkpoint) return fail(VF_EINVAL, "vf_build_resumable: NULL checkpoint path");
+    if (params && params->b > 32) return fail(VF_EINVAL, "vf_build_resumable: b above 32 (use vf_build)");
     ResumeOpts ro{checkpoint, group_keys, max_groups};
     return build_impl(keys, offsets, values, n, params, stream, out, &ro);
 }

@@ -48,7 +48,8 @@ struct Geom {
     int32_t regime;
     int32_t b;
     int32_t kind;         // 0 function, 1 filter
-    int32_t pad;
+    int32_t fpb;          // filter: bits of the full fingerprint (0: b); a structure wider than 32 bits
+    int32_t fps;          //   is built as 32-bit slices, this one holding fingerprint bits [fps, fps + b)
 };
 
 // ----------------------------------------------------------------- signatures
@@ -146,11 +147,30 @@ __device__ __forceinline__ void edge_of(const Geom& g, uint64_t local, uint64_t 
 }
 
 // Filter fingerprint: top b bits of a remix of the local signature (Sec. 4.5).
-__device__ __forceinline__ uint32_t fingerprint(uint64_t local, int b) {
-    return uint32_t(mix64(local ^ kFpSalt) >> (64 - b));
+__device__ __forceinline__ uint64_t fingerprint64(uint64_t local, int b) { return mix64(local ^ kFpSalt) >> (64 - b); }
+
+// Bits [fps, fps + b) of the fpb-bit fingerprint (fpb = 0: b bits, the whole one).
+__device__ __forceinline__ uint32_t fingerprint_slice(uint64_t local, int b, int fpb, int fps) {
+    const uint64_t s = fingerprint64(local, fpb ? fpb : b) >> fps;
+    return b >= 32 ? uint32_t(s) : uint32_t(s) & ((1u << b) - 1u);
 }
 
+__device__ __forceinline__ uint32_t fingerprint(uint64_t local, int b) { return fingerprint_slice(local, b, 0, 0); }
+
 // ------------------------------------------------------------------- cells
+
+// Cell i of a b-bit array with 32 < b <= 64 (b = 64 native; otherwise a bit
+// array whose last word is followed by a pad word, so reading q + 1 is safe).
+__device__ __forceinline__ uint64_t cell_get64(const uint8_t* __restrict__ data, int b, uint64_t i) {
+    const uint64_t* w = reinterpret_cast<const uint64_t*>(data);
+    if (b == 64) return __ldg(w + i);
+    const uint64_t bit = i * uint64_t(b);
+    const uint64_t q = bit >> 6;
+    const uint32_t o = uint32_t(bit & 63);
+    uint64_t x = __ldg(w + q) >> o;
+    if (o + b > 64) x |= __ldg(w + q + 1) << (64 - o);
+    return x & ((uint64_t(1) << b) - 1);
+}
 
 __device__ __forceinline__ bool native_width(int b) { return b == 8 || b == 16 || b == 32; }
 

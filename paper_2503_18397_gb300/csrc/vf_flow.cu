@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
                             pe = uint32_t(st0 + (w1 >> 5));
                         }
                     }
-                    a.rec[rs] = make_uint4(v, o0, o1, a.val ? value : fingerprint(local, a.g.b));
+                    a.rec[rs] = make_uint4(v, o0, o1, a.val ? value : fingerprint_slice(local, a.g.b, a.g.fpb, a.g.fps));
                 } else {
                     a.rec[rs].x = kHole;
                 }

@@ -151,7 +151,8 @@ struct LgeTask {
     int32_t b;
     int32_t kind;        // 0 function (values from `val`), 1 filter (fingerprints)
     uint32_t item;       // structure index: failures are recorded in item_fail[item]
-    uint32_t pad;
+    uint8_t fpb, fps;    // filter fingerprint slice (see Geom)
+    uint16_t pad;
 };
 
 struct LgeArgs {
@@ -244,5 +245,14 @@ cudaError_t launch_query_batch(const QueryReq* reqs, uint32_t count, uint64_t to
 
 cudaError_t launch_query(int key_kind, const void* keys, const uint64_t* offs, uint64_t m, const Geom& g,
                          const uint8_t* data, void* out, cudaStream_t st);
+
+// Values wider than 32 bits (csrc/vf_wide.cu): split u64 values into the two
+// slices' value arrays, pack two solved slices into b-bit cells (words =
+// data_bytes / 8 of the b-bit structure), query a b-bit structure.
+cudaError_t launch_split64(const uint64_t* v, uint64_t n, int b, uint32_t* lo, void* hi, cudaStream_t st);
+cudaError_t launch_pack_wide(const uint32_t* lo, const uint8_t* hi, uint64_t cells, int b, uint64_t words,
+                             uint64_t* out, cudaStream_t st);
+cudaError_t launch_query_wide(const void* keys, const uint64_t* offs, uint64_t m, const Geom& g, const uint8_t* data,
+                              void* out, cudaStream_t st);
 
 }  // namespace vf

@@ -30,7 +30,7 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 uint64_t lge_scratch_words_per_cta(uint32_t m_cap, uint32_t v_cap) { return lge_offsets(m_cap, v_cap).total; }
 
 __device__ __forceinline__ uint32_t rhs_of(const LgeArgs& a, const LgeTask& t, uint64_t ge) {
-    return t.kind == 0 ? __ldg(a.val + ge) : fingerprint(__ldg(a.loc + ge), t.b);
+    return t.kind == 0 ? __ldg(a.val + ge) : fingerprint_slice(__ldg(a.loc + ge), t.b, t.fpb, t.fps);
 }
 
 __device__ __forceinline__ uint32_t deg_of(const uint32_t* degw, uint32_t v) {
@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
         gg.regime = kRegimeLge;
         gg.b = b;
         gg.kind = task.kind;
-        gg.pad = 0;
+        gg.fpb = task.fpb;
+        gg.fps = task.fps;
         if (m > a.m_cap || V > a.v_cap || V > 65535u) {
             if (tid == 0) {
                 atomicOr(a.err, kErrCapacity);

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kPT, 1) k_peel2(FuseSolveArgs a) {
                             old[k] = got;
                         }
                     }
-                    rec = make_uint4(v, other[0], other[1], a.val ? value : fingerprint(local, a.g.b));
+                    rec = make_uint4(v, other[0], other[1], a.val ? value : fingerprint_slice(local, a.g.b, a.g.fpb, a.g.fps));
                 }
             }
             const uint32_t slot = warp_reserve(&a.ctr[2], peel ? 1u : 0u);

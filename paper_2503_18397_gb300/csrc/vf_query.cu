@@ -123,6 +123,13 @@ __global__ void __launch_bounds__(kQThreads) k_query_batch(const QueryReq* __res
         const uint64_t local = local_of(s, r.g.h);
         uint64_t v[3];
         edge_of(r.g, local, v);
+        if (r.g.b > 32) {  // values wider than 32 bits
+            const uint64_t y = cell_get64(r.data, r.g.b, base + v[0]) ^ cell_get64(r.data, r.g.b, base + v[1]) ^
+                               cell_get64(r.data, r.g.b, base + v[2]);
+            if (r.g.kind == 1) static_cast<uint8_t*>(r.out)[i] = uint8_t(y == fingerprint64(local, r.g.b));
+            else static_cast<uint64_t*>(r.out)[i] = y;
+            continue;
+        }
         const uint32_t x = cell_get_nc(r.data, r.g.b, base + v[0]) ^ cell_get_nc(r.data, r.g.b, base + v[1]) ^
                            cell_get_nc(r.data, r.g.b, base + v[2]);
         if (r.g.kind == 1) static_cast<uint8_t*>(r.out)[i] = uint8_t(x == fingerprint(local, r.g.b));
@@ -145,6 +152,7 @@ cudaError_t launch_query(int key_kind, const void* keys, const uint64_t* offs, u
                          const uint8_t* data, void* out, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     bool bytes = key_kind != 0;
+    if (g.b > 32) return launch_query_wide(keys, bytes ? offs : nullptr, m, g, data, out, st);
     if (g.kind == 1) launch_w<true>(bytes, keys, offs, m, g, data, out, st);
     else launch_w<false>(bytes, keys, offs, m, g, data, out, st);
     return cudaGetLastError();

@@ -9,7 +9,7 @@
 //   64.. the vf_info fields, u64 / i32 / f64 in declaration order, then
 //   u64 dropped duplicates and i32 key kind.
 // The data array starts at byte 4096 in the device layout (shard s owns cells
-// [s*cells, (s+1)*cells); b in {8,16,32}: native little-endian; otherwise a
+// [s*cells, (s+1)*cells); b in {8,16,32,64}: native little-endian; otherwise a
 // bit array with one pad word), so a file can be mapped and used in place.
 #include <cstdio>
 #include <cstring>
@@ -89,7 +89,7 @@ void store_encode(const StoreHeader& h, uint8_t* out) {
 }
 
 static uint64_t data_bytes_of(const vf_info& i) {
-    if (i.b == 8 || i.b == 16 || i.b == 32) return i.total_cells * uint64_t(i.b / 8);
+    if (i.b == 8 || i.b == 16 || i.b == 32 || i.b == 64) return i.total_cells * uint64_t(i.b / 8);
     return ((i.total_cells * uint64_t(i.b) + 63) / 64 + 1) * 8;
 }
 
@@ -115,7 +115,7 @@ bool store_decode(const uint8_t* in, uint64_t avail, StoreHeader& h) {
     // consistency: a corrupt or foreign file is rejected, never half-used
     if (get_u64(in + 24) != i.data_bytes) return false;
     if (i.kind != VF_FUNC && i.kind != VF_FILTER) return false;
-    if (i.b < 1 || i.b > 32 || i.h < 0 || i.h > 40) return false;
+    if (i.b < 1 || i.b > 64 || i.h < 0 || i.h > 40) return false;
     if (i.regime != VF_REGIME_FUSE && i.regime != VF_REGIME_LGE && i.regime != VF_REGIME_MWHC) return false;
     if (i.shards != (uint64_t(1) << i.h) || i.cells == 0 || i.cells >= (uint64_t(1) << 32)) return false;
     if (i.total_cells != i.shards * i.cells || i.data_bytes != data_bytes_of(i)) return false;

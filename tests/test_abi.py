@@ -68,7 +68,7 @@ def test_plan_matches_oracle_over_many_sizes(vf, orc):
     ns = sorted(set([0, 1, 2, 1000, 799_999, 800_000, 2**20, 10**7, 10**8, 5 * 10**9, 10**10, 10**11, 10**12]
                     + [int(10 ** x) for x in rng.uniform(0, 13, 400)]))
     for n in ns:
-        for b in (1, 8, 13, 32):
+        for b in (1, 8, 13, 32, 33, 64):
             mean = n / (1 << max(0, 0))
             info, (h, regime, h_bb, h_dup), _ = _plan_pair(vf, orc, n, 1, b=b)
             assert (info.h, info.regime, info.h_bb, info.h_dup) == (h, regime, h_bb, h_dup), n

@@ -44,8 +44,9 @@ def dev(a: np.ndarray):
 
 
 def host(t) -> np.ndarray:
+    # int64 tensors are 64-bit results (values wider than 32 bits) or u64 keys
     m = {torch.uint16: (torch.int16, np.uint16), torch.uint32: (torch.int32, np.uint32),
-         torch.uint64: (torch.int64, np.uint64)}
+         torch.uint64: (torch.int64, np.uint64), torch.int64: (torch.int64, np.uint64)}
     if t.dtype in m:
         sd, nd = m[t.dtype]
         return t.view(sd).cpu().numpy().view(nd)
@@ -264,6 +265,41 @@ def test_mwhc_retries_match_oracle(vf, orc, solver):
         assert info.h == 8
         retried += info.retries > 0
     assert retried > 0
+
+
+# ------------------------------------------------------------ values wider than 32 bits
+
+@pytest.mark.parametrize("b", [33, 40, 63, 64])
+@pytest.mark.parametrize("regime", ["fuse", "lge", "mwhc"])
+def test_wide_function(vf, orc, b, regime):
+    # b > 32: two bit-plane slices on one hypergraph, packed into b-bit cells
+    n = {"fuse": 1_200_000, "lge": 50_000, "mwhc": 300_000}[regime]
+    keys = synth.u64_keys(0, n, 71)
+    vals = synth.values(n, b, 71)
+    extra = {"mode": vf.MODE_MWHC, "eps": 0.01, "eta": 1e-3} if regime == "mwhc" else {}
+    s, info, _ = check_build(vf, orc, keys, vals, b=b, seed=3, n_other=30_000, **extra)
+    assert info.b == b and info.regime == {"fuse": vf.REGIME_FUSE, "lge": vf.REGIME_LGE, "mwhc": vf.REGIME_MWHC}[regime]
+
+
+@pytest.mark.parametrize("b", [33, 64])
+def test_wide_filter(vf, orc, b):
+    n = 1_000_003
+    keys = with_repeats(n, 0.001, 72)
+    s, info, oi = check_build(vf, orc, keys, None, b=b, seed=5, n_other=100_000)
+    assert info.n_eff == oi.n_eff == n
+    assert host(s.query(dev(synth.u64_keys(n, 400_000, 72)))).sum() == 0
+
+
+def test_wide_byte_strings_and_host_buffers(vf, orc):
+    data, offs = synth.byte_strings(0, 40_000, 73)
+    vals = synth.values(40_000, 48, 73)
+    check_build(vf, orc, data, vals, offsets=offs, b=48, seed=1, n_other=5_000)
+    # host inputs and host output through the same entry points
+    keys = synth.u64_keys(0, 20_000, 74)
+    v = synth.values(20_000, 37, 74)
+    s = vf.vf_build(keys, v, params=vf.vf_params_default(b=37, seed=2))
+    out = s.query(keys)
+    assert out.dtype == np.uint64 and (out == v).all()
 
 
 def with_repeats(n, frac, seed, triples=False):
