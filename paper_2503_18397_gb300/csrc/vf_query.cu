@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(kQThreads) k_query(const void* __restrict__ ke
                     uint64_t o0 = __ldg(offs + idx[k]), o1 = __ldg(offs + idx[k] + 1);
                     s = sig_bytes(static_cast<const uint8_t*>(keys), total, o0, o1 - o0, g.kh, g.kl);
                 } else {
-                    s = sig_u64(__ldg(static_cast<const uint64_t*>(keys) + idx[k]), g.kh, g.kl);
+                    // keys are read once: evict-first, so the cells they probe stay in L2
+                    s = sig_u64(__ldcs(static_cast<const uint64_t*>(keys) + idx[k]), g.kh, g.kl);
                 }
             }
             uint64_t base = shard_of(s, g.h) * g.cells;
