@@ -128,7 +128,10 @@ void vf_params_default(vf_params *p);
  * memory, 32 GiB) of freed memory cached for the process (release threshold).
  * Errors: VF_EINVAL, VF_ENOMEM, VF_EBUILD, VF_ETIMEOUT, VF_ECUDA, VF_ECAPACITY
  * (a fuse shard above 2^27 keys; more than 2^30 keys with byte strings or in
- * the LGE regime). */
+ * the LGE regime; an LGE shard whose 2-core needs more active variables or
+ * coefficient rows than the solver's per-shard pool: 4096 active variables
+ * and 40 words per key up to 24576 keys, growing beyond; a 24576-key shard
+ * uses ~1500 and ~30). Only unsolvable systems are retried. */
 vf_status vf_build(const void *keys, const uint64_t *offsets, const void *values, uint64_t n,
                    const vf_params *params, void *stream, vf_struct **out);
 

@@ -562,7 +562,7 @@ vf_status run_lge_tasks(std::vector<vf::LgeTask>& tasks, bool lpt, const uint64_
     const uint64_t per_cta = vf::lge_scratch_words_per_cta(m_cap, v_cap);
     DevBuf scratch, misc, tbuf;
     VF_CK(scratch.alloc(per_cta * grid * 4, st));
-    VF_CK(misc.alloc(64, st));
+    VF_CK(misc.alloc(64 + 4 * tasks.size(), st));  // counters, then the spill list
     VF_CK(cudaMemsetAsync(misc.p, 0, 64, st));
     vf_status rs = h2d(tbuf, tasks, st);
     if (rs != VF_OK) return rs;
@@ -579,8 +579,9 @@ vf_status run_lge_tasks(std::vector<vf::LgeTask>& tasks, bool lpt, const uint64_
     a.v_cap = v_cap;
     a.err = misc.as<uint32_t>();
     a.stats = misc.as<uint32_t>() + 4;
+    a.spill = misc.as<uint32_t>() + 16;
     {
-        PhaseTimer t(kPhLge, st);
+        PhaseTimer t(kPhLge, st, 2);  // small configuration, then the spill list
         VF_CK(vf::launch_lge(a, grid, st));
     }
     uint32_t h[8];
@@ -602,8 +603,12 @@ vf_status solve_lge(const vf_info& in, const std::vector<unsigned long long>& st
     uint32_t err = 0;
     vf_status rs = run_lge_tasks(tasks, true, loc, val, nullptr, st, peeled, core, &err, dups);
     if (rs != VF_OK) return rs;
+    // A capacity failure is this solver's limit, not a property of the system:
+    // it ends the build (a retry would give another seed than the method's).
     if (err & vf::kErrCapacity) return fail(VF_ECAPACITY, "LGE shard exceeds the per-CTA solver capacity");
-    if (err & (vf::kErrUnsolvable | vf::kErrDegOverflow | vf::kErrLgeSize)) return VF_EBUILD;
+    if (err & vf::kErrLgeSize)
+        return fail(VF_ECAPACITY, "LGE shard needs more active variables or coefficient rows than the solver holds");
+    if (err & (vf::kErrUnsolvable | vf::kErrDegOverflow)) return VF_EBUILD;
     return VF_OK;
 }
 
@@ -749,7 +754,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     const uint64_t per_cta = vf::lge_scratch_words_per_cta(m_cap, v_cap);
     DevBuf scratch, misc, tbuf;
     VF_CK(scratch.alloc(per_cta * grid * 4, st));
-    VF_CK(misc.alloc(64, st));
+    VF_CK(misc.alloc(64 + 4 * tasks.size(), st));  // counters, then the spill list
     rs = h2d(tbuf, tasks, st);
     if (rs != VF_OK) return free_data(), rs;
     vf::LgeArgs a;
@@ -766,6 +771,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     a.v_cap = v_cap;
     a.err = misc.as<uint32_t>();
     a.stats = misc.as<uint32_t>() + 4;
+    a.spill = misc.as<uint32_t>() + 16;
     // scatter + solver: one CUDA graph (or plain launches)
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(fails.p, 0, std::max<uint64_t>(P, 1) * 8, q);
@@ -793,7 +799,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
         }
         e = cudaGraphInstantiate(&exec, graph, 0);
         if (e == cudaSuccess) {
-            PhaseTimer t(kPhLge, st, 2);  // scatter + solver
+            PhaseTimer t(kPhLge, st, 3);  // scatter + both solver configurations
             e = cudaGraphLaunch(exec, st);
         }
         if (exec) cudaGraphExecDestroy(exec);
@@ -803,7 +809,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
             return fail(VF_ECUDA, std::string("graph launch failed: ") + cudaGetErrorString(e));
         }
     } else {
-        PhaseTimer t(kPhLge, st, 2);  // scatter + solver
+        PhaseTimer t(kPhLge, st, 3);  // scatter + both solver configurations
         cudaError_t e = enqueue(st);
         if (e != cudaSuccess) {
             free_data();
@@ -837,7 +843,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     }
     VF_CK(cudaStreamSynchronize(st));
     for (uint32_t j = 0; j < P; j++) {
-        if (fail_bits[j] & vf::kErrCapacity) {
+        if (fail_bits[j] & (vf::kErrCapacity | vf::kErrLgeSize)) {
             free_data();
             return fail(VF_ECAPACITY, "batched LGE shard exceeds the solver capacity");
         }

@@ -26,7 +26,7 @@ constexpr uint32_t kErrTimeout = 1u << 1;       // a bounded wait gave up
 constexpr uint32_t kErrFrontier = 1u << 2;      // frontier or round buffer overflow
 constexpr uint32_t kErrCapacity = 1u << 3;      // shard larger than the solver handles
 constexpr uint32_t kErrUnsolvable = 1u << 4;    // a shard's system has no solution
-constexpr uint32_t kErrLgeSize = 1u << 5;       // LGE dense system or coefficient pool too large (retry)
+constexpr uint32_t kErrLgeSize = 1u << 5;       // LGE shard beyond the solver: active variables or coefficient rows
 constexpr uint32_t kErrLevel = 1u << 6;         // asynchronous peel: too many levels (use the round solver)
 
 // Stafford Mix13, the SplitMix64 output function.

@@ -165,16 +165,27 @@ struct LgeArgs {
     uint64_t scratch_words_per_cta;
     uint32_t m_cap, v_cap;            // largest shard / cell count the scratch layout holds
     uint32_t* err;                    // OR of all failure bits
-    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] task counter, [3] dropped duplicates
+    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] task counter, [3] dropped duplicates,
+                                      // [4] spill-list counter, [5] spilled tasks
     uint32_t* item_dup;               // per-structure dropped duplicate filter keys, or NULL
+    // Two-configuration launch: the spill list (room for ntasks indices) that the
+    // small configuration fills; NULL runs the large configuration alone.
+    uint32_t* spill;
+    const uint32_t* spill_in;         // set by launch_lge for the second launch
+    const uint32_t* spilled;          // count of spill_in (device), set by launch_lge
 };
 // Layout (in 32-bit words) of one CTA's LGE scratch slab for shards of at most
 // m keys and V cells.
-constexpr uint32_t kMaxActive = 2048;  // active variables per shard
-constexpr uint32_t kLPoolPerKey = 40;  // words of coefficient rows per shard key
+constexpr uint32_t kMaxActive = 4096;  // active variables per shard (up to kLgeBigShard keys)
+constexpr uint32_t kLPoolPerKey = 40;  // words of coefficient rows per shard key (up to kLgeBigShard keys)
+// Above kLgeBigShard keys (the regime's default largest shard) both grow with
+// the shard: ~6.6% of a shard's keys become active variables, and the affine
+// rows take ~0.0011 m words per key.
+constexpr uint32_t kLgeBigShard = 24576;
 struct LgeOffsets {
     uint64_t cev, porder, proff, f0, f1, cand, core, eqst, eqdone, inc_off, inc_cur, inc_list, vstate, act, actv,
         solves, soff, dense, lc, L, lpool, total;
+    uint32_t a_cap;  // active variables a shard may have
 };
 
 __host__ __device__ constexpr uint64_t lge_take(uint64_t& p, uint64_t words) {
@@ -200,12 +211,14 @@ __host__ __device__ constexpr LgeOffsets lge_offsets(uint32_t m, uint32_t V) {
     o.inc_list = lge_take(p, 3ull * m);
     o.vstate = lge_take(p, V);
     o.act = lge_take(p, V);
-    o.actv = lge_take(p, kMaxActive);
+    const uint64_t big = m > kLgeBigShard ? m - kLgeBigShard : 0;
+    o.a_cap = uint32_t(kMaxActive + big / 8);
+    o.actv = lge_take(p, o.a_cap);
     o.solves = lge_take(p, m);
     o.soff = lge_take(p, uint64_t(m) + V + 4);
     o.dense = lge_take(p, m);
     o.lc = lge_take(p, m);
-    o.lpool = uint64_t(m) * kLPoolPerKey + 4096;
+    o.lpool = uint64_t(m) * (kLPoolPerKey + big / 500) + 4096;
     o.L = lge_take(p, o.lpool);
     o.total = p;
     return o;

@@ -18,13 +18,29 @@
 //     round by round, the dense rows are reduced by Gauss-Jordan elimination
 //     in shared memory (free variables = 0), solved variables are evaluated
 //     forward, and peeled edges are assigned in reverse peel order.
+//
+// Two configurations of the kernel share this code. Each round of steps 2-3
+// ends in a CTA barrier, so one CTA per SM leaves the SM idle at every
+// barrier; the small configuration (256 threads, 108 KB of shared memory, two
+// CTAs per SM) overlaps two shards instead. A shard whose peel arrays or dense
+// system do not fit its 108 KB is handed, unchanged, to the spill list, which
+// the large configuration (512 threads, 200 KB, one CTA per SM) then solves
+// from the start: both configurations solve the same system, so which one ran
+// changes neither the outcome nor the retry count.
+#include <algorithm>
+#include <atomic>
+
 #include "vf_internal.h"
 
 namespace vf {
 
-constexpr int kLT = 512;
 constexpr uint32_t kMaxBatch = 256;
-constexpr uint32_t kLgeSmemWords = 50 * 1024;  // 200 KB dynamic shared memory
+// large configuration: 512 threads, 200 KB dynamic shared memory, 1 CTA per SM
+constexpr int kBigT = 512;
+constexpr uint32_t kBigWords = 50 * 1024;
+// small configuration: 256 threads, 108 KB, 2 CTAs per SM
+constexpr int kSmallT = 256;
+constexpr uint32_t kSmallWords = 27 * 1024;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 uint64_t lge_scratch_words_per_cta(uint32_t m_cap, uint32_t v_cap) { return lge_offsets(m_cap, v_cap).total; }
@@ -67,7 +83,16 @@ __device__ void cta_exclusive_scan(uint32_t* arr, uint32_t len, uint32_t* s_part
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
+// Hands task s to the spill list (small configuration) and reports whether
+// it did; the large configuration has no spill list and fails the shard.
+__device__ __forceinline__ bool spill_task(const LgeArgs& a, uint32_t s) {
+    if (!a.spill) return false;
+    if (threadIdx.x == 0) a.spill[atomicAdd(&a.stats[5], 1u)] = s;
+    return true;
+}
+
+template <int kLT, uint32_t kLgeSmemWords, int kMinBlocks>
+__global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ uint32_t s_shard, s_fail;
     __shared__ uint32_t s_cnt[4];
@@ -100,18 +125,23 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
     uint32_t* L = scr + o.L;
     constexpr uint32_t kBad = kErrUnsolvable | kErrCapacity | kErrLgeSize | kErrDegOverflow;
 
+    // The large configuration behind a small one takes its tasks from the
+    // spill list (written by the previous launch), otherwise from all tasks.
+    const bool from_spill = a.spilled != nullptr;
+    const uint32_t ntasks = from_spill ? *a.spilled : a.ntasks;
     for (;;) {
         __shared__ uint32_t s_skip;
         if (tid == 0) {
-            s_shard = atomicAdd(&a.stats[2], 1u);
-            s_skip = s_shard < a.ntasks &&
+            const uint32_t q = atomicAdd(&a.stats[from_spill ? 4 : 2], 1u);
+            s_shard = q < ntasks ? (from_spill ? a.spill_in[q] : q) : kNone;
+            s_skip = s_shard != kNone &&
                      (*reinterpret_cast<volatile uint32_t*>(a.item_fail + a.tasks[s_shard].item) & kBad) != 0;
             s_fail = 0;
             s_dup = 0;
         }
         __syncthreads();
         const uint32_t s = s_shard;
-        if (s >= a.ntasks) break;
+        if (s == kNone) break;
         if (s_skip) {  // another shard of this structure already failed: the attempt is void
             __syncthreads();
             continue;
@@ -148,6 +178,14 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
         uint32_t* xrw = degw + (V + 3) / 4;
         uint32_t* clm = xrw + (V + 1) / 2;
         const uint32_t pw = (V + 3) / 4 + (V + 1) / 2 + (m + 31) / 32;
+        if (pw > kLgeSmemWords) {
+            if (!spill_task(a, s) && tid == 0) {
+                atomicOr(a.err, kErrCapacity);
+                atomicOr(a.item_fail + task.item, kErrCapacity);
+            }
+            __syncthreads();
+            continue;
+        }
         for (uint32_t i = tid; i < pw; i += T) sm[i] = 0;
         __syncthreads();
         for (uint32_t e = tid; e < m; e += T) {
@@ -357,7 +395,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                         const uint32_t nb = min(K, tot);
                         s_apos = tot >= K ? s_nbatch : base + wn;
                         s_nbatch = nb;
-                        if (s_A + nb > kMaxActive || (nb == 0 && s_apos >= s_nact)) s_fail = 2;
+                        if (s_A + nb > o.a_cap || (nb == 0 && s_apos >= s_nact)) s_fail = 2;
                     }
                     __syncthreads();
                     if (s_fail) break;
@@ -446,7 +484,13 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
             const uint32_t A = s_A, S = s_S, D = s_D, R = s_r;
             const uint32_t AW = (A + 31) / 32;
             const uint32_t RS = AW | 1u;  // odd row stride: conflict-free shared-memory rows
-            if (uint64_t(S) * AW > o.lpool || uint64_t(D) * RS + 2ull * D + A > kLgeSmemWords) {
+            // The dense system (rows, right-hand sides, pivot flags, column map) is
+            // solved in shared memory when it fits, else in the slab after the
+            // affine rows (large shards only; L2-resident, slower).
+            const uint64_t rows_off = (uint64_t(S) * AW + 3) & ~uint64_t(3);
+            const uint64_t dense_words = uint64_t(D) * RS + 2ull * D + A;
+            const bool dense_smem = dense_words <= kLgeSmemWords;
+            if (uint64_t(S) * AW > o.lpool || (!dense_smem && rows_off + dense_words > o.lpool)) {
                 if (tid == 0) {
                     atomicOr(a.err, kErrLgeSize);
                     atomicOr(a.item_fail + task.item, kErrLgeSize);
@@ -482,8 +526,7 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
                 }
                 __syncthreads();
             }
-            // dense rows in shared memory
-            uint32_t* rows = sm;
+            uint32_t* rows = dense_smem ? sm : L + rows_off;
             uint32_t* rhs = rows + uint64_t(D) * RS;
             uint32_t* pivf = rhs + D;
             uint32_t* colrow = pivf + D;
@@ -593,22 +636,47 @@ __global__ void __launch_bounds__(kLT, 1) k_lge(LgeArgs a) {
     }
 }
 
-unsigned lge_grid() {
-    static unsigned g = 0;
-    if (g == 0) {
-        cudaFuncSetAttribute(k_lge, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLgeSmemWords * 4));
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lge, kLT, kLgeSmemWords * 4);
-        if (per_sm < 1) per_sm = 1;
-        g = unsigned(per_sm) * unsigned(num_sms());
+#define VF_LGE_SMALL k_lge<kSmallT, kSmallWords, 2>
+#define VF_LGE_BIG k_lge<kBigT, kBigWords, 1>
+
+// Resident CTAs of one configuration on the whole GPU (attributes set once per device).
+static unsigned resident(bool small) {
+    static std::atomic<uint64_t> done{0};
+    static unsigned per_sm_small = 1, per_sm_big = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (!(done.load() & bit)) {
+        int ps = 0, pb = 0;
+        cudaFuncSetAttribute(VF_LGE_SMALL, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmallWords * 4));
+        cudaFuncSetAttribute(VF_LGE_BIG, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBigWords * 4));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, VF_LGE_SMALL, kSmallT, kSmallWords * 4);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, VF_LGE_BIG, kBigT, kBigWords * 4);
+        per_sm_small = unsigned(ps < 1 ? 1 : ps);
+        per_sm_big = unsigned(pb < 1 ? 1 : pb);
+        done.fetch_or(bit);
     }
-    return g;
+    return (small ? per_sm_small : per_sm_big) * unsigned(num_sms());
 }
+
+unsigned lge_grid() { return std::max(resident(true), resident(false)); }
 
 cudaError_t launch_lge(const LgeArgs& a, unsigned grid, cudaStream_t st) {
     if (a.ntasks == 0) return cudaSuccess;
-    lge_grid();
-    k_lge<<<grid, kLT, kLgeSmemWords * 4, st>>>(a);
+    if (!a.spill) {  // large configuration alone
+        VF_LGE_BIG<<<std::min(grid, resident(false)), kBigT, kBigWords * 4, st>>>(a);
+        return cudaGetLastError();
+    }
+    LgeArgs first = a;
+    first.spilled = nullptr;
+    VF_LGE_SMALL<<<std::min(grid, resident(true)), kSmallT, kSmallWords * 4, st>>>(first);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    LgeArgs second = a;
+    second.spill = nullptr;
+    second.spilled = a.stats + 5;
+    second.spill_in = a.spill;
+    VF_LGE_BIG<<<std::min(grid, resident(false)), kBigT, kBigWords * 4, st>>>(second);
     return cudaGetLastError();
 }
 

@@ -170,8 +170,8 @@ extern "C" vf_status vf_build_static(const uint64_t* keys, const void* values, u
         if (cudaMemcpyAsync(h, misc, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return fail_static(VF_ECUDA, "vf_build_static: reading the outcome failed");
-        if (h[0] & kErrCapacity) return fail_static(VF_ECAPACITY, "vf_build_static: shard exceeds the solver");
-        if (h[0] & (kErrUnsolvable | kErrDegOverflow | kErrLgeSize)) continue;
+        if (h[0] & (kErrCapacity | kErrLgeSize)) return fail_static(VF_ECAPACITY, "vf_build_static: shard exceeds the solver");
+        if (h[0] & (kErrUnsolvable | kErrDegOverflow)) continue;
         in.peeled = h[4];
         in.core = h[5];
         in.rounds = 0;

@@ -112,6 +112,25 @@ def test_batch_all_lge_threshold_and_tuner(vf, orc):
     assert ms2 == -1.0 and best2.as_dict() == best.as_dict()  # cached per batch shape
 
 
+def test_batch_large_shards(vf, orc):
+    # single-shard structures of 20K-24.5K keys next to small ones: the largest
+    # dense systems are solved outside shared memory, in the same launch as
+    # shards solved inside it; every structure keeps the oracle's seed and retries
+    sizes = [24_000, 500, 21_000, 23_500, 7_000, 60_000, 24_500, 20_000]
+    items, host = _make(sizes, 17)
+    structs = vf.vf_build_batch(items, opts=vf.vf_batch_opts_default(lge_target=24_576))
+    for (kd, vd, kind, b, seed), (keys, vals, _, _), s in zip(items, host, structs):
+        info = s.info
+        out = _host(s.query(kd))
+        assert (out == vals).all() if kind == 0 else out.all()
+        op = orc.default_params(kind=kind, b=b, seed=seed, lge_target=24_576)
+        st, oi, _ = orc.build(op, keys, vals)
+        assert st == orc.OK
+        for f in FIELDS:
+            assert getattr(info, f) == getattr(oi, f), f
+        s.free()
+
+
 def test_batch_filter_duplicate_keys(vf, orc):
     # filters with repeated keys inside a batch: copies are dropped per shard in the
     # LGE solver (Sec. 4.5); n_eff and every query equal the oracle's build

@@ -147,6 +147,36 @@ def test_filter_lge_regime(vf, orc, b):
     assert info.h >= 2 and info.core > 0
 
 
+@pytest.mark.parametrize("kind", ["func", "filter"])
+@pytest.mark.parametrize("n,s", [(22_000, 2), (24_000, 1)])
+def test_lge_large_shard_dense_system_in_slab(vf, orc, kind, n, s):
+    # One LGE shard of 22K-24K keys, near the largest shard the regime allows:
+    # its dense system (~1000 rows over ~1450 active variables) outgrows shared
+    # memory and is solved in the CTA's global slab. Seed and retries must stay
+    # the oracle's (a capacity failure would retry where the oracle does not).
+    keys = synth.u64_keys(s * 1_000_003, n, 77)
+    vals = synth.values(n, 8, 77) if kind == "func" else None
+    st, info, _ = check_build(vf, orc, keys, vals, b=8, mode=vf.MODE_LGE, lge_target=24_576, seed=5 + s,
+                              n_other=5000)
+    assert info.shards == 1 and info.retries == 0
+
+
+def test_lge_peel_arrays_spill_to_large_configuration(vf, orc):
+    # 8 shards of ~31K keys whose peel arrays (cells/4 + cells/2 + keys/32 words)
+    # straddle the small solver configuration's 27648 words: 6 shards go through
+    # the spill list to the large configuration, 2 stay in the small one
+    n = 250_950
+    keys = synth.u64_keys(0, n, 78)
+    vals = synth.values(n, 16, 78)
+    st, info, _ = check_build(vf, orc, keys, vals, b=16, mode=vf.MODE_LGE, lge_target=36_000, lge_max_shard=60_000,
+                              seed=6, n_other=5000)
+    assert info.shards == 8 and info.retries == 0
+    sh, _ = orc.shard_local(orc.sigs(keys, info.seed), info.h)
+    m = np.bincount(sh, minlength=8)
+    words = -(-info.cells // 4) + -(-info.cells // 2) + -(-m // 32)
+    assert 0 < int((words > 27 * 1024).sum()) < 8
+
+
 def test_lge_sharded_byte_strings(vf, orc):
     n = 60_000
     data, offs = synth.byte_strings(0, n, 5)
