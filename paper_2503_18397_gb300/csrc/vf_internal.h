@@ -184,7 +184,7 @@ constexpr uint32_t kLPoolPerKey = 40;  // words of coefficient rows per shard ke
 constexpr uint32_t kLgeBigShard = 24576;
 struct LgeOffsets {
     uint64_t cev, porder, proff, f0, f1, cand, core, eqst, eqdone, inc_off, inc_cur, inc_list, vstate, act, actv,
-        solves, soff, dense, lc, L, lpool, total;
+        solves, soff, srec, dense, lc, L, lpool, total;
     uint32_t a_cap;  // active variables a shard may have
 };
 
@@ -216,6 +216,7 @@ __host__ __device__ constexpr LgeOffsets lge_offsets(uint32_t m, uint32_t V) {
     o.actv = lge_take(p, o.a_cap);
     o.solves = lge_take(p, m);
     o.soff = lge_take(p, uint64_t(m) + V + 4);
+    o.srec = lge_take(p, 4ull * m);  // one uint4 per solve
     o.dense = lge_take(p, m);
     o.lc = lge_take(p, m);
     o.lpool = uint64_t(m) * (kLPoolPerKey + big / 500) + 4096;

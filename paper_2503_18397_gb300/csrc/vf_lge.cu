@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
     uint32_t* actv = scr + o.actv;
     uint32_t* solves = scr + o.solves;
     uint32_t* soff = scr + o.soff;
+    uint4* srec = reinterpret_cast<uint4*>(scr + o.srec);
     uint32_t* dense = scr + o.dense;
     uint32_t* lc = scr + o.lc;
     uint32_t* L = scr + o.L;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
         gg.kind = task.kind;
         gg.fpb = task.fpb;
         gg.fps = task.fps;
-        if (m > a.m_cap || V > a.v_cap || V > 65535u) {
+        if (m > a.m_cap || V > a.v_cap || V > 65535u || m > 65535u) {
             if (tid == 0) {
                 atomicOr(a.err, kErrCapacity);
                 atomicOr(a.item_fail + task.item, kErrCapacity);
@@ -498,6 +499,18 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 __syncthreads();
                 continue;
             }
+            // One record per solve, gathered for all solves at once: the solved
+            // cell x, its equation's edge e, the two other cells and their states
+            // (final when x was solved: active, or solved in an earlier round). The
+            // rounds below then wait on two dependent loads instead of five.
+            for (uint32_t si = tid; si < S; si += T) {
+                const uint32_t sv = __ldcg(&solves[si]);
+                const uint32_t x = sv & 0xFFFFu, e = __ldcg(&core[sv >> 16]);
+                const uint32_t c0 = __ldcg(&cev[3 * e]), c1 = __ldcg(&cev[3 * e + 1]), c2 = __ldcg(&cev[3 * e + 2]);
+                const uint32_t u1 = c0 == x ? c1 : c0, u2 = c2 == x ? c1 : c2;
+                srec[si] = make_uint4(x | (e << 16), u1 | (u2 << 16), __ldcg(&vstate[u1]), __ldcg(&vstate[u2]));
+            }
+            __syncthreads();
             // solved variables as affine functions of the active ones, round by round
             for (uint32_t r = 0; r < R; r++) {
                 const uint32_t lo = __ldcg(&soff[r]), hi = __ldcg(&soff[r + 1]);
@@ -505,24 +518,21 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 const uint32_t items = (hi - lo) * AW;
                 for (uint32_t it = tid; it < items; it += T) {
                     const uint32_t si = lo + it / AW, w = it % AW;
-                    const uint32_t j = __ldcg(&solves[si]) >> 16, x = __ldcg(&solves[si]) & 0xFFFFu;
-                    const uint32_t e = __ldcg(&core[j]);
+                    const uint4 q = __ldcg(&srec[si]);
+                    const uint32_t st[2] = {q.z, q.w};
                     uint32_t acc = 0, c = 0;
 #pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        uint32_t u = __ldcg(&cev[3 * e + k]);
-                        if (u == x) continue;
-                        uint32_t st = __ldcg(&vstate[u]);
-                        if ((st & 3u) == 1u) {
-                            uint32_t ai = st >> 2;
+                    for (int k = 0; k < 2; k++) {
+                        if ((st[k] & 3u) == 1u) {
+                            const uint32_t ai = st[k] >> 2;
                             if ((ai >> 5) == w) acc ^= 1u << (ai & 31u);
                         } else {
-                            acc ^= __ldcg(&L[uint64_t(st >> 2) * AW + w]);
-                            c ^= __ldcg(&lc[st >> 2]);
+                            acc ^= __ldcg(&L[uint64_t(st[k] >> 2) * AW + w]);
+                            if (w == 0) c ^= __ldcg(&lc[st[k] >> 2]);
                         }
                     }
                     L[uint64_t(si) * AW + w] = acc;
-                    if (w == 0) lc[si] = c ^ rhs_of(a, task, e0 + e);
+                    if (w == 0) lc[si] = c ^ rhs_of(a, task, e0 + (q.x >> 16));
                 }
                 __syncthreads();
             }
@@ -596,15 +606,10 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 const uint32_t lo = __ldcg(&soff[r]), hi = __ldcg(&soff[r + 1]);
                 if (hi == lo) continue;
                 for (uint32_t si = lo + tid; si < hi; si += T) {
-                    const uint32_t j = __ldcg(&solves[si]) >> 16, x = __ldcg(&solves[si]) & 0xFFFFu;
-                    const uint32_t e = __ldcg(&core[j]);
-                    uint32_t val = rhs_of(a, task, e0 + e);
-#pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        uint32_t u = __ldcg(&cev[3 * e + k]);
-                        if (u != x) val ^= cell_get_cg(data, b, cbase + u);
-                    }
-                    cell_put_zero(data, b, cbase + x, val);
+                    const uint4 q = __ldcg(&srec[si]);
+                    const uint32_t val = rhs_of(a, task, e0 + (q.x >> 16)) ^ cell_get_cg(data, b, cbase + (q.y & 0xFFFFu)) ^
+                                         cell_get_cg(data, b, cbase + (q.y >> 16));
+                    cell_put_zero(data, b, cbase + (q.x & 0xFFFFu), val);
                 }
                 __syncthreads();
             }
