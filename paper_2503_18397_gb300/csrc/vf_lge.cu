@@ -338,6 +338,15 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 }
                 __syncthreads();
             }
+            // The incidence offsets (at most 3C) go to shared memory as 16-bit
+            // entries after the states when they fit: the elimination rounds then
+            // read only the incidence list itself from the slab.
+            uint16_t* ioff16 = nullptr;
+            if (in_smem && 3ull * C < 65536 && uint64_t(V) + C + (V + 2) / 2 <= kLgeSmemWords) {
+                ioff16 = reinterpret_cast<uint16_t*>(sm + V + C);
+                for (uint32_t v = tid; v <= V; v += T) ioff16[v] = uint16_t(__ldcg(&inc_off[v]));
+            }
+            auto off_of = [&](uint32_t v) -> uint32_t { return ioff16 ? uint32_t(ioff16[v]) : __ldcg(&inc_off[v]); };
             if (tid == 0) {
                 s_rem = C - s_dup;
                 s_A = s_S = s_D = s_r = s_apos = s_lo = 0;
@@ -369,8 +378,8 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                     if (tid < wn) {
                         v = __ldcg(&act[base + tid]);
                         if (vst[v] == 0) {
-                            const uint32_t q1 = __ldcg(&inc_off[v + 1]);
-                            for (uint32_t q = __ldcg(&inc_off[v]); q < q1 && !elig; q++)
+                            const uint32_t q1 = off_of(v + 1);
+                            for (uint32_t q = off_of(v); q < q1 && !elig; q++)
                                 elig = (est[__ldcg(&inc_list[q])] & 4u) == 0;
                         }
                     }
@@ -405,8 +414,8 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                         const uint32_t u = s_batch[i];
                         vst[u] = 1u | ((abase + i) << 2);
                         actv[abase + i] = u;
-                        const uint32_t q1 = __ldcg(&inc_off[u + 1]);
-                        for (uint32_t q = __ldcg(&inc_off[u]); q < q1; q++) {
+                        const uint32_t q1 = off_of(u + 1);
+                        for (uint32_t q = off_of(u); q < q1; q++) {
                             const uint32_t k = __ldcg(&inc_list[q]);
                             if (est[k] & 4u) continue;
                             const uint32_t old = atomicSub(&est[k], 1u);
@@ -426,6 +435,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 } else {
                     const uint32_t* F = fr[fi];
                     const uint32_t lo = s_lo;  // solves of earlier rounds; s_S moves below
+                    uint32_t mine = kNone;     // this thread's solve (rounds of at most T entries)
                     for (uint32_t i = tid; i < nF; i += T) {
                         const uint32_t j = __ldcg(&F[i]);
                         const uint32_t w = est[j];
@@ -434,17 +444,17 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                         if (atomicCAS(&vst[x], 0u, 3u) != 0u) continue;
                         const uint32_t si = atomicAdd(&s_S, 1u);
                         vst[x] = 2u | (si << 2);
-                        solves[si] = (j << 16) | x;
+                        mine = (j << 16) | x;
+                        solves[si] = mine;
                         atomicOr(&est[j], 4u);
                         atomicSub(&s_rem, 1u);
                     }
                     __syncthreads();
-                    const uint32_t hi = s_S;
-                    for (uint32_t si = lo + tid; si < hi; si += T) {
-                        const uint32_t sv = __ldcg(&solves[si]);
+                    // eliminate each variable solved this round from its other equations
+                    auto eliminate = [&](uint32_t sv) {
                         const uint32_t j = sv >> 16, x = sv & 0xFFFFu;
-                        const uint32_t q1 = __ldcg(&inc_off[x + 1]);
-                        for (uint32_t q = __ldcg(&inc_off[x]); q < q1; q++) {
+                        const uint32_t q1 = off_of(x + 1);
+                        for (uint32_t q = off_of(x); q < q1; q++) {
                             const uint32_t k = __ldcg(&inc_list[q]);
                             if (k == j || (est[k] & 4u)) continue;
                             const uint32_t old = atomicSub(&est[k], 1u);
@@ -458,6 +468,12 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                                 atomicSub(&s_rem, 1u);
                             }
                         }
+                    };
+                    if (nF <= T) {  // each solve is still in the register of the thread that made it
+                        if (mine != kNone) eliminate(mine);
+                    } else {
+                        const uint32_t hi = s_S;
+                        for (uint32_t si = lo + tid; si < hi; si += T) eliminate(__ldcg(&solves[si]));
                     }
                     __syncthreads();
                 }
