@@ -347,6 +347,23 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 for (uint32_t v = tid; v <= V; v += T) ioff16[v] = uint16_t(__ldcg(&inc_off[v]));
             }
             auto off_of = [&](uint32_t v) -> uint32_t { return ioff16 ? uint32_t(ioff16[v]) : __ldcg(&inc_off[v]); };
+            // The rest of shared memory holds the first qcap entries of the two
+            // round queues; entries beyond stay in the slab's queues.
+            uint32_t qcap = 0;
+            uint32_t* sq0 = nullptr;
+            if (in_smem) {
+                const uint32_t used = (V + C + (ioff16 ? (V + 2) / 2 : 0) + 3) & ~3u;
+                qcap = used < kLgeSmemWords ? (kLgeSmemWords - used) / 2 : 0;
+                sq0 = sm + used;
+            }
+            auto qpush = [&](uint32_t q, uint32_t k) {
+                const uint32_t idx = atomicAdd(&s_cnt[q], 1u);
+                if (idx < qcap) sq0[q * qcap + idx] = k;
+                else fr[q][idx] = k;
+            };
+            auto qread = [&](uint32_t q, uint32_t i) -> uint32_t {
+                return i < qcap ? sq0[q * qcap + i] : __ldcg(&fr[q][i]);
+            };
             if (tid == 0) {
                 s_rem = C - s_dup;
                 s_A = s_S = s_D = s_r = s_apos = s_lo = 0;
@@ -365,7 +382,6 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                     break;
                 }
                 const uint32_t nF = s_cnt[fi];
-                uint32_t* G = fr[fi ^ 1];
                 if (nF == 0) {
                     // Activate the next heaviest idle variables that still occur in
                     // open equations: the block examines a window of the activation
@@ -422,7 +438,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                             atomicXor(&est[k], u << 3);
                             const uint32_t c = (old & 3u) - 1u;
                             if (c == 1u) {
-                                G[atomicAdd(&s_cnt[fi ^ 1], 1u)] = k;
+                                qpush(fi ^ 1, k);
                             } else if (c == 0u) {
                                 atomicOr(&est[k], 4u);
                                 dense[atomicAdd(&s_D, 1u)] = k;
@@ -433,11 +449,10 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                     __syncthreads();
                     if (tid == 0) s_A += nb;
                 } else {
-                    const uint32_t* F = fr[fi];
                     const uint32_t lo = s_lo;  // solves of earlier rounds; s_S moves below
                     uint32_t mine = kNone;     // this thread's solve (rounds of at most T entries)
                     for (uint32_t i = tid; i < nF; i += T) {
-                        const uint32_t j = __ldcg(&F[i]);
+                        const uint32_t j = qread(fi, i);
                         const uint32_t w = est[j];
                         if ((w & 4u) || (w & 3u) != 1u) continue;
                         const uint32_t x = w >> 3;
@@ -461,7 +476,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                             atomicXor(&est[k], x << 3);
                             const uint32_t c = (old & 3u) - 1u;
                             if (c == 1u) {
-                                G[atomicAdd(&s_cnt[fi ^ 1], 1u)] = k;
+                                qpush(fi ^ 1, k);
                             } else if (c == 0u) {
                                 atomicOr(&est[k], 4u);
                                 dense[atomicAdd(&s_D, 1u)] = k;
