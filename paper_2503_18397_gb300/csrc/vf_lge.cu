@@ -609,7 +609,17 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 }
                 for (uint32_t d = tid; d < D; d += T) {
                     if (d == p || !(rows[d * RS + cw] & cb)) continue;
-                    for (uint32_t w = cw; w < AW; w++) rows[d * RS + w] ^= rows[p * RS + w];
+                    // rows d and p never alias: four words of each are loaded
+                    // before any is stored, so the round trips overlap
+                    uint32_t* rd = rows + d * RS;
+                    const uint32_t* rp = rows + p * RS;
+                    uint32_t w = cw;
+                    for (; w + 4 <= AW; w += 4) {
+                        const uint32_t a0 = rd[w], a1 = rd[w + 1], a2 = rd[w + 2], a3 = rd[w + 3];
+                        const uint32_t b0 = rp[w], b1 = rp[w + 1], b2 = rp[w + 2], b3 = rp[w + 3];
+                        rd[w] = a0 ^ b0, rd[w + 1] = a1 ^ b1, rd[w + 2] = a2 ^ b2, rd[w + 3] = a3 ^ b3;
+                    }
+                    for (; w < AW; w++) rd[w] ^= rp[w];
                     rhs[d] ^= rhs[p];
                 }
                 if (tid == 0) {
