@@ -595,7 +595,9 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
             for (uint32_t c = tid; c < A; c += T) colrow[c] = kNone;
             __syncthreads();
             // Gauss-Jordan over GF(2): pivot = lowest unused row with the column bit
-            for (uint32_t col = 0; col < A; col++) {
+            // once every row is a pivot no later column can have one (its active
+            // variable stays free, 0): the loop ends there
+            for (uint32_t col = 0, npiv = 0; col < A && npiv < D; col++) {
                 const uint32_t cw = col >> 5, cb = 1u << (col & 31u);
                 if (tid == 0) s_piv = kNone;
                 __syncthreads();
@@ -626,6 +628,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                     pivf[p] = 1;
                     colrow[col] = p;
                 }
+                npiv++;
                 __syncthreads();
             }
             for (uint32_t d = tid; d < D; d += T)
