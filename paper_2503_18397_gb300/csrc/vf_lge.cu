@@ -534,12 +534,17 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
             // cell x, its equation's edge e, the two other cells and their states
             // (final when x was solved: active, or solved in an earlier round). The
             // rounds below then wait on two dependent loads instead of five.
+            // Shared memory is idle until the dense system is built: the affine
+            // rounds read the records from there when they fit.
+            uint4* const srs = 4ull * S <= kLgeSmemWords ? reinterpret_cast<uint4*>(sm) : nullptr;
             for (uint32_t si = tid; si < S; si += T) {
                 const uint32_t sv = __ldcg(&solves[si]);
                 const uint32_t x = sv & 0xFFFFu, e = __ldcg(&core[sv >> 16]);
                 const uint32_t c0 = __ldcg(&cev[3 * e]), c1 = __ldcg(&cev[3 * e + 1]), c2 = __ldcg(&cev[3 * e + 2]);
                 const uint32_t u1 = c0 == x ? c1 : c0, u2 = c2 == x ? c1 : c2;
-                srec[si] = make_uint4(x | (e << 16), u1 | (u2 << 16), __ldcg(&vstate[u1]), __ldcg(&vstate[u2]));
+                const uint4 rec = make_uint4(x | (e << 16), u1 | (u2 << 16), __ldcg(&vstate[u1]), __ldcg(&vstate[u2]));
+                srec[si] = rec;
+                if (srs) srs[si] = rec;
             }
             __syncthreads();
             // solved variables as affine functions of the active ones, round by round
@@ -549,7 +554,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 const uint32_t items = (hi - lo) * AW;
                 for (uint32_t it = tid; it < items; it += T) {
                     const uint32_t si = lo + it / AW, w = it % AW;
-                    const uint4 q = __ldcg(&srec[si]);
+                    const uint4 q = srs ? srs[si] : __ldcg(&srec[si]);
                     const uint32_t st[2] = {q.z, q.w};
                     uint32_t acc = 0, c = 0;
 #pragma unroll
