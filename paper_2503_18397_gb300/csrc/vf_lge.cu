@@ -535,8 +535,9 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
             // (final when x was solved: active, or solved in an earlier round). The
             // rounds below then wait on two dependent loads instead of five.
             // Shared memory is idle until the dense system is built: the affine
-            // rounds read the records from there when they fit.
-            uint4* const srs = 4ull * S <= kLgeSmemWords ? reinterpret_cast<uint4*>(sm) : nullptr;
+            // rounds read the records from its top end when they fit, and so does
+            // the back-substitution if the dense system leaves them room.
+            uint4* const srs = 4ull * S <= kLgeSmemWords ? reinterpret_cast<uint4*>(sm + (kLgeSmemWords - 4 * S)) : nullptr;
             for (uint32_t si = tid; si < S; si += T) {
                 const uint32_t sv = __ldcg(&solves[si]);
                 const uint32_t x = sv & 0xFFFFu, e = __ldcg(&core[sv >> 16]);
@@ -650,12 +651,14 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
             for (uint32_t c = tid; c < A; c += T)
                 cell_put_zero(data, b, cbase + __ldcg(&actv[c]), colrow[c] != kNone ? rhs[colrow[c]] : 0u);
             __syncthreads();
+            const uint4* const srs_bs =
+                srs && (!dense_smem || dense_words + 4ull * S <= kLgeSmemWords) ? srs : nullptr;
             // solved variables, in solve order (their equations as generated)
             for (uint32_t r = 0; r < R; r++) {
                 const uint32_t lo = __ldcg(&soff[r]), hi = __ldcg(&soff[r + 1]);
                 if (hi == lo) continue;
                 for (uint32_t si = lo + tid; si < hi; si += T) {
-                    const uint4 q = __ldcg(&srec[si]);
+                    const uint4 q = srs_bs ? srs_bs[si] : __ldcg(&srec[si]);
                     const uint32_t val = rhs_of(a, task, e0 + (q.x >> 16)) ^ cell_get_cg(data, b, cbase + (q.y & 0xFFFFu)) ^
                                          cell_get_cg(data, b, cbase + (q.y >> 16));
                     cell_put_zero(data, b, cbase + (q.x & 0xFFFFu), val);
