@@ -364,6 +364,34 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
             auto qread = [&](uint32_t q, uint32_t i) -> uint32_t {
                 return i < qcap ? sq0[q * qcap + i] : __ldcg(&fr[q][i]);
             };
+            // Removes variable u (now solved from equation `skip`, or active) from
+            // every other open equation; an equation left with one idle variable
+            // joins the next round's queue, one left with none joins the dense
+            // system. Incidence entries are loaded four at a time, before any
+            // equation is touched, so their global loads overlap.
+            auto remove_var = [&](uint32_t u, uint32_t skip, uint32_t gq) {
+                const uint32_t q1 = off_of(u + 1);
+                for (uint32_t q = off_of(u); q < q1; q += 4) {
+                    uint32_t ks[4];
+#pragma unroll
+                    for (uint32_t t = 0; t < 4; t++) ks[t] = q + t < q1 ? __ldcg(&inc_list[q + t]) : kNone;
+#pragma unroll
+                    for (uint32_t t = 0; t < 4; t++) {
+                        const uint32_t k = ks[t];
+                        if (k == kNone || k == skip || (est[k] & 4u)) continue;
+                        const uint32_t old = atomicSub(&est[k], 1u);
+                        atomicXor(&est[k], u << 3);
+                        const uint32_t c = (old & 3u) - 1u;
+                        if (c == 1u) {
+                            qpush(gq, k);
+                        } else if (c == 0u) {
+                            atomicOr(&est[k], 4u);
+                            dense[atomicAdd(&s_D, 1u)] = k;
+                            atomicSub(&s_rem, 1u);
+                        }
+                    }
+                }
+            };
             if (tid == 0) {
                 s_rem = C - s_dup;
                 s_A = s_S = s_D = s_r = s_apos = s_lo = 0;
@@ -395,8 +423,13 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                         v = __ldcg(&act[base + tid]);
                         if (vst[v] == 0) {
                             const uint32_t q1 = off_of(v + 1);
-                            for (uint32_t q = off_of(v); q < q1 && !elig; q++)
-                                elig = (est[__ldcg(&inc_list[q])] & 4u) == 0;
+                            for (uint32_t q = off_of(v); q < q1 && !elig; q += 4) {
+                                uint32_t ks[4];
+#pragma unroll
+                                for (uint32_t t = 0; t < 4; t++) ks[t] = q + t < q1 ? __ldcg(&inc_list[q + t]) : kNone;
+#pragma unroll
+                                for (uint32_t t = 0; t < 4; t++) elig |= ks[t] != kNone && (est[ks[t]] & 4u) == 0;
+                            }
                         }
                     }
                     const unsigned bal = __ballot_sync(0xFFFFFFFFu, elig);
@@ -430,21 +463,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                         const uint32_t u = s_batch[i];
                         vst[u] = 1u | ((abase + i) << 2);
                         actv[abase + i] = u;
-                        const uint32_t q1 = off_of(u + 1);
-                        for (uint32_t q = off_of(u); q < q1; q++) {
-                            const uint32_t k = __ldcg(&inc_list[q]);
-                            if (est[k] & 4u) continue;
-                            const uint32_t old = atomicSub(&est[k], 1u);
-                            atomicXor(&est[k], u << 3);
-                            const uint32_t c = (old & 3u) - 1u;
-                            if (c == 1u) {
-                                qpush(fi ^ 1, k);
-                            } else if (c == 0u) {
-                                atomicOr(&est[k], 4u);
-                                dense[atomicAdd(&s_D, 1u)] = k;
-                                atomicSub(&s_rem, 1u);
-                            }
-                        }
+                        remove_var(u, kNone, fi ^ 1);
                     }
                     __syncthreads();
                     if (tid == 0) s_A += nb;
@@ -466,24 +485,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                     }
                     __syncthreads();
                     // eliminate each variable solved this round from its other equations
-                    auto eliminate = [&](uint32_t sv) {
-                        const uint32_t j = sv >> 16, x = sv & 0xFFFFu;
-                        const uint32_t q1 = off_of(x + 1);
-                        for (uint32_t q = off_of(x); q < q1; q++) {
-                            const uint32_t k = __ldcg(&inc_list[q]);
-                            if (k == j || (est[k] & 4u)) continue;
-                            const uint32_t old = atomicSub(&est[k], 1u);
-                            atomicXor(&est[k], x << 3);
-                            const uint32_t c = (old & 3u) - 1u;
-                            if (c == 1u) {
-                                qpush(fi ^ 1, k);
-                            } else if (c == 0u) {
-                                atomicOr(&est[k], 4u);
-                                dense[atomicAdd(&s_D, 1u)] = k;
-                                atomicSub(&s_rem, 1u);
-                            }
-                        }
-                    };
+                    auto eliminate = [&](uint32_t sv) { remove_var(sv & 0xFFFFu, sv >> 16, fi ^ 1); };
                     if (nF <= T) {  // each solve is still in the register of the thread that made it
                         if (mine != kNone) eliminate(mine);
                     } else {
