@@ -271,9 +271,11 @@ def run_gpu(args):
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
+    timed_seeds = []
     for _ in range(args.steps):
         if l2_flush is not None:
             l2_flush.fill_(step_no[0] & 0xFF)
+        timed_seeds.append(1 + rank + 1000 * step_no[0])
         s, e0, e1, e2, o1, o2 = step(True)
         torch.cuda.synchronize()
         build_ms.append(e0.elapsed_time(e1))
@@ -292,7 +294,10 @@ def run_gpu(args):
     kh, vh, oh, xh, xoh = (None if a is None else to_dev(a, torch, pin=True) for a in (keys, vals, offs, other, ooffs))
     outh = torch.empty(n, dtype=torch.uint8 if (kind == "filter" or b <= 8) else torch.int16).pin_memory()
     e2e_b, e2e_q = [], []
-    for _ in range(max(1, min(args.steps, 3))):
+    # one build per timed step with that step's seed, so retries (a property
+    # of the seed) weigh the same as in the device-timed steps
+    for seed in timed_seeds:
+        p.seed = seed
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = vf.vf_build(kh, vh, offsets=oh, params=p)
@@ -388,7 +393,8 @@ def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse):
 # from the captured case by units processed; absent until a capture of the
 # current kernel exists (profiles/ holds the summaries).
 TRAFFIC = {("c2", "peel"): round(1067.88e6 / 2e7 * 1e8),   # k_flow_peel, one launch per attempt at 1e8
-           ("c2", "query"): round(189.42e6 / 2e7 * 1e8)}  # k_query, one launch per 1e8 queries
+           ("c2", "query"): round(189.42e6 / 2e7 * 1e8),  # k_query, one launch per 1e8 queries
+           ("c3", "lge"): round(1688.95e6)}               # k_lge small configuration, full-size capture
 
 
 # ---------------------------------------------------------------- reference arm
