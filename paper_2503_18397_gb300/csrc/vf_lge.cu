@@ -15,18 +15,22 @@
 //     dense system over the active variables;
 //  4. every solved variable is an affine function of the active ones; the
 //     bit-packed coefficient rows (32 active variables per word) are built
-//     round by round, the dense rows are reduced by Gauss-Jordan elimination
-//     in shared memory (free variables = 0), solved variables are evaluated
-//     forward, and peeled edges are assigned in reverse peel order.
+//     round by round (from one record per solve gathered after step 3), the
+//     dense rows are reduced by Gauss-Jordan elimination in shared memory, or
+//     in the CTA's slab when they do not fit (free variables = 0), solved
+//     variables are evaluated forward, and peeled edges are assigned in
+//     reverse peel order.
 //
 // Two configurations of the kernel share this code. Each round of steps 2-3
 // ends in a CTA barrier, so one CTA per SM leaves the SM idle at every
 // barrier; the small configuration (256 threads, 108 KB of shared memory, two
-// CTAs per SM) overlaps two shards instead. A shard whose peel arrays or dense
-// system do not fit its 108 KB is handed, unchanged, to the spill list, which
-// the large configuration (512 threads, 200 KB, one CTA per SM) then solves
-// from the start: both configurations solve the same system, so which one ran
-// changes neither the outcome nor the retry count.
+// CTAs per SM) overlaps two shards instead. A shard whose peel arrays do not
+// fit its 108 KB is handed, unchanged, to the spill list, which the large
+// configuration (512 threads, 200 KB, one CTA per SM) then solves from the
+// start: both configurations solve the same system, so which one ran changes
+// neither the outcome nor the retry count. A shard beyond the solver's pool
+// (active variables, coefficient rows) fails with kErrLgeSize, a capacity
+// error that ends the build rather than a retry.
 #include <algorithm>
 #include <atomic>
 
