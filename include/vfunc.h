@@ -84,7 +84,9 @@ typedef struct {
     uint64_t lge_threshold;  /* 800000 keys (Sec. 4.2) */
     uint64_t lge_target;     /* LGE regime: shard bits chosen so mean shard <= this (16384) */
     uint64_t lge_max_shard;  /* LGE regime: shard bits grow until no shard exceeds this
-                                (24576, the per-CTA solver's capacity) */
+                                (24576); larger shards are solved too (up to 65535
+                                cells per shard), with a per-shard pool that grows
+                                with the shard (see VF_ECAPACITY under vf_build) */
     int fuse_solver;         /* VF_SOLVER_FLOW (default) or VF_SOLVER_ROUNDS */
 } vf_params;
 
