@@ -552,6 +552,7 @@ vf_status run_lge_tasks(std::vector<vf::LgeTask>& tasks, bool lpt, const uint64_
     if (lpt)
         std::stable_sort(tasks.begin(), tasks.end(),
                          [](const vf::LgeTask& x, const vf::LgeTask& y) { return x.m > y.m; });
+    const uint32_t n_mid = vf::lge_partition(tasks);
     uint32_t m_cap = 1, v_cap = 32;
     for (auto& t : tasks) {
         m_cap = std::max(m_cap, t.m);
@@ -580,8 +581,9 @@ vf_status run_lge_tasks(std::vector<vf::LgeTask>& tasks, bool lpt, const uint64_
     a.err = misc.as<uint32_t>();
     a.stats = misc.as<uint32_t>() + 4;
     a.spill = misc.as<uint32_t>() + 16;
+    a.n_mid = n_mid;
     {
-        PhaseTimer t(kPhLge, st, 2);  // small configuration, then the spill list
+        PhaseTimer t(kPhLge, st, 3);  // medium and small configurations, then the spill list
         VF_CK(vf::launch_lge(a, grid, st));
     }
     uint32_t h[8];
@@ -744,6 +746,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     if (opts.lpt)
         std::stable_sort(tasks.begin(), tasks.end(),
                          [](const vf::LgeTask& x, const vf::LgeTask& y) { return x.m > y.m; });
+    const uint32_t n_mid = vf::lge_partition(tasks);
     uint32_t m_cap = 1, v_cap = 32;
     for (auto& t : tasks) {
         m_cap = std::max(m_cap, t.m);
@@ -772,6 +775,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     a.err = misc.as<uint32_t>();
     a.stats = misc.as<uint32_t>() + 4;
     a.spill = misc.as<uint32_t>() + 16;
+    a.n_mid = n_mid;
     // scatter + solver: one CUDA graph (or plain launches)
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(fails.p, 0, std::max<uint64_t>(P, 1) * 8, q);
@@ -799,7 +803,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
         }
         e = cudaGraphInstantiate(&exec, graph, 0);
         if (e == cudaSuccess) {
-            PhaseTimer t(kPhLge, st, 3);  // scatter + both solver configurations
+            PhaseTimer t(kPhLge, st, 4);  // scatter + three solver configurations
             e = cudaGraphLaunch(exec, st);
         }
         if (exec) cudaGraphExecDestroy(exec);
@@ -809,7 +813,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
             return fail(VF_ECUDA, std::string("graph launch failed: ") + cudaGetErrorString(e));
         }
     } else {
-        PhaseTimer t(kPhLge, st, 3);  // scatter + both solver configurations
+        PhaseTimer t(kPhLge, st, 4);  // scatter + three solver configurations
         cudaError_t e = enqueue(st);
         if (e != cudaSuccess) {
             free_data();

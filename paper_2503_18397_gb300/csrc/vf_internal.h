@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <vector>
 
 #include "vf_device.cuh"
 #include "vfunc.h"
@@ -165,15 +166,24 @@ struct LgeArgs {
     uint64_t scratch_words_per_cta;
     uint32_t m_cap, v_cap;            // largest shard / cell count the scratch layout holds
     uint32_t* err;                    // OR of all failure bits
-    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] task counter, [3] dropped duplicates,
-                                      // [4] spill-list counter, [5] spilled tasks
+    uint32_t* stats;                  // [0] peeled edges, [1] core edges, [2] task counter (medium
+                                      // configuration), [3] dropped duplicates, [4] spill-list counter,
+                                      // [5] spilled tasks, [6] task counter (small configuration)
     uint32_t* item_dup;               // per-structure dropped duplicate filter keys, or NULL
     // Two-configuration launch: the spill list (room for ntasks indices) that the
     // small configuration fills; NULL runs the large configuration alone.
     uint32_t* spill;
-    const uint32_t* spill_in;         // set by launch_lge for the second launch
+    const uint32_t* spill_in;         // set by launch_lge for the last launch
     const uint32_t* spilled;          // count of spill_in (device), set by launch_lge
+    uint32_t n_mid;                   // tasks[0, n_mid) have more than kLgeSmallTaskKeys keys
+                                      // (lge_partition); the rest go to the small configuration
+    uint32_t task_lo, ctr;            // set by launch_lge: first task and counter word of a launch
 };
+// Tasks of at most this many keys run in the small configuration (three CTAs
+// per SM); larger ones in the medium one (two per SM).
+constexpr uint32_t kLgeSmallTaskKeys = 7168;
+// Stable partition: tasks above kLgeSmallTaskKeys first; returns their count.
+uint32_t lge_partition(std::vector<LgeTask>& tasks);
 // Layout (in 32-bit words) of one CTA's LGE scratch slab for shards of at most
 // m keys and V cells.
 constexpr uint32_t kMaxActive = 4096;  // active variables per shard (up to kLgeBigShard keys)

@@ -21,14 +21,15 @@
 //     variables are evaluated forward, and peeled edges are assigned in
 //     reverse peel order.
 //
-// Two configurations of the kernel share this code. Each round of steps 2-3
+// Three configurations of the kernel share this code. Each round of steps 2-3
 // ends in a CTA barrier, so one CTA per SM leaves the SM idle at every
-// barrier; the small configuration (256 threads, 108 KB of shared memory, two
-// CTAs per SM) overlaps two shards instead. A shard whose peel arrays do not
-// fit its 108 KB is handed, unchanged, to the spill list, which the large
-// configuration (512 threads, 200 KB, one CTA per SM) then solves from the
-// start: both configurations solve the same system, so which one ran changes
-// neither the outcome nor the retry count. A shard beyond the solver's pool
+// barrier; several CTAs per SM overlap several shards instead. Shards of at
+// most kLgeSmallTaskKeys keys run in the small configuration (192 threads,
+// 72 KB of shared memory, three CTAs per SM), larger ones in the medium one
+// (256 threads, 108 KB, two per SM). A shard whose peel arrays do not fit is
+// handed, unchanged, to the spill list, which the large configuration (512
+// threads, 200 KB, one CTA per SM) then solves from the start: all solve the
+// same system, so which one ran changes neither the outcome nor the retry count. A shard beyond the solver's pool
 // (active variables, coefficient rows) fails with kErrLgeSize, a capacity
 // error that ends the build rather than a retry.
 #include <algorithm>
@@ -42,9 +43,12 @@ constexpr uint32_t kMaxBatch = 256;
 // large configuration: 512 threads, 200 KB dynamic shared memory, 1 CTA per SM
 constexpr int kBigT = 512;
 constexpr uint32_t kBigWords = 50 * 1024;
-// small configuration: 256 threads, 108 KB, 2 CTAs per SM
-constexpr int kSmallT = 256;
-constexpr uint32_t kSmallWords = 27 * 1024;
+// medium configuration: 256 threads, 108 KB, 2 CTAs per SM
+constexpr int kMidT = 256;
+constexpr uint32_t kMidWords = 27 * 1024;
+// small configuration: 192 threads, 72 KB, 3 CTAs per SM
+constexpr int kSmallT = 192;
+constexpr uint32_t kSmallWords = 18 * 1024;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 uint64_t lge_scratch_words_per_cta(uint32_t m_cap, uint32_t v_cap) { return lge_offsets(m_cap, v_cap).total; }
@@ -137,8 +141,8 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
     for (;;) {
         __shared__ uint32_t s_skip;
         if (tid == 0) {
-            const uint32_t q = atomicAdd(&a.stats[from_spill ? 4 : 2], 1u);
-            s_shard = q < ntasks ? (from_spill ? a.spill_in[q] : q) : kNone;
+            const uint32_t q = atomicAdd(&a.stats[from_spill ? 4 : a.ctr], 1u);
+            s_shard = q < ntasks ? (from_spill ? a.spill_in[q] : a.task_lo + q) : kNone;
             s_skip = s_shard != kNone &&
                      (*reinterpret_cast<volatile uint32_t*>(a.item_fail + a.tasks[s_shard].item) & kBad) != 0;
             s_fail = 0;
@@ -699,47 +703,81 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
     }
 }
 
-#define VF_LGE_SMALL k_lge<kSmallT, kSmallWords, 2>
+#define VF_LGE_SMALL k_lge<kSmallT, kSmallWords, 3>
+#define VF_LGE_MID k_lge<kMidT, kMidWords, 2>
 #define VF_LGE_BIG k_lge<kBigT, kBigWords, 1>
 
+enum LgeCfg { kCfgSmall = 0, kCfgMid = 1, kCfgBig = 2 };
+
 // Resident CTAs of one configuration on the whole GPU (attributes set once per device).
-static unsigned resident(bool small) {
+static unsigned resident(LgeCfg c) {
     static std::atomic<uint64_t> done{0};
-    static unsigned per_sm_small = 1, per_sm_big = 1;
+    static unsigned per_sm[3] = {1, 1, 1};
     int dev = 0;
     cudaGetDevice(&dev);
     const uint64_t bit = uint64_t(1) << (dev & 63);
     if (!(done.load() & bit)) {
-        int ps = 0, pb = 0;
+        int p[3] = {0, 0, 0};
         cudaFuncSetAttribute(VF_LGE_SMALL, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmallWords * 4));
+        cudaFuncSetAttribute(VF_LGE_MID, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMidWords * 4));
         cudaFuncSetAttribute(VF_LGE_BIG, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBigWords * 4));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, VF_LGE_SMALL, kSmallT, kSmallWords * 4);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, VF_LGE_BIG, kBigT, kBigWords * 4);
-        per_sm_small = unsigned(ps < 1 ? 1 : ps);
-        per_sm_big = unsigned(pb < 1 ? 1 : pb);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p[0], VF_LGE_SMALL, kSmallT, kSmallWords * 4);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p[1], VF_LGE_MID, kMidT, kMidWords * 4);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p[2], VF_LGE_BIG, kBigT, kBigWords * 4);
+        for (int i = 0; i < 3; i++) per_sm[i] = unsigned(p[i] < 1 ? 1 : p[i]);
         done.fetch_or(bit);
     }
-    return (small ? per_sm_small : per_sm_big) * unsigned(num_sms());
+    return per_sm[c] * unsigned(num_sms());
 }
 
-unsigned lge_grid() { return std::max(resident(true), resident(false)); }
+unsigned lge_grid() { return std::max(resident(kCfgSmall), std::max(resident(kCfgMid), resident(kCfgBig))); }
+
+uint32_t lge_partition(std::vector<LgeTask>& tasks) {
+    auto mid = std::stable_partition(tasks.begin(), tasks.end(),
+                                     [](const LgeTask& t) { return t.m > kLgeSmallTaskKeys; });
+    return uint32_t(mid - tasks.begin());
+}
 
 cudaError_t launch_lge(const LgeArgs& a, unsigned grid, cudaStream_t st) {
     if (a.ntasks == 0) return cudaSuccess;
     if (!a.spill) {  // large configuration alone
-        VF_LGE_BIG<<<std::min(grid, resident(false)), kBigT, kBigWords * 4, st>>>(a);
+        LgeArgs only = a;
+        only.task_lo = 0;
+        only.ctr = 2;
+        VF_LGE_BIG<<<std::min(grid, resident(kCfgBig)), kBigT, kBigWords * 4, st>>>(only);
         return cudaGetLastError();
     }
-    LgeArgs first = a;
-    first.spilled = nullptr;
-    VF_LGE_SMALL<<<std::min(grid, resident(true)), kSmallT, kSmallWords * 4, st>>>(first);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    LgeArgs second = a;
-    second.spill = nullptr;
-    second.spilled = a.stats + 5;
-    second.spill_in = a.spill;
-    VF_LGE_BIG<<<std::min(grid, resident(false)), kBigT, kBigWords * 4, st>>>(second);
+    // tasks[0, n_mid): medium configuration, counter word 2; the rest: small
+    // configuration, counter word 6; then the spill list (counter word 4)
+    const uint32_t n_mid = std::min(a.n_mid, a.ntasks);
+    if (n_mid > 0) {
+        LgeArgs mid = a;
+        mid.spilled = nullptr;
+        mid.ntasks = n_mid;
+        mid.task_lo = 0;
+        mid.ctr = 2;
+        VF_LGE_MID<<<std::min(std::min(grid, resident(kCfgMid)), n_mid), kMidT, kMidWords * 4, st>>>(mid);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (a.ntasks > n_mid) {
+        LgeArgs small = a;
+        small.spilled = nullptr;
+        small.ntasks = a.ntasks - n_mid;
+        small.task_lo = n_mid;
+        small.ctr = 6;
+        VF_LGE_SMALL<<<std::min(std::min(grid, resident(kCfgSmall)), small.ntasks), kSmallT, kSmallWords * 4, st>>>(
+            small);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    LgeArgs last = a;
+    last.spill = nullptr;
+    last.spilled = a.stats + 5;
+    last.spill_in = a.spill;
+    last.task_lo = 0;
+    last.ctr = 4;
+    VF_LGE_BIG<<<std::min(grid, resident(kCfgBig)), kBigT, kBigWords * 4, st>>>(last);
     return cudaGetLastError();
 }
 
