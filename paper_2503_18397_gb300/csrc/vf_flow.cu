@@ -434,13 +434,12 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_order(uint64_t* __restric
     uint64_t* s_loc = reinterpret_cast<uint64_t*>(smem_tile);
     uint32_t* s_val = reinterpret_cast<uint32_t*>(s_loc + kTile);
     uint32_t* s_cnt = s_val + kTile;  // 2 * nb
-    __shared__ uint32_t s_first, s_split, s_skip, s_warp[kTileThreads / 32];
+    __shared__ uint32_t s_split, s_skip, s_warp[kTileThreads / 32];
     const uint32_t nbins = 2 * nb;
     for (uint64_t t0 = uint64_t(blockIdx.x) * kTile; t0 < n; t0 += uint64_t(gridDim.x) * kTile) {
         const uint32_t m = n - t0 < uint64_t(kTile) ? uint32_t(n - t0) : uint32_t(kTile);
         if (threadIdx.x == 0) {
             const uint32_t f = flow_shard_of_edge(start, S, t0), l = flow_shard_of_edge(start, S, t0 + m - 1);
-            s_first = f;
             s_skip = l - f > 1;
             const unsigned long long sp = __ldg(start + f + 1) - t0;  // first key of shard f+1
             s_split = sp < m ? uint32_t(sp) : m;

@@ -193,7 +193,7 @@ constexpr uint32_t kLPoolPerKey = 40;  // words of coefficient rows per shard ke
 // rows take ~0.0011 m words per key.
 constexpr uint32_t kLgeBigShard = 24576;
 struct LgeOffsets {
-    uint64_t cev, porder, proff, f0, f1, cand, core, eqst, eqdone, inc_off, inc_cur, inc_list, vstate, act, actv,
+    uint64_t cev, porder, proff, f0, f1, cand, core, eqst, inc_off, inc_cur, inc_list, vstate, act, actv,
         solves, soff, srec, dense, lc, L, lpool, total;
     uint32_t a_cap;  // active variables a shard may have
 };
@@ -215,7 +215,6 @@ __host__ __device__ constexpr LgeOffsets lge_offsets(uint32_t m, uint32_t V) {
     o.cand = lge_take(p, V);
     o.core = lge_take(p, m);
     o.eqst = lge_take(p, m);
-    o.eqdone = lge_take(p, m);
     o.inc_off = lge_take(p, V + 1ull);
     o.inc_cur = lge_take(p, V);
     o.inc_list = lge_take(p, 3ull * m);

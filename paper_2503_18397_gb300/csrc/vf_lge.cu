@@ -119,7 +119,6 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
     uint32_t* cand = scr + o.cand;
     uint32_t* core = scr + o.core;
     uint32_t* eqst = scr + o.eqst;
-    uint32_t* eqdone = scr + o.eqdone;
     uint32_t* inc_off = scr + o.inc_off;
     uint32_t* inc_cur = scr + o.inc_cur;
     uint32_t* inc_list = scr + o.inc_list;
