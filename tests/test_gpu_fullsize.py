@@ -1,8 +1,12 @@
-"""Full-size builds checked on sampled outputs: the 10^8-key VFilter (b = 8)
-of the benchmark and a build above 2^30 keys (built one shard group at a time).
-Every sampled member is accepted, the false-positive rate is 2^-b within 5
-sigma, and the oracle's query on the GPU-built data array equals the GPU query
-for sampled members and non-members."""
+"""Full-size builds of the benchmark's workloads, in its parameters and seeds.
+
+The 2^20-key VFunc is compared with a complete oracle build. The larger ones
+are checked on sampled outputs: every (sampled) member is accepted or decodes
+to its value, the false-positive rate is 2^-b within 5 sigma, the oracle's
+query on the GPU-built data array equals the GPU query for sampled members and
+non-members, the plan equals the oracle's, and (LGE regime) sampled shards'
+systems are solvable for the oracle at the seed the GPU settled on. A build
+above 2^30 keys (one shard group at a time) is checked the same way."""
 import math
 
 import numpy as np
@@ -76,3 +80,152 @@ def test_build_above_2pow30_by_shard_group(vf, orc):
     assert info.n == n and info.peeled == n and info.shards >= 8
     _check_sampled(vf, orc, s, keys, n, 2, 8)
     s.free()
+
+
+def _dev(a):
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).cuda()
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.view(np.int16)).cuda()
+    return torch.from_numpy(a).cuda()
+
+
+def _oracle_info(orc, info):
+    oi = orc.Info()
+    for f, _ in orc.Info._fields_:
+        setattr(oi, f, getattr(info, f))
+    return oi
+
+
+def test_vfunc_2pow20_equals_oracle_build(vf, orc):
+    # the 2^20-key VFunc (b = 8) of the benchmark, its inputs and first seed
+    n, seed = 1 << 20, 0x5EED
+    keys = synth.u64_keys(0, n, seed)
+    vals = synth.values(n, 8, seed)
+    s = vf.vf_build(_dev(keys), _dev(vals), params=vf.vf_params_default(kind=vf.FUNC, b=8, seed=1))
+    info = s.info
+    st, oi, _ = orc.build(orc.default_params(kind=orc.FUNC, b=8, seed=1), keys, vals)
+    assert st == orc.OK
+    for f in ("regime", "h", "shards", "M", "c", "lg_seg", "seg", "l", "T", "cells", "total_cells", "data_bytes",
+              "seed", "retries", "n_eff", "peeled"):
+        assert getattr(info, f) == getattr(oi, f), f
+    assert (s.query(_dev(keys)).cpu().numpy() == vals).all()
+    other = synth.u64_keys(n, n, seed)
+    gq = s.query(_dev(other)).cpu().numpy()
+    assert (gq == orc.query(_oracle_info(orc, info), vf.vf_export(s), other)).all()
+    s.free()
+
+
+def test_vfunc_strings_1e7_lge_sampled(vf, orc):
+    # 10^7 byte strings, b = 16, LGE regime (the benchmark's string workload)
+    n, seed = 10_000_000, 0x5EED
+    data, offs = synth.byte_strings(0, n, seed)
+    vals = synth.values(n, 16, seed)
+    p = vf.vf_params_default(kind=vf.FUNC, b=16, key_kind=vf.KEYS_BYTES, mode=vf.MODE_LGE, seed=1)
+    dd, do, dv = _dev(data), _dev(offs), _dev(vals)
+    s = vf.vf_build(dd, dv, offsets=do, params=p)
+    info = s.info
+    op = orc.default_params(kind=orc.FUNC, b=16, key_kind=orc.KEYS_BYTES, mode=orc.MODE_LGE, seed=1)
+    h, regime, _, _ = orc.plan_h(op, n)
+    assert (info.h, info.regime) == (h, regime) == (10, orc.REGIME_LGE)
+    # every member decodes to its value
+    assert bool((s.query(dd, offsets=do).view(torch.int16) == dv).all().item())
+    # the oracle's query on the GPU-built array, sampled members and non-members
+    rng = np.random.default_rng(7)
+    pick = np.sort(rng.choice(n, size=50_000, replace=False))
+    sub_lens = (offs[pick + 1] - offs[pick]).astype(np.uint64)
+    sub_offs = np.concatenate([[0], np.cumsum(sub_lens)]).astype(np.uint64)
+    sub = np.concatenate([data[int(offs[i]):int(offs[i + 1])] for i in pick])
+    oi = _oracle_info(orc, info)
+    arr = vf.vf_export(s)
+    gq = _np(s.query(_dev(sub), offsets=_dev(sub_offs)))
+    assert (gq == vals[pick]).all() and (orc.query(oi, arr, sub, offsets=sub_offs) == gq).all()
+    ob, oo = synth.byte_strings(n, 50_000, seed)
+    gq = _np(s.query(_dev(ob), offsets=_dev(oo)))
+    assert (orc.query(oi, arr, ob, offsets=oo) == gq).all()
+    # the geometry follows from the largest shard at the final seed, and sampled
+    # shards' systems are solvable for the oracle (peel, then GF(2) elimination)
+    sig = orc.sigs(data, info.seed, offsets=offs)
+    shard, local = orc.shard_local(sig, info.h)
+    counts = np.bincount(shard.astype(np.int64), minlength=info.shards)
+    assert info.M == counts.max()
+    g = orc.geometry(orc.REGIME_LGE, info.h, int(info.M), 16, orc.FUNC)
+    assert (g.cells, g.total_cells, g.data_bytes) == (info.cells, info.total_cells, info.data_bytes)
+    for sh in rng.choice(info.shards, size=3, replace=False):
+        sel = shard == np.uint64(sh)
+        e = orc.edges_of(g, local[sel]).astype(np.uint32)
+        ne, order, _ = orc.peel(int(g.cells), e)
+        core = np.ones(len(e), bool)
+        core[order] = False
+        ok, _ = orc.gf2_solve(int(g.cells), e[core], vals[sel][core].astype(np.uint64))
+        assert ok, f"shard {sh}"
+    s.free()
+
+
+def test_batch_4096_structures_sampled(vf, orc):
+    # the benchmark's batch: 4096 structures of 10^3..10^6 keys, b in {1,8,16,32},
+    # kind 50/50, built with the autotuned options
+    count = 4096
+    rng = np.random.default_rng(0xC4)
+    sizes = synth.log_uniform_sizes(count, 1e3, 1e6, 0xC4)
+    kinds = rng.integers(0, 2, size=count)
+    bs = rng.choice([1, 8, 16, 32], size=count)
+    items, starts, start = [], [], 0
+    for i in range(count):
+        m = int(sizes[i])
+        keys = synth.u64_keys_torch(start, m, 0xC4)
+        starts.append(start)
+        start += m
+        vals = synth.values_torch(m, int(bs[i]), 0xC4 + i) if kinds[i] == 0 else None
+        items.append((keys, vals, int(kinds[i]), int(bs[i]), 1000 + i))
+    best, _ = vf.vf_tune_batch(items)
+    structs = vf.vf_build_batch(items, opts=best)
+    # every structure: all members accepted / decoded
+    for (kd, vd, kind, b, _), st in zip(items, structs):
+        out = st.query(kd)
+        if kind == 0:
+            assert bool((_bits(out) == _bits(vd)).all().item())
+        else:
+            assert bool(out.bool().all().item())
+    # sampled structures: the plan equals the oracle's; small ones equal a full oracle build;
+    # larger ones: the oracle's query on the GPU-built array for members and non-members
+    small = [i for i in range(count) if sizes[i] <= 20_000]
+    large = [i for i in range(count) if sizes[i] >= 200_000]
+    for i in list(rng.choice(small, size=6, replace=False)) + list(rng.choice(large, size=4, replace=False)):
+        kd, vd, kind, b, seed = items[i]
+        info = structs[i].info
+        keys = kd.cpu().numpy().view(np.uint64)
+        vals = None if vd is None else _host_vals(vd, b)
+        op = orc.default_params(kind=kind, b=b, seed=seed, lge_target=best.lge_target,
+                                lge_threshold=best.lge_threshold)
+        h, regime, _, _ = orc.plan_h(op, len(keys))
+        assert (info.h, info.regime) == (h, regime)
+        if sizes[i] <= 20_000:
+            st, oi, _ = orc.build(op, keys, vals)
+            assert st == orc.OK
+            for f in ("regime", "h", "shards", "M", "cells", "total_cells", "data_bytes", "seed", "retries", "n_eff"):
+                assert getattr(info, f) == getattr(oi, f), (i, f)
+        oi = _oracle_info(orc, info)
+        arr = vf.vf_export(structs[i])
+        other = synth.u64_keys(10**10 + starts[i], 20_000, 0xC4)
+        for q in (keys[:20_000], other):
+            gq = _np(structs[i].query(_dev(np.ascontiguousarray(q))))
+            assert (orc.query(oi, arr, q) == gq).all(), i
+    for st in structs:
+        st.free()
+
+
+def _bits(t):
+    """Same-width signed view (unsigned 16/32-bit tensors have few kernels)."""
+    return {torch.uint16: lambda x: x.view(torch.int16), torch.uint32: lambda x: x.view(torch.int32)}.get(
+        t.dtype, lambda x: x)(t)
+
+
+def _np(t):
+    """Host copy of a result tensor as unsigned numpy."""
+    a = _bits(t).cpu().numpy()
+    return a.view({1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[a.dtype.itemsize])
+
+
+def _host_vals(vd, b):
+    return _np(vd)
