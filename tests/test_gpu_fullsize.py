@@ -72,6 +72,21 @@ def test_vfilter_1e8_sampled(vf, orc):
     s.free()
 
 
+def test_mwhc_vfilter_1e8_sampled(vf, orc):
+    # the MWHC variant of the benchmark: 10^8 keys, b = 8, eps = 0.01, eta = 10^-3
+    n = 100_000_000
+    keys = _keys(n, 0xC2)
+    p = vf.vf_params_default(kind=vf.FILTER, b=8, seed=1, mode=vf.MODE_MWHC, eps=0.01, eta=1e-3)
+    s = vf.vf_build(keys, None, params=p)
+    info = s.info
+    h, regime, _, _ = orc.plan_h(orc.default_params(kind=orc.FILTER, b=8, seed=1, mode=orc.MODE_MWHC, eps=0.01,
+                                                    eta=1e-3), n)
+    assert (info.h, info.regime) == (h, regime) == (6, orc.REGIME_MWHC)
+    assert info.c == 1.23 and info.cells % 3 == 0
+    _check_sampled(vf, orc, s, keys, n, 3, 8)
+    s.free()
+
+
 def test_build_above_2pow30_by_shard_group(vf, orc):
     n = (1 << 30) + 12_345
     keys = _keys(n, 0xB16)
