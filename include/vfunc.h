@@ -268,7 +268,7 @@ vf_status vf_timing_read(double *ms, uint64_t *launches);
  *          data_capacity >= vf_info.data_bytes bytes (get it from vf_plan with
  *          M = n), written with the structure's cells; info: host, receives
  *          the geometry, seed and retries, as vf_get_info would.
- *  All scratch lives in one static device array of about 4.2 MB that every
+ *  All scratch lives in one static device array of about 4.6 MB that every
  *  GPU loading the library keeps until the process exits; no call allocates
  *  or frees memory. The first call on a device looks up that array's device
  *  address; make it before any stream capture. All calls share the array,
@@ -278,6 +278,20 @@ vf_status vf_timing_read(double *ms, uint64_t *launches);
  *  small, byte-string keys, bad b/kind), VF_EBUILD, VF_ECUDA. */
 vf_status vf_build_static(const uint64_t *keys, const void *values, uint64_t n, const vf_params *params,
                           void *data, uint64_t data_capacity, vf_info *info, void *stream);
+
+/* Fault injection for tests of the failure paths (the paper has no
+ * counterpart; its failure model is a failed attempt retried with the next
+ * seed, Sec. 4). Process-wide, off by default (0, 0, 0); not for production.
+ *   fail_attempts: the first fail_attempts attempts of every vf_build report
+ *     failure after solving, so the build retries with seed+1, seed+2, ... as
+ *     it does after a 2-core or an unsolvable system (VF_EBUILD once
+ *     max_retries is exceeded).
+ *   assign_poll_limit: polls after which a wait of the fuse-regime dataflow
+ *     assignment gives up (0: the default, ~8 s).
+ *   stall_assign: no vertex starts final in that assignment, so every wait
+ *     runs out; the build returns VF_ETIMEOUT and the CUDA context stays usable.
+ * Errors: VF_EINVAL (fail_attempts < 0). */
+vf_status vf_debug_faults(int fail_attempts, uint32_t assign_poll_limit, int stall_assign);
 
 /* Release a structure (NULL is accepted). */
 vf_status vf_free(vf_struct *s);

@@ -124,8 +124,9 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.vf_last_error.argtypes = []
         L.vf_last_error.restype = C.c_char_p
+        L.vf_debug_faults.argtypes = [i32, C.c_uint32, i32]
         for name in ("vf_build", "vf_query", "vf_get_info", "vf_plan", "vf_data", "vf_export", "vf_signatures",
-                     "vf_free", "vf_timing_enable", "vf_timing_read"):
+                     "vf_free", "vf_timing_enable", "vf_timing_read", "vf_debug_faults"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -411,6 +412,11 @@ PHASES = ["hash_hist", "scatter", "incidence", "peel", "assign", "lge", "query"]
 
 def vf_timing_enable(on: bool = True):
     _check(lib().vf_timing_enable(1 if on else 0))
+
+
+def vf_debug_faults(fail_attempts: int = 0, assign_poll_limit: int = 0, stall_assign: bool = False):
+    """Fault injection for tests (process-wide; all zero = off)."""
+    _check(lib().vf_debug_faults(int(fail_attempts), int(assign_poll_limit), 1 if stall_assign else 0))
 
 
 def vf_timing_read() -> dict:

@@ -14,9 +14,16 @@
 
 #include "vf_internal.h"
 
+#include <atomic>
+
 namespace {
 
 thread_local std::string g_last_error;
+
+// Test hooks (vf_debug_faults), off unless a test sets them.
+std::atomic<int> g_debug_fail_attempts{0};
+std::atomic<uint32_t> g_debug_assign_limit{0};
+std::atomic<int> g_debug_stall_assign{0};
 
 vf_status fail(vf_status st, const std::string& msg) {
     g_last_error = msg;
@@ -430,6 +437,8 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.err = a.ctr + vf::kFlowErr;
     a.data = data;
     a.cell_base = cell_base;
+    a.assign_limit = g_debug_assign_limit.load();
+    a.stall = g_debug_stall_assign.load() ? 1u : 0u;
     {
         PhaseTimer t(kPhAccum, st);
         VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, drop, st));
@@ -1196,6 +1205,7 @@ vf_status build_impl(const void* keys, const uint64_t* offsets, const void* valu
         in.n_eff = n_all - dropped;
         in.core = in.regime == VF_REGIME_LGE ? core : 0;
         in.rounds = rounds;
+        if (rs == VF_OK && attempt < g_debug_fail_attempts.load()) rs = VF_EBUILD;  // test hook
         if (rs == VF_OK) {
             VF_CK(cudaStreamSynchronize(st));
             if (ck.f) {
@@ -1468,6 +1478,14 @@ vf_status vf_signatures(int key_kind, const void* keys, const uint64_t* offsets,
 
 vf_status vf_timing_enable(int on) {
     g_timing = on != 0;
+    return VF_OK;
+}
+
+vf_status vf_debug_faults(int fail_attempts, uint32_t assign_poll_limit, int stall_assign) {
+    if (fail_attempts < 0) return fail(VF_EINVAL, "vf_debug_faults: fail_attempts < 0");
+    g_debug_fail_attempts = fail_attempts;
+    g_debug_assign_limit = assign_poll_limit;
+    g_debug_stall_assign = stall_assign != 0;
     return VF_OK;
 }
 

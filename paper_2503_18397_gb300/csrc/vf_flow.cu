@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
 __global__ void __launch_bounds__(kFT) k_final_init(FlowArgs a) {
     const uint64_t V = uint64_t(a.S) * a.g.cells;
     for (uint64_t v = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; v < V; v += uint64_t(gridDim.x) * blockDim.x)
-        a.fv[v] = ((__ldg(a.pv + (v >> 5)) >> (v & 31u)) & 1u) ? 0ull : kFinal;
+        a.fv[v] = (a.stall || ((__ldg(a.pv + (v >> 5)) >> (v & 31u)) & 1u)) ? 0ull : kFinal;
 }
 
 // Dataflow assignment over the record slots, largest slot first.
@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
     const uint64_t count = a.nrec;
     const unsigned lane = lane32();
     const uint32_t vmask = b == 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
+    const uint32_t limit = a.assign_limit ? a.assign_limit : kIdleLimit;
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(ctr64(a, kFlowNext), 32ull);
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
                 }
             }
             if (__all_sync(0xFFFFFFFFu, done)) break;
-            if (++polls > kIdleLimit) fail = true;
+            if (++polls > limit) fail = true;
             if ((polls & 63u) == 0 && (dev_atomic32(*a.err).load(cuda::memory_order_relaxed) & kErrTimeout)) fail = true;
             if (__any_sync(0xFFFFFFFFu, fail)) {
                 fail = true;

@@ -121,6 +121,8 @@ struct FlowArgs {
     uint32_t* err;                    // == ctr + kFlowErr
     uint8_t* data;                    // assignment target
     uint64_t cell_base;               // cell of the first vertex (shard groups)
+    uint32_t assign_limit;            // polls after which an assignment wait gives up (0: default)
+    uint32_t stall;                   // test hook: no vertex starts final, so every wait runs out
 };
 cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
                                const Geom& g, uint32_t* W, uint32_t* err, const uint32_t* drop, cudaStream_t st);

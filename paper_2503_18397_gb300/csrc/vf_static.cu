@@ -23,7 +23,7 @@ constexpr uint64_t kValWords = kStaticMaxKeys;
 constexpr uint64_t kSlabWords = lge_offsets(kStaticMaxKeys, kStaticMaxCells).total;
 constexpr uint64_t kStaticWords = kMiscWords + kStartWords + kTaskWords + kLocWords + kValWords + kSlabWords;
 
-// The scratch itself: about 4.2 MB, resident on every GPU that loads the
+// The scratch itself: about 4.6 MB, resident on every GPU that loads the
 // library for the life of the process. Shared by every call.
 static __device__ __align__(256) uint32_t g_static_scratch[kStaticWords];
 
