@@ -21,7 +21,7 @@ FUNC, FILTER = 0, 1
 KEYS_U64, KEYS_BYTES = 0, 1
 MODE_AUTO, MODE_FUSE, MODE_LGE, MODE_MWHC = 0, 1, 2, 3
 REGIME_FUSE, REGIME_LGE, REGIME_MWHC = 1, 2, 3
-OK, EINVAL, ENOMEM, EBUILD = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, EBUILD, EDUP = 0, 1, 2, 3, 4
 
 
 class Params(C.Structure):
@@ -29,6 +29,7 @@ class Params(C.Structure):
         ("kind", C.c_int), ("b", C.c_int), ("key_kind", C.c_int), ("mode", C.c_int),
         ("max_retries", C.c_int), ("seed", C.c_uint64), ("eps", C.c_double), ("eta", C.c_double),
         ("lge_threshold", C.c_uint64), ("lge_target", C.c_uint64), ("lge_max_shard", C.c_uint64),
+        ("threads", C.c_int),
     ]
 
 
@@ -50,7 +51,7 @@ def build_oracle(force: bool = False) -> str:
     """Compile the oracle (plain C, -O2) if missing or stale."""
     if force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC):
         tmp = LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB_PATH)
     return LIB_PATH
 
@@ -83,6 +84,7 @@ def lib():
         L.orc_build.argtypes = [C.POINTER(Params), vp, vp, vp, u64, C.POINTER(Info), C.POINTER(C.c_void_p)]
         L.orc_free.argtypes = [vp]
         L.orc_query.argtypes = [C.POINTER(Info), vp, i32, vp, vp, u64, vp]
+        L.orc_query_mt.argtypes = [C.POINTER(Info), vp, i32, vp, vp, u64, vp, i32]
         L.orc_cell_get.restype = C.c_uint64
         L.orc_cell_get.argtypes = [vp, i32, u64]
         L.orc_peel.restype = u64
@@ -179,7 +181,7 @@ def out_dtype(kind: int, b: int):
     return np.uint8 if b <= 8 else np.uint16 if b <= 16 else np.uint32 if b <= 32 else np.uint64
 
 
-def query(info: Info, data: np.ndarray, keys, offsets=None) -> np.ndarray:
+def query(info: Info, data: np.ndarray, keys, offsets=None, threads: int = 1) -> np.ndarray:
     keys = np.ascontiguousarray(keys)
     m = len(keys) if offsets is None else len(offsets) - 1
     offs = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.uint64)
@@ -187,8 +189,11 @@ def query(info: Info, data: np.ndarray, keys, offsets=None) -> np.ndarray:
     data = np.ascontiguousarray(data, dtype=np.uint8)
     if data.size == 0:
         data = np.zeros(8, dtype=np.uint8)
-    lib().orc_query(C.byref(info), _ptr(data), KEYS_U64 if offsets is None else KEYS_BYTES,
-                    _ptr(keys), _ptr(offs), m, _ptr(out))
+    kk = KEYS_U64 if offsets is None else KEYS_BYTES
+    if threads > 1:
+        lib().orc_query_mt(C.byref(info), _ptr(data), kk, _ptr(keys), _ptr(offs), m, _ptr(out), threads)
+    else:
+        lib().orc_query(C.byref(info), _ptr(data), kk, _ptr(keys), _ptr(offs), m, _ptr(out))
     return out
 
 

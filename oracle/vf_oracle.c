@@ -32,6 +32,7 @@
 #include "vf_oracle.h"
 
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -56,6 +57,7 @@ void orc_params_default(orc_params *p) {
     p->lge_threshold = 800000; /* Sec. 4.2: below 800,000 keys, LGE with c = 1.12 */
     p->lge_target = 16384;
     p->lge_max_shard = 24576;
+    p->threads = 1;
 }
 
 /* ------------------------------------------------------------------ hashing */
@@ -193,6 +195,9 @@ void orc_geometry(orc_info *in) {
         uint64_t part = (uint64_t)ceil(in->c * Mf / 3.0);
         in->cells = 3 * (part < 16 ? 16 : part);
     } else if (in->regime == ORC_REGIME_LGE) {
+        /* Sec. 4.2: small sizes are solved by LGE with c = 1.12, on three
+         * distinct uniform vertices per key (not a fuse graph: at these sizes
+         * a c = 1.12 fuse graph is overdetermined inside, see orc_edge). */
         in->c = 1.12;
         in->lg_seg = 0;
         in->seg = 0;
@@ -259,7 +264,12 @@ void orc_edge(const orc_info *in, uint64_t local, uint64_t v[3]) {
         v[1] = P + orc_mulhi(orc_mix64(local ^ ORC_C_EDGE), P);
         v[2] = 2 * P + orc_mulhi(orc_mix64(local ^ ORC_C_EDGE2), P);
     } else {
-        /* LGE regime: three distinct vertices drawn uniformly over the shard. */
+        /* LGE regime: three distinct vertices drawn uniformly over the shard.
+         * A fuse graph with c = 1.12 and l start segments has (l + 2) / (l c)
+         * equations per vertex inside; with eq. (ln) segments at the LGE
+         * regime's sizes (l < 20 up to 16384 keys) that exceeds the GF(2)
+         * solvability threshold of ~0.918, and segments small enough to stay
+         * below it repeat edges (m / (2 c s^2) > 1). */
         uint64_t V = in->cells;
         uint64_t r = orc_mix64(local ^ ORC_C_EDGE);
         uint64_t q = orc_mix64(local ^ ORC_C_EDGE2);
@@ -429,7 +439,7 @@ static uint64_t value_at(const void *values, int b, uint64_t i) {
 /* Solve one shard: edges from local signatures, peel, optional GE on the
  * 2-core, reverse assignment. Returns 1 on success. */
 static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, const uint64_t *val,
-                       uint8_t *data, uint64_t base, uint64_t *peeled_out) {
+                       uint8_t *data, uint64_t base, uint64_t *peeled_out, pthread_mutex_t *cell_mu) {
     uint64_t V = in->cells;
     uint32_t *edges = malloc((m ? m : 1) * 3 * sizeof(uint32_t));
     uint32_t *order = malloc((m ? m : 1) * sizeof(uint32_t));
@@ -474,13 +484,139 @@ static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, cons
                 if (k != sd) x ^= w[edges[3 * e + k]];
             w[edges[3 * e + sd]] = x;
         }
+        /* cells of a bit array can share bytes with the neighbouring shard's */
+        if (cell_mu) pthread_mutex_lock(cell_mu);
         for (uint64_t v = 0; v < V; v++) cell_set(data, in->b, base + v, w[v]);
+        if (cell_mu) pthread_mutex_unlock(cell_mu);
     }
     free(w);
     free(edges);
     free(order);
     free(side);
     return ok;
+}
+
+/* (local signature, value) of one key of a function shard. */
+typedef struct {
+    uint64_t loc, val;
+} orc_pair;
+
+static int pair_cmp(const void *a, const void *b) {
+    const orc_pair *x = a, *y = b;
+    if (x->loc != y->loc) return x->loc < y->loc ? -1 : 1;
+    return x->val < y->val ? -1 : x->val > y->val;
+}
+
+/* Duplicate keys of one shard (Sec. 4.4-4.5). Within a shard, equal local
+ * signatures stand for the same key (for 64-bit keys exactly: the high
+ * signature word is a bijection of the key). A filter keeps one copy of each
+ * local signature. A function keeps one copy of each repeated (key, value)
+ * pair; a key given with two different values has no solution at any seed,
+ * which *conflict reports. Returns the shard's key count after de-duplication. */
+static uint64_t dedup_shard(int kind, int b, uint64_t m, uint64_t *L, uint64_t *Vv, int *conflict) {
+    if (kind == ORC_FILTER) {
+        qsort(L, m, sizeof(uint64_t), u64_cmp);
+        uint64_t u = 0;
+        for (uint64_t i = 0; i < m; i++)
+            if (u == 0 || L[i] != L[u - 1]) L[u++] = L[i];
+        /* the fingerprint is a function of the local signature */
+        for (uint64_t i = 0; i < u; i++) Vv[i] = orc_fingerprint(L[i], b);
+        return u;
+    }
+    orc_pair *pr = malloc((m ? m : 1) * sizeof *pr);
+    for (uint64_t i = 0; i < m; i++) {
+        pr[i].loc = L[i];
+        pr[i].val = Vv[i];
+    }
+    qsort(pr, m, sizeof *pr, pair_cmp);
+    uint64_t u = 0;
+    for (uint64_t i = 0; i < m; i++) {
+        if (u > 0 && pr[i].loc == pr[u - 1].loc) {
+            if (pr[i].val != pr[u - 1].val) *conflict = 1;
+            continue;
+        }
+        pr[u++] = pr[i];
+    }
+    for (uint64_t i = 0; i < u; i++) {
+        L[i] = pr[i].loc;
+        Vv[i] = pr[i].val;
+    }
+    free(pr);
+    return u;
+}
+
+/* The shards of one attempt, solved one after the other or by a pool of
+ * threads that take shards in turn (shards are independent systems, Sec. 4). */
+typedef struct {
+    const orc_info *in;
+    const uint64_t *start, *meff;
+    uint64_t *loc, *val;
+    uint8_t *data;
+    pthread_mutex_t mu, cell_mu;
+    int use_cell_mu;
+    uint64_t next;
+    int failed;
+    uint64_t peeled, core;
+} solve_ctx;
+
+static void *solve_worker(void *arg) {
+    solve_ctx *c = arg;
+    for (;;) {
+        pthread_mutex_lock(&c->mu);
+        uint64_t s = c->next++;
+        int stop = c->failed;
+        pthread_mutex_unlock(&c->mu);
+        if (stop || s >= c->in->shards) break;
+        uint64_t m = c->meff[s], pe = 0;
+        int ok = solve_shard(c->in, m, c->loc + c->start[s], c->val + c->start[s], c->data, s * c->in->cells, &pe,
+                             c->use_cell_mu ? &c->cell_mu : NULL);
+        pthread_mutex_lock(&c->mu);
+        c->peeled += pe;
+        c->core += m - pe;
+        if (!ok) c->failed = 1;
+        pthread_mutex_unlock(&c->mu);
+    }
+    return NULL;
+}
+
+/* Signatures of keys [i0, i1). */
+typedef struct {
+    const orc_params *p;
+    const void *keys;
+    const uint64_t *offsets;
+    uint64_t seed, i0, i1;
+    uint64_t *sig;
+} sig_ctx;
+
+static void *sig_worker(void *arg) {
+    sig_ctx *c = arg;
+    for (uint64_t i = c->i0; i < c->i1; i++) {
+        if (c->p->key_kind == ORC_KEYS_U64)
+            orc_sig_u64(((const uint64_t *)c->keys)[i], c->seed, c->sig + 2 * i);
+        else
+            orc_sig_bytes((const uint8_t *)c->keys + c->offsets[i], c->offsets[i + 1] - c->offsets[i], c->seed,
+                          c->sig + 2 * i);
+    }
+    return NULL;
+}
+
+static int thread_count(const orc_params *p) {
+    int t = p->threads;
+    if (t < 1) t = 1;
+    if (t > 256) t = 256;
+    return t;
+}
+
+/* Runs fn on ctx[0..t) in t threads (the calling thread takes ctx[0]). */
+static void run_threads(int t, void *(*fn)(void *), void *ctx, size_t ctx_size) {
+    pthread_t th[256];
+    int started[256] = {0};
+    for (int k = 1; k < t; k++) started[k] = pthread_create(&th[k], NULL, fn, (char *)ctx + (size_t)k * ctx_size) == 0;
+    fn(ctx);
+    for (int k = 1; k < t; k++) {
+        if (started[k]) pthread_join(th[k], NULL);
+        else fn((char *)ctx + (size_t)k * ctx_size);
+    }
 }
 
 int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
@@ -491,6 +627,7 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
     if (p->key_kind == ORC_KEYS_BYTES && offsets == NULL) return ORC_EINVAL;
     if (p->kind == ORC_FUNC && n > 0 && values == NULL) return ORC_EINVAL;
     *data_out = NULL;
+    const int nt = thread_count(p);
     uint64_t *sig = malloc((n ? n : 1) * 2 * sizeof(uint64_t));
     uint64_t *loc = malloc((n ? n : 1) * sizeof(uint64_t));
     uint64_t *val = malloc((n ? n : 1) * sizeof(uint64_t));
@@ -504,12 +641,18 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
         in.b = p->b;
         in.seed = p->seed + (uint64_t)attempt;
         in.retries = attempt;
-        for (uint64_t i = 0; i < n; i++) {
-            if (p->key_kind == ORC_KEYS_U64)
-                orc_sig_u64(((const uint64_t *)keys)[i], in.seed, sig + 2 * i);
-            else
-                orc_sig_bytes((const uint8_t *)keys + offsets[i], offsets[i + 1] - offsets[i], in.seed,
-                              sig + 2 * i);
+        {
+            sig_ctx sc[256];
+            for (int k = 0; k < nt; k++) {
+                sc[k].p = p;
+                sc[k].keys = keys;
+                sc[k].offsets = offsets;
+                sc[k].seed = in.seed;
+                sc[k].i0 = n * (uint64_t)k / (uint64_t)nt;
+                sc[k].i1 = n * (uint64_t)(k + 1) / (uint64_t)nt;
+                sc[k].sig = sig;
+            }
+            run_threads(nt, sig_worker, sc, sizeof sc[0]);
         }
         in.h = orc_plan_h(p, n, &in.regime, &in.h_bb, &in.h_dup);
         uint64_t *cnt = NULL;
@@ -536,32 +679,49 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
             loc[j] = orc_local(sig + 2 * i, in.h);
             val[j] = p->kind == ORC_FUNC ? value_at(values, p->b, i) : 0;
         }
-        uint8_t *data = calloc(in.data_bytes ? in.data_bytes : 1, 1);
-        int ok = 1;
+        /* Duplicates of every shard first, then the shards' systems. */
+        uint64_t *meff = malloc(in.shards * sizeof(uint64_t));
+        int conflict = 0;
         in.n_eff = 0;
-        for (uint64_t s = 0; s < in.shards && ok; s++) {
-            uint64_t m = cnt[s];
-            uint64_t *L = loc + start[s];
-            uint64_t *Vv = val + start[s];
-            if (p->kind == ORC_FILTER) {
-                /* Sec. 4.5: duplicate local signatures are dropped; the
-                 * fingerprint is a function of the local signature. */
-                qsort(L, m, sizeof(uint64_t), u64_cmp);
-                uint64_t u = 0;
-                for (uint64_t i = 0; i < m; i++)
-                    if (u == 0 || L[i] != L[u - 1]) L[u++] = L[i];
-                m = u;
-                for (uint64_t i = 0; i < m; i++) Vv[i] = orc_fingerprint(L[i], p->b);
+        for (uint64_t s = 0; s < in.shards; s++) {
+            meff[s] = dedup_shard(p->kind, p->b, cnt[s], loc + start[s], val + start[s], &conflict);
+            in.n_eff += meff[s];
+        }
+        uint8_t *data = NULL;
+        int ok = 0;
+        if (!conflict) {
+            data = calloc(in.data_bytes ? in.data_bytes : 1, 1);
+            solve_ctx c;
+            memset(&c, 0, sizeof c);
+            c.in = &in;
+            c.start = start;
+            c.meff = meff;
+            c.loc = loc;
+            c.val = val;
+            c.data = data;
+            pthread_mutex_init(&c.mu, NULL);
+            pthread_mutex_init(&c.cell_mu, NULL);
+            c.use_cell_mu = nt > 1 && !(p->b == 8 || p->b == 16 || p->b == 32 || p->b == 64);
+            if (nt == 1) {
+                solve_worker(&c);
+            } else {
+                pthread_t th[256];
+                int started[256] = {0};
+                for (int k = 1; k < nt; k++) started[k] = pthread_create(&th[k], NULL, solve_worker, &c) == 0;
+                solve_worker(&c);
+                for (int k = 1; k < nt; k++)
+                    if (started[k]) pthread_join(th[k], NULL);
             }
-            in.n_eff += m;
-            uint64_t pe = 0;
-            ok = solve_shard(&in, m, L, Vv, data, s * in.cells, &pe);
-            in.peeled += pe;
-            in.core += m - pe;
+            pthread_mutex_destroy(&c.mu);
+            pthread_mutex_destroy(&c.cell_mu);
+            ok = !c.failed;
+            in.peeled = c.peeled;
+            in.core = c.core;
         }
         free(cnt);
         free(start);
         free(fill);
+        free(meff);
         *info = in;
         if (ok) {
             *data_out = data;
@@ -571,6 +731,13 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
             return ORC_OK;
         }
         free(data);
+        if (conflict) {
+            /* the same key with two values: no seed can solve it */
+            free(sig);
+            free(loc);
+            free(val);
+            return ORC_EDUP;
+        }
     }
     free(sig);
     free(loc);
@@ -612,6 +779,46 @@ void orc_query(const orc_info *in, const uint8_t *data, int key_kind, const void
             ((uint64_t *)out)[i] = x;
         }
     }
+}
+
+typedef struct {
+    const orc_info *in;
+    const uint8_t *data;
+    int key_kind;
+    const void *keys;
+    const uint64_t *offsets;
+    uint64_t i0, i1;
+    void *out;
+} query_ctx;
+
+static void *query_worker(void *arg) {
+    query_ctx *c = arg;
+    uint64_t m = c->i1 - c->i0;
+    if (m == 0) return NULL;
+    size_t ob = c->in->kind == ORC_FILTER || c->in->b <= 8 ? 1 : c->in->b <= 16 ? 2 : c->in->b <= 32 ? 4 : 8;
+    if (c->key_kind == ORC_KEYS_U64)
+        orc_query(c->in, c->data, c->key_kind, (const uint64_t *)c->keys + c->i0, NULL, m,
+                  (uint8_t *)c->out + c->i0 * ob);
+    else  /* offsets stay absolute: the sub-range's offsets index the same byte buffer */
+        orc_query(c->in, c->data, c->key_kind, c->keys, c->offsets + c->i0, m, (uint8_t *)c->out + c->i0 * ob);
+    return NULL;
+}
+
+void orc_query_mt(const orc_info *in, const uint8_t *data, int key_kind, const void *keys,
+                  const uint64_t *offsets, uint64_t m, void *out, int threads) {
+    int t = threads < 1 ? 1 : threads > 256 ? 256 : threads;
+    query_ctx qc[256];
+    for (int k = 0; k < t; k++) {
+        qc[k].in = in;
+        qc[k].data = data;
+        qc[k].key_kind = key_kind;
+        qc[k].keys = keys;
+        qc[k].offsets = offsets;
+        qc[k].i0 = m * (uint64_t)k / (uint64_t)t;
+        qc[k].i1 = m * (uint64_t)(k + 1) / (uint64_t)t;
+        qc[k].out = out;
+    }
+    run_threads(t, query_worker, qc, sizeof qc[0]);
 }
 
 /* --------------------------------------------------- batch helpers for tests */

@@ -9,8 +9,10 @@
  * includes or calls anything in this directory, and this directory includes
  * nothing from the product.
  *
- * Everything here is deliberately slow and sequential: one key at a time, a
- * plain stack-based peeling visit, plain Gaussian elimination over GF(2).
+ * Everything here is deliberately slow and plain: one key at a time, a
+ * stack-based peeling visit, plain Gaussian elimination over GF(2). The only
+ * concurrency is optional (orc_params.threads): independent shards, and
+ * contiguous ranges of keys, handed to a pool of threads.
  *
  * Parity status of each function is stated next to its declaration.
  */
@@ -26,7 +28,9 @@ enum { ORC_FUNC = 0, ORC_FILTER = 1 };
 enum { ORC_KEYS_U64 = 0, ORC_KEYS_BYTES = 1 };
 enum { ORC_MODE_AUTO = 0, ORC_MODE_FUSE = 1, ORC_MODE_LGE = 2, ORC_MODE_MWHC = 3 };
 enum { ORC_REGIME_FUSE = 1, ORC_REGIME_LGE = 2, ORC_REGIME_MWHC = 3 };
-enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EBUILD = 3 };
+/* ORC_EDUP: a function was given the same key with two different values
+ * (no seed can solve it, so it is not retried). */
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EBUILD = 3, ORC_EDUP = 4 };
 
 typedef struct {
     int kind;             /* ORC_FUNC or ORC_FILTER */
@@ -40,11 +44,13 @@ typedef struct {
     uint64_t lge_threshold;  /* auto mode: n below this -> LGE regime */
     uint64_t lge_target;     /* LGE regime: wanted mean keys per shard */
     uint64_t lge_max_shard;  /* LGE regime: largest allowed shard */
+    int threads;          /* signatures and shards computed by this many threads (1: one after the other);
+                           * shards are independent, so the result does not depend on it */
 } orc_params;
 
 typedef struct {
     uint64_t n;           /* keys given */
-    uint64_t n_eff;       /* keys after filter de-duplication */
+    uint64_t n_eff;       /* keys after de-duplication */
     int kind, b, regime;
     int h;                /* shard bits; shards = 2^h */
     int h_bb, h_dup;      /* the two bounds h is the minimum of (fuse and MWHC regimes) */
@@ -98,6 +104,9 @@ uint64_t orc_fingerprint(uint64_t local, int b);
 
 /* Build. keys: uint64 array (ORC_KEYS_U64) or packed bytes with offsets[n+1].
  * values: func only, uint8/16/32/64 per b (<=8, <=16, <=32, <=64 bits); low b bits used.
+ * Keys with equal (shard, local signature) are the same key: a filter keeps one
+ * copy, a function one copy of each repeated (key, value) pair, and a key with
+ * two different values returns ORC_EDUP at once (info then describes that attempt).
  * On success *data is a malloc'ed array of info->data_bytes bytes. */
 int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
               const void *values, uint64_t n, orc_info *info, uint8_t **data);
@@ -106,6 +115,9 @@ void orc_free(void *ptr);
 /* Query m keys against (info, data). out: func -> value type of b; filter -> uint8 0/1. */
 void orc_query(const orc_info *info, const uint8_t *data, int key_kind, const void *keys,
                const uint64_t *offsets, uint64_t m, void *out);
+/* orc_query with the keys split into `threads` contiguous ranges, one per thread. */
+void orc_query_mt(const orc_info *info, const uint8_t *data, int key_kind, const void *keys,
+                  const uint64_t *offsets, uint64_t m, void *out, int threads);
 
 /* Cell access (Sec. 5 layout: native array for b in {8,16,32,64}, else a bit array). */
 uint64_t orc_cell_get(const uint8_t *data, int b, uint64_t i);

@@ -182,7 +182,7 @@ def test_segment_size_estimates(orc):
     assert g.cells == g.T * g.seg and g.T == math.ceil(1.12 * 2**20 / 8192)
     g = orc.geometry(orc.REGIME_LGE, 4, 10_000)
     assert g.cells == math.ceil(1.12 * 10_000)
-    assert orc.geometry(orc.REGIME_LGE, 0, 3).cells == 32
+    assert orc.geometry(orc.REGIME_LGE, 4, 3).cells == 32
 
 
 # -------------------------------------------------------- edges, fingerprints
@@ -210,7 +210,8 @@ def test_fuse_edges_in_consecutive_segments_and_monotone(orc):
 
 
 def test_lge_edges_distinct_uniform(orc):
-    info = _info(orc, orc.REGIME_LGE, 0, 1000)
+    # sharded LGE-regime shards: three distinct uniform vertices
+    info = _info(orc, orc.REGIME_LGE, 1, 1000)
     loc = synth.u64_keys(0, 50_000, 8)
     e = orc.edges_of(info, loc).astype(np.int64)
     assert (e < info.cells).all()
@@ -221,7 +222,7 @@ def test_lge_edges_distinct_uniform(orc):
         dof = info.cells - 1
         assert ((cnt - exp_) ** 2 / exp_).sum() < dof + 6 * math.sqrt(2 * dof)
     # small case, exhaustive: every ordered distinct triple is reachable
-    tiny = _info(orc, orc.REGIME_LGE, 0, 3)
+    tiny = _info(orc, orc.REGIME_LGE, 1, 3)
     tiny.cells = 5
     e = orc.edges_of(tiny, synth.u64_keys(0, 40_000, 9))
     assert len({tuple(r) for r in e.tolist()}) == 5 * 4 * 3
@@ -406,12 +407,156 @@ def test_filter_deduplicates_keys(orc):
 
 
 def test_function_with_conflicting_duplicates_fails(orc):
+    # a key given twice with two values makes two equations with the same left
+    # side and different right sides (eq. MWHC): no seed solves it, so the build
+    # stops at the first attempt with ORC_EDUP instead of retrying
     keys = synth.u64_keys(0, 1000, 5)
     dup = np.concatenate([keys, keys[:1]])
     vals = np.zeros(1001, dtype=np.uint8)
     vals[-1] = 1
-    st, _, _ = orc.build(orc.default_params(max_retries=2), dup, vals)
-    assert st == orc.EBUILD
+    for mode in (orc.MODE_AUTO, orc.MODE_FUSE, orc.MODE_MWHC):
+        for seed in (0, 1, 7):
+            st, info, _ = orc.build(orc.default_params(max_retries=2, mode=mode, seed=seed), dup, vals)
+            assert st == orc.EDUP and info.retries == 0 and info.seed == seed, (mode, seed)
+
+
+def _lge_sharded(orc, **kw):
+    return orc.default_params(mode=orc.MODE_LGE, lge_target=1024, **kw)
+
+
+@pytest.mark.parametrize("regime", ["lge_unsharded", "lge_sharded", "fuse", "mwhc"])
+def test_function_repeated_pairs_are_dropped(orc, regime):
+    # Sec. 4.4: the local signature stands for the key inside its shard. A
+    # function given the same (key, value) pair several times describes the
+    # same function as one given it once: one copy of each equation is kept
+    # (n_eff counts the distinct keys; the largest shard M, and with it the
+    # geometry, counts every key given), and every key decodes to its value
+    # (Problem 1).
+    n = {"lge_unsharded": 6000, "lge_sharded": 20_000, "fuse": 3000, "mwhc": 30_000}[regime]
+    keys = synth.u64_keys(0, n, 41)
+    vals = synth.values(n, 8, 41)
+    rng = np.random.default_rng(41)
+    rep = rng.integers(0, n, size=n // 4)
+    dk = np.concatenate([keys, keys[rep], keys[rep[:50]]])
+    dv = np.concatenate([vals, vals[rep], vals[rep[:50]]])
+    perm = rng.permutation(len(dk))
+    dk, dv = dk[perm], dv[perm]
+    kw = {"lge_unsharded": dict(), "lge_sharded": dict(mode=orc.MODE_LGE, lge_target=1024),
+          "fuse": dict(mode=orc.MODE_FUSE, max_retries=60), "mwhc": dict(mode=orc.MODE_MWHC, eps=0.01, eta=1e-3,
+                                                                       max_retries=60)}[regime]
+    for seed in (3, 4):
+        st, info, data = orc.build(orc.default_params(seed=seed, **kw), dk, dv)
+        assert st == orc.OK
+        assert info.n == len(dk) and info.n_eff == n and info.seed == seed + info.retries
+        assert (orc.query(info, data, dk) == dv).all()
+        # the same structure decodes the distinct keys: it is their function
+        assert (orc.query(info, data, keys) == vals).all()
+
+
+def test_byte_string_function_duplicates(orc):
+    data_, offs = synth.byte_strings(0, 3000, 12)
+    vals = synth.values(3000, 16, 12)
+    # repeat string 7 with its value, and string 9 with another value
+    strs = [bytes(data_[offs[i]:offs[i + 1]]) for i in range(3000)]
+    for extra, ok in (([(7, vals[7])], True), ([(7, vals[7]), (9, vals[9] ^ 1)], False)):
+        s2 = strs + [strs[i] for i, _ in extra]
+        v2 = np.concatenate([vals, np.array([v for _, v in extra], dtype=vals.dtype)])
+        o2 = np.zeros(len(s2) + 1, dtype=np.uint64)
+        o2[1:] = np.cumsum([len(x) for x in s2])
+        buf = np.frombuffer(b"".join(s2), dtype=np.uint8)
+        st, info, data = orc.build(orc.default_params(b=16, key_kind=orc.KEYS_BYTES, seed=2), buf, v2, offsets=o2)
+        if ok:
+            assert st == orc.OK and info.n_eff == 3000
+            assert (orc.query(info, data, buf, offsets=o2) == v2).all()
+        else:
+            assert st == orc.EDUP
+
+
+def test_threads_give_the_same_structure(orc):
+    # shards are independent systems (Sec. 4): solving them on a pool of threads
+    # changes nothing in the result; bit-array cells (b = 13) share bytes across
+    # shard boundaries
+    cases = [(orc.FUNC, 8, dict(mode=orc.MODE_LGE, lge_target=2048), 40_000),
+             (orc.FUNC, 13, dict(mode=orc.MODE_MWHC, eps=0.01, eta=1e-3), 100_000),
+             (orc.FILTER, 8, dict(mode=orc.MODE_MWHC, eps=0.01, eta=1e-3), 100_000),
+             (orc.FUNC, 5, dict(mode=orc.MODE_LGE, lge_target=1024), 20_000)]
+    for kind, b, kw, n in cases:
+        keys = synth.u64_keys(0, n, 17)
+        vals = synth.values(n, b, 17) if kind == orc.FUNC else None
+        st1, i1, d1 = orc.build(orc.default_params(kind=kind, b=b, seed=5, **kw), keys, vals)
+        st4, i4, d4 = orc.build(orc.default_params(kind=kind, b=b, seed=5, threads=4, **kw), keys, vals)
+        assert st1 == st4 == orc.OK and i1.h > 0
+        assert i1.as_dict() == i4.as_dict()
+        assert (d1 == d4).all()
+        other = synth.u64_keys(n, n, 17)
+        assert (orc.query(i1, d1, other) == orc.query(i1, d1, other, threads=5)).all()
+
+
+# ------------------------------------------- LGE-regime hypergraphs (reading)
+
+def _gf2_consistent(rows, rhs, nbits):
+    """Rank test over GF(2), bit plane by bit plane: [A] and [A | v] have the
+    same rank. rows: vertex sets as Python integer bit masks."""
+    for j in range(nbits):
+        piv = {}
+        for r, v in zip(rows, rhs):
+            x, y = r, (int(v) >> j) & 1
+            while x:
+                top = x.bit_length() - 1
+                if top not in piv:
+                    piv[top] = (x, y)
+                    break
+                px, py = piv[top]
+                x, y = x ^ px, y ^ py
+            if x == 0 and y == 1:
+                return False
+    return True
+
+
+def _rows(e):
+    return [(1 << int(a)) ^ (1 << int(c)) ^ (1 << int(d)) for a, c, d in e]
+
+
+def test_lge_regime_uses_uniform_triples_not_small_fuse_graphs(orc):
+    # Sec. 4.2 keeps c = 1.12 for small sizes with LGE. A fuse graph with l
+    # start segments and c = 1.12 has (l + 2) / (l c) equations per vertex away
+    # from its ends; with eq. (ln) segments at 1000 keys (l = 7) that is 1.15,
+    # above the ~0.918 GF(2) solvability threshold of random 3-uniform systems,
+    # so the system is inconsistent (rank test); three distinct uniform
+    # vertices over the same ceil(1.12 n) cells are consistent.
+    M = 1000
+    lg = math.floor(math.log(M) / math.log(3.33) + 2.25)
+    fuse = orc.geometry(orc.REGIME_FUSE, 0, M)
+    assert fuse.lg_seg == lg == 7 and fuse.c == 1.12 and fuse.l == 7
+    uni = orc.geometry(orc.REGIME_LGE, 0, M)
+    assert uni.cells == math.ceil(1.12 * M)
+    for r in range(4):
+        loc = synth.u64_keys(0, M, 900 + r)
+        rhs = synth.values(M, 1, 900 + r)
+        assert not _gf2_consistent(_rows(orc.edges_of(fuse, loc)), rhs, 1)
+        assert _gf2_consistent(_rows(orc.edges_of(uni, loc)), rhs, 1)
+
+
+def test_lge_success_matches_gf2_rank(orc):
+    # Sec. 3.3: a shard is solvable iff its system is consistent. Small builds
+    # (40 keys in 45 cells, b = 2) fail often enough to see both outcomes; the
+    # oracle's first attempt must succeed exactly when the rank test on its
+    # edges says the system is consistent.
+    n, b = 40, 2
+    seen = {True: 0, False: 0}
+    for seed in range(120):
+        keys = synth.u64_keys(0, n, 1000 + seed)
+        vals = synth.values(n, b, 1000 + seed)
+        st, info, data = orc.build(orc.default_params(b=b, seed=seed, max_retries=0), keys, vals)
+        geo = orc.geometry(orc.REGIME_LGE, 0, n)
+        e = orc.edges_of(geo, orc.sigs(keys, seed)[:, 0])
+        want = _gf2_consistent(_rows(e), vals, b)
+        assert (st == orc.OK) == want, seed
+        seen[want] += 1
+        if st == orc.OK:
+            assert info.regime == orc.REGIME_LGE and info.h == 0
+            assert (orc.query(info, data, keys) == vals).all()
+    assert seen[True] > 0 and seen[False] > 0, seen
 
 
 def test_retry_restarts_with_next_seed(orc):
