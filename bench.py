@@ -8,11 +8,20 @@ the 10^8 members and 10^8 disjoint non-members (false-positive rate ~ 2^-8).
 CUDA events on the launching stream); the query rate is reported next to it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                    [--workload c2|c1|c3]
+                    [--workload c2|c1|c3|c4|c5|mwhc] [--no-extras] [--no-cpu-baseline]
 
---impl reference times the plain CPU oracle (the paper's algorithm, one
-thread) on a bounded sample of the same workload. Under torchrun every rank
-builds its own replica (the structure is single-GPU; replicas only).
+The default run also carries the rest of the metric as sub-objects, each
+measured after the headline: "c4" (4096 uneven structures, one batched
+graph-captured build against one vf_build per structure), "c5_scale" (one
+VFilter of 5e9 keys built by shard group, and its queries against the HBM
+random-sector roofline) and "c5_serving" (Poisson builds and queries under a
+memory budget, p50/p99 latency). "cpu_baseline" is the oracle on every host
+core over the whole workload; "cpu_baseline_1core" one core on a sample.
+
+--impl reference times the plain CPU oracle (the paper's algorithm; shards
+solved on every host core) on a bounded sample of the same workload. Under
+torchrun every rank builds its own replica (the structure is single-GPU;
+replicas only).
 """
 from __future__ import annotations
 
@@ -59,20 +68,40 @@ WORKLOADS = {
              {"mode": "mwhc", "eps": 0.01, "eta": 1e-3}),
 }
 
-# Algorithmic DRAM bytes per unit for each phase kernel (unit: key, edge or query).
-# Random accesses count one 32-byte sector each.
+# Algorithmic DRAM bytes per unit (key, edge or query) of each phase: the
+# method's own traffic with shard state off chip, every random access one
+# 32-byte sector and every random update a read-modify-write of one (64 B).
+# Streams: the key is read by the histogram and again by the scatter pass (hash
+# recomputed), the bucketed (local signature, value) pair is written once and
+# read once, the data array written once (c cells of b bits per key).
+# Random updates: incidence 3 (degree/edge-index words of the three vertices),
+# peel 3 (removal from the three vertices), assignment 3 + 1 (the other two
+# vertices' values read, the peeled cell written, its word updated).
+def _vb(b, kind):
+    return 0.0 if kind == "filter" else (1.0 if b <= 8 else 2.0 if b <= 16 else 4.0)
+
+
 ALGO_BYTES = {
-    "hash_hist": lambda b, kind: 8.0,                                   # key read
-    # key in, local signature out (+ values); the fuse regime's tile sort is added in phase_table
+    "hash_hist": lambda b, kind: 8.0,
+    "scatter": lambda b, kind: 8.0 + _vb(b, kind) + 8.0 + _vb(b, kind),
+    "incidence": lambda b, kind: 8.0 + 3 * 64.0,
+    "peel": lambda b, kind: 3 * 64.0,
+    "assign": lambda b, kind: _vb(b, kind) + 4 * 64.0 + 1.105 * b / 8,
+    "lge": lambda b, kind: 8.0 + _vb(b, kind) + 1.12 * b / 8,   # shard state on chip
+    "query": lambda b, kind: 8.0 + 3 * 32.0 + (1.0 if kind == "filter" else max(1.0, b / 8)),
+}
+
+# The same phases counted by what the kernels here move (the tile sort's extra
+# pass, the asynchronous peel's 16-byte records and queue items, the polled
+# value words of the dataflow assignment): a second figure, for comparison.
+KERNEL_BYTES = {
+    "hash_hist": lambda b, kind: 8.0,
     "scatter": lambda b, kind: 8.0 + 8.0 + (0 if kind == "filter" else 1.0 + 4.0),
-    "incidence": lambda b, kind: 8.0 + 3 * 32.0,                        # local sig + 3 vertex-word sectors
-    # asynchronous fuse solver (the default): local signature (tile-ordered, streamed), value,
-    # two vertex-word sectors (fetch-and-add), record written, queue item written + read
+    "incidence": lambda b, kind: 8.0 + 3 * 32.0,
     "peel": lambda b, kind: 8 + (0 if kind == "filter" else 4) + 2 * 32 + 16 + 16,
-    # record read, two value-word sectors polled, own value word, data cell
     "assign": lambda b, kind: 16 + 2 * 32 + 32 + 32,
-    "lge": lambda b, kind: 8.0 + 8.0 * 3,                               # per key, shard state on chip (lower bound)
-    "query": lambda b, kind: 8.0 + 3 * 32.0 + 1.0,                      # key, 3 cell sectors, output
+    "lge": lambda b, kind: 8.0 + 8.0 * 3,
+    "query": lambda b, kind: 8.0 + 3 * 32.0 + 1.0,
 }
 
 
@@ -349,8 +378,34 @@ def run_gpu(args):
         "clocks": clk,
         "check": {"members_ok": ok, "fpr": fpr, "retries": int(info.retries)},
     }
+    # the query's bound: its three random sectors come from L2 while the data
+    # array fits there (the key stream and the output from HBM), else from HBM
+    qps = 2 * n * world / (q_ms * 1e-3)
+    q_hbm = random_sector_roofline(qps / world, b, kind, hbm, peak_kind)
+    out["query"]["roofline"] = {"hbm": q_hbm}
+    if info.data_bytes <= L2_BYTES:
+        l2 = l2_sector_rate(int(info.data_bytes), kd.device)
+        got = 3 * qps / world
+        out["query"]["roofline"]["l2"] = {
+            "bound": "l2", "unit": "G sectors/s", "achieved": round(got / 1e9, 3),
+            "peak": round(l2["sectors_per_s"] / 1e9, 3), "frac": round(got / l2["sectors_per_s"], 4),
+            "peak_source": "measured in this run: " + l2["source"],
+            "data_bytes": int(info.data_bytes), "l2_bytes": L2_BYTES}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload, quick=True)
+        # the oracle on every host core over the whole workload, and on one
+        # core over a bounded sample
+        full = args.workload in ("c1", "c2", "mwhc") and not args.n
+        out["cpu_baseline"] = cpu_baseline(args.workload, quick=True, threads=host_threads(), full=full)
+        out["cpu_baseline_1core"] = cpu_baseline(args.workload, quick=True, threads=1)
+    if rank == 0 and world == 1 and args.workload == "c2" and not args.n and not args.no_extras:
+        # the other parts of the metric, each with its own warm-up and clocks:
+        # batched vs plain per-structure builds, the 5e9-key build and its
+        # HBM-bound queries, and serving latency percentiles
+        del kd, vd, od, xd, xo, kh, vh, oh, xh, xoh, outh, l2_flush
+        torch.cuda.empty_cache()
+        out["c4"] = measure_c4(3, 3)
+        out["c5_scale"] = measure_c5_scale(5_000_000_000, hbm, peak_kind)
+        out["c5_serving"] = measure_c5_serving()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -372,20 +427,23 @@ def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse):
     for ph, (ms, cnt) in phases.items():
         if cnt == 0:
             continue
-        per_unit = ALGO_BYTES[ph](b, kind)
+        kb = KERNEL_BYTES[ph](b, kind)
         if ph == "scatter" and fuse:  # tile sort: signatures (and values) read and written once more
-            per_unit += 16.0 + (0 if kind == "filter" else 8.0)
-        algo = per_unit * units[ph]
+            kb += 16.0 + (0 if kind == "filter" else 8.0)
         per_phase[ph] = {"ms_total": round(ms, 3), "kernels": cnt, "passes": passes[ph],
                          "ms_per_pass": round(ms / passes[ph], 4), "share": round(ms / total, 4),
-                         "achieved_gbs": round(algo / (ms * 1e-3) / 1e9, 2)}
+                         "achieved_gbs": round(ALGO_BYTES[ph](b, kind) * units[ph] / (ms * 1e-3) / 1e9, 2),
+                         "kernel_model_gbs": round(kb * units[ph] / (ms * 1e-3) / 1e9, 2)}
     dom = max(per_phase, key=lambda k: per_phase[k]["share"]) if per_phase else None
     roof = None
     if dom:
         d = per_phase[dom]
+        kb = KERNEL_BYTES[dom](b, kind) + (16.0 + (0 if kind == "filter" else 8.0) if dom == "scatter" and fuse else 0)
         roof = {"bound": "hbm", "kernel": dom, "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": round(d["achieved_gbs"] / hbm, 4), "traffic": TRAFFIC.get((workload, dom)),
-                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_unit": ALGO_BYTES[dom](b, kind)}
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_unit": ALGO_BYTES[dom](b, kind),
+                "kernel_model": {"bytes_per_unit": kb, "achieved": d["kernel_model_gbs"],
+                                 "frac": round(d["kernel_model_gbs"] / hbm, 4)}}
     return per_phase, dom, roof
 
 
@@ -399,41 +457,56 @@ TRAFFIC = {("c2", "peel"): round(1067.88e6 / 2e7 * 1e8),   # k_flow_peel, one la
 
 # ---------------------------------------------------------------- reference arm
 
-def oracle_sample(workload: str, quick: bool):
-    """Bounded sample of the workload for the single-thread oracle."""
+def oracle_sample(workload: str, quick: bool, threads: int = 1):
+    """Bounded sample of the workload for the oracle: a few seconds of host
+    work per build (more keys, hence several shards, for several threads)."""
     kind, b, n, kk = WORKLOADS[workload][:4]
     if len(WORKLOADS[workload]) > 5 and WORKLOADS[workload][5].get("mode") == "lge":
         # plain Gaussian elimination of every 2-core is cubic: a few shards only
-        return kind, b, min(n, 40_000), kk
-    ns = min(n, 4_000_000 if quick else 8_000_000)
+        return kind, b, min(n, 40_000 * threads), kk
+    ns = min(n, 25_000_000 if threads > 1 else 4_000_000 if quick else 8_000_000)
     return kind, b, ns, kk
 
 
-def cpu_baseline(workload: str, quick: bool = True):
+def host_threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except Exception:
+        return max(1, os.cpu_count() or 1)
+
+
+def cpu_baseline(workload: str, quick: bool = True, threads: int = 1, full: bool = False):
+    """The oracle timed on the host: `threads` threads (shards solved side by
+    side, queries split), on the whole workload (`full`) or a bounded sample."""
     from oracle import oracle as O
     from paper_2503_18397_gb300 import synth
 
-    kind, b, ns, kk = oracle_sample(workload, quick)
+    kind, b, ns, kk = oracle_sample(workload, quick, threads)
+    if full:
+        ns = WORKLOADS[workload][2]
+    gseed = 0x5EED if full else 3
     if kk == "u64":
-        keys, offs = synth.u64_keys(0, ns, 3), None
-        other, ooffs = synth.u64_keys(ns, ns, 3), None
+        keys, offs = synth.u64_keys(0, ns, gseed), None
+        other, ooffs = synth.u64_keys(ns, ns, gseed), None
     else:
-        keys, offs = synth.byte_strings(0, ns, 3)
-        other, ooffs = synth.byte_strings(ns, ns, 3)
-    vals = synth.values(ns, b, 3) if kind == "func" else None
+        keys, offs = synth.byte_strings(0, ns, gseed)
+        other, ooffs = synth.byte_strings(ns, ns, gseed)
+    vals = synth.values(ns, b, gseed) if kind == "func" else None
     p = O.default_params(kind=O.FILTER if kind == "filter" else O.FUNC, b=b,
-                         key_kind=O.KEYS_BYTES if offs is not None else O.KEYS_U64, seed=1)
+                         key_kind=O.KEYS_BYTES if offs is not None else O.KEYS_U64, seed=1, threads=threads)
     apply_overrides(p, workload, O)
     t0 = time.perf_counter()
     st, info, data = O.build(p, keys, vals, offsets=offs)
     t1 = time.perf_counter()
-    O.query(info, data, keys, offsets=offs)
-    O.query(info, data, other, offsets=ooffs)
+    O.query(info, data, keys, offsets=offs, threads=threads)
+    O.query(info, data, other, offsets=ooffs, threads=threads)
     t2 = time.perf_counter()
-    return {"value": round((t1 - t0) * 1e9 / ns, 3), "unit": "ns/key", "cores": 1, "kind": "oracle",
-            "query_gqps": round(2 * ns / (t2 - t1) / 1e9, 6),
-            "sample": f"oracle build of {ns} keys ({kind}, b={b}, same parameters) + query of {2 * ns} keys "
-                      f"(members + disjoint), single thread"}
+    what = "the whole workload" if full else f"a sample of {ns} keys"
+    return {"value": round((t1 - t0) * 1e9 / ns, 3), "unit": "ns/key", "cores": threads, "kind": "oracle",
+            "query_gqps": round(2 * ns / (t2 - t1) / 1e9, 6), "retries": int(info.retries),
+            "sample": f"oracle build of {what} ({ns} keys, {kind}, b={b}, same parameters, seed 1, "
+                      f"{info.retries} retries) + query of {2 * ns} keys (members + disjoint), "
+                      f"{threads} thread{'s' if threads > 1 else ''} (shards solved side by side)"}
 
 
 def run_reference(args):
@@ -444,38 +517,36 @@ def run_reference(args):
     from oracle import oracle as O
 
     O.build_oracle()
-    kind, b, ns, kk = oracle_sample(args.workload, quick=True)
+    threads = host_threads()
+    kind, b, ns, kk = oracle_sample(args.workload, quick=True, threads=threads)
     for _ in range(args.warmup if args.warmup < 1 else 1):
-        cpu_baseline(args.workload, quick=True)
+        cpu_baseline(args.workload, quick=True, threads=threads)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args.workload, quick=True))
+        vals.append(cpu_baseline(args.workload, quick=True, threads=threads))
     t1 = time.perf_counter()
     v = statistics.mean(x["value"] for x in vals)
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "ns/key", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round((t1 - t0) * 1e3 / args.steps, 3),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][4], "n": ns, "b": b, "kind": kind},
-           "cpu_baseline": {"value": round(v, 3), "unit": "ns/key", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": round(v, 3), "unit": "ns/key", "cores": threads, "kind": "oracle",
                             "sample": vals[0]["sample"]},
            "e2e": {"value": round(v, 3), "unit": "ns/key", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "query_gqps": statistics.mean(x["query_gqps"] for x in vals)}
     print(json.dumps(out), flush=True)
 
 
-def run_batch(args):
-    """Batched build of many uneven structures against the plain per-structure path."""
+def measure_c4(steps: int, warmup: int, count: int = 4096) -> dict:
+    """Batched build of `count` uneven structures (one persistent, graph-captured
+    solver launch, autotuned options) against the plain per-structure path (one
+    vf_build per structure, same seeds and options) on the same GPU."""
     import torch
 
     import paper_2503_18397_gb300 as vf
-    from paper_2503_18397_gb300 import build as vbuild
     from paper_2503_18397_gb300 import synth
 
-    torch.cuda.set_device(0)
-    vbuild.build()
-    vf.lib()
-    count = args.n or 4096
     rng = np.random.default_rng(0xC4)
     sizes = synth.log_uniform_sizes(count, 1e3, 1e6, 0xC4)
     kinds = rng.integers(0, 2, size=count)
@@ -493,84 +564,119 @@ def run_batch(args):
     best, sample_ms = vf.vf_tune_batch(items)
     tune_s = time.perf_counter() - t0
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         for s_ in vf.vf_build_batch(items, opts=best):
             s_.free()
     torch.cuda.synchronize()
-    clocks = Clocks(0)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     vf.vf_timing_read()
     vf.vf_timing_enable(True)
     ms = []
-    for _ in range(args.steps):
+    last = None
+    for _ in range(steps):
         ev[0].record(stream)
         structs = vf.vf_build_batch(items, opts=best, stream=stream)
         ev[1].record(stream)
         torch.cuda.synchronize()
         ms.append(ev[0].elapsed_time(ev[1]))
+        if last is not None:
+            for s_ in last:
+                s_.free()
         last = structs
-        for s_ in structs[:-8]:
-            s_.free()
     vf.vf_timing_enable(False)
     phases = vf.vf_timing_read()
-    clk = clocks.stop()
     # members of a few structures decode exactly
     ok = True
     for i in range(count - 8, count):
         out = last[i].query(items[i][0])
         if items[i][2] == 0:
-            ok &= bool((out.view(torch.int32 if bs[i] == 32 else torch.int16 if bs[i] > 8 else torch.uint8) ==
-                        items[i][1].view(torch.int32 if bs[i] == 32 else torch.int16 if bs[i] > 8 else torch.uint8))
-                       .all().item())
+            dt = torch.int32 if bs[i] == 32 else torch.int16 if bs[i] > 8 else torch.uint8
+            ok &= bool((out.view(dt) == items[i][1].view(dt)).all().item())
         else:
             ok &= bool(out.bool().all().item())
-        last[i].free()
+    for s_ in last:
+        s_.free()
     # plain per-structure path: one vf_build per structure, same seeds and options
     torch.cuda.synchronize()
-    ev[0].record(stream)
-    for (k, v, kind, b, seed) in items:
-        p = vf.vf_params_default(kind=kind, b=b, seed=seed, lge_threshold=best.lge_threshold,
-                                 lge_target=best.lge_target)
-        vf.vf_build(k, v, params=p, stream=stream).free()
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    plain_ms = ev[0].elapsed_time(ev[1])
+    plain = []
+    for _ in range(2):
+        ev[0].record(stream)
+        for (k, v, kind, b, seed) in items:
+            p = vf.vf_params_default(kind=kind, b=b, seed=seed, lge_threshold=best.lge_threshold,
+                                     lge_target=best.lge_target)
+            vf.vf_build(k, v, params=p, stream=stream).free()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        plain.append(ev[0].elapsed_time(ev[1]))
+    clk = clocks.stop()
+    plain_ms = plain[-1]  # the first pass is its warm-up
     b_ms = statistics.mean(ms)
     total_ms = sum(v[0] for v in phases.values())
-    out = {
-        "metric": METRIC, "value": round(b_ms * 1e6 / total, 4), "unit": "ns/key", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(b_ms, 3), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOADS["c4"][4], "structures": count, "total_keys": total,
-                   "l2": "inputs larger than L2 (no flush)", "tuned": best.as_dict()},
+    del items
+    torch.cuda.empty_cache()
+    return {
+        "workload": WORKLOADS["c4"][4], "structures": count, "total_keys": total,
+        "value": round(b_ms * 1e6 / total, 4), "unit": "ns/key", "ms_per_batch": round(b_ms, 3),
+        "steps": steps, "warmup": warmup, "tuned": best.as_dict(),
         "plain_path": {"ms": round(plain_ms, 3), "ns_per_key": round(plain_ms * 1e6 / total, 4),
-                       "speedup_batched": round(plain_ms / b_ms, 3)},
+                       "speedup_batched": round(plain_ms / b_ms, 3),
+                       "what": "one vf_build per structure, same seeds and options, after one untimed pass"},
         "tuner": {"seconds": round(tune_s, 3), "sample_ms": sample_ms},
         "phases": {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / max(total_ms, 1e-9), 4)}
                    for k, v in phases.items() if v[1]},
         "gpu_launches": int(sum(v[1] for v in phases.values())),
-        "clocks": clk,
-        "check": {"members_ok": ok},
+        "clocks": clk, "check": {"members_ok": ok},
     }
-    print(json.dumps(out), flush=True)
 
 
-def run_serving(args):
-    """Scale (one 5e9-key VFilter built by shard group) and serving (Poisson mix)."""
+def random_sector_roofline(qps: float, b: int, kind: str, hbm: float, peak_kind: str) -> dict:
+    """A query against a data array larger than L2: three random 32-byte
+    sectors from HBM per key, plus its 8-byte key and its output."""
+    per_q = ALGO_BYTES["query"](b, kind)
+    sectors = 3 * qps
+    return {"bound": "hbm", "unit": "GB/s", "achieved": round(per_q * qps / 1e9, 2), "peak": hbm,
+            "frac": round(per_q * qps / 1e9 / hbm, 4), "peak_source": f"{peak_kind} hbm_gbs",
+            "sectors_per_s": round(sectors / 1e9, 3), "sector_peak_per_s": round(hbm / 32, 3),
+            "bytes_per_query": per_q}
+
+
+def l2_sector_rate(table_bytes: int, device) -> dict:
+    """Random 32-byte sector reads per second that torch.take sustains from an
+    L2-resident table of `table_bytes` (one random 4-byte element per index,
+    indices streamed from HBM): the L2 denominator of an L2-resident query."""
+    import torch
+
+    n = max(1 << 20, table_bytes // 4)
+    table = torch.arange(n, dtype=torch.int32, device=device)
+    m = 1 << 27
+    idx = torch.randint(0, n, (m,), device=device, dtype=torch.int64)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 0.0
+    for it in range(6):
+        torch.take(table, idx[: 1 << 20])  # touch the table: it stays in L2
+        e0.record(st)
+        out = torch.take(table, idx)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if it > 0:
+            best = max(best, m / (e0.elapsed_time(e1) * 1e-3))
+    del table, idx, out
+    torch.cuda.empty_cache()
+    return {"sectors_per_s": best, "source": f"torch.take of 2^27 random 4-byte elements from a "
+                                             f"{table_bytes / 1e6:.1f} MB int32 table (best of 5)"}
+
+
+def measure_c5_scale(n: int, hbm: float, peak_kind: str) -> dict:
+    """One VFilter over n keys generated on the device in chunks, built one
+    shard group at a time; queries of 10^8 members and 10^8 disjoint keys
+    against its data array (far larger than L2)."""
     import torch
 
     import paper_2503_18397_gb300 as vf
-    from paper_2503_18397_gb300 import build as vbuild
-    from paper_2503_18397_gb300 import serve, synth
+    from paper_2503_18397_gb300 import synth
 
-    torch.cuda.set_device(0)
-    vbuild.build()
-    vf.lib()
-    out = {"metric": METRIC, "unit": "ns/key", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-           "config": {"workload": WORKLOADS["c5"][4]}}
-    # ---- scale: keys generated on the device in chunks
-    n = args.n or 5_000_000_000
     keys = torch.empty(n, dtype=torch.int64, device="cuda")
     chunk = 1 << 28
     for c0 in range(0, n, chunk):
@@ -580,7 +686,7 @@ def run_serving(args):
     p = vf.vf_params_default(kind=vf.FILTER, b=8, seed=3)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    clocks = Clocks(0)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     vf.vf_timing_read()
     vf.vf_timing_enable(True)
@@ -592,6 +698,8 @@ def run_serving(args):
     mq = min(n, 100_000_000)
     member = keys[:: max(1, n // mq)][:mq].contiguous()
     other = synth.u64_keys_torch(n, mq, 0xC5)
+    for _ in range(3):  # warm-up
+        s.query(member[: 1 << 24], stream=stream)
     ev[2].record(stream)
     o1 = s.query(member, stream=stream)
     o2 = s.query(other, stream=stream)
@@ -601,20 +709,30 @@ def run_serving(args):
     phases = vf.vf_timing_read()
     clk = clocks.stop()
     b_ms, q_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
-    out["value"] = round(b_ms * 1e6 / n, 4)
-    out["ms_per_step"] = round(b_ms + q_ms, 3)
-    out["scale"] = {"n": n, "build_ms": round(b_ms, 3), "shards": int(info.shards), "cells_per_shard": int(info.cells),
-                    "lg_seg": int(info.lg_seg), "c": info.c, "space_overhead": round(info.total_cells / n - 1, 4),
-                    "retries": int(info.retries), "peel_rounds": int(info.rounds),
-                    "query_gqps": round(2 * mq / (q_ms * 1e-3) / 1e9, 3),
-                    "members_ok": bool(o1.bool().all().item()), "fpr": float(o2.float().mean().item()),
-                    "phases": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in phases.items() if v[1]}}
-    out["gpu_launches"] = int(sum(v[1] for v in phases.values()))
-    out["clocks"] = clk
+    qps = 2 * mq / (q_ms * 1e-3)
+    res = {"workload": "one VFilter of %d uniform 64-bit keys, b=8, keys generated on the device in chunks, "
+                       "built by shard group; 1e8 members + 1e8 disjoint keys queried" % n,
+           "n": n, "value": round(b_ms * 1e6 / n, 4), "unit": "ns/key", "build_ms": round(b_ms, 3),
+           "shards": int(info.shards), "cells_per_shard": int(info.cells), "lg_seg": int(info.lg_seg), "c": info.c,
+           "data_bytes": int(info.data_bytes), "space_overhead": round(info.total_cells / n - 1, 4),
+           "retries": int(info.retries), "query_gqps": round(qps / 1e9, 3),
+           "query_roofline": random_sector_roofline(qps, 8, "filter", hbm, peak_kind),
+           "members_ok": bool(o1.bool().all().item()), "fpr": float(o2.float().mean().item()),
+           "phases": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in phases.items() if v[1]},
+           "gpu_launches": int(sum(v[1] for v in phases.values())), "clocks": clk}
     s.free()
     del keys, member, other, o1, o2
     torch.cuda.empty_cache()
-    # ---- serving: Poisson arrivals under a memory budget
+    return res
+
+
+def measure_c5_serving() -> dict:
+    """Poisson arrivals of builds and query batches under a device-memory
+    budget: continuous batching, resident structures, p50/p99 latency."""
+    import torch
+
+    from paper_2503_18397_gb300 import serve, synth
+
     rng = np.random.default_rng(0x5E)
     nb, nq = 24, 96
     sizes = synth.log_uniform_sizes(nb, 1e4, 1e8, 0x5E)
@@ -652,11 +770,49 @@ def run_serving(args):
     srv.close()
     total_b = int(sum(sizes))
     total_q = int(sum(qsizes))
-    out["serving"] = {"requests": len(reqs), "builds": serve.percentiles(recs, "build"),
-                      "queries": serve.percentiles(recs, "query"), "span_s": round(span, 3),
-                      "arrival_rate_per_s": round(rate, 2), "budget_gb": round(free * 0.25 / 2**30, 1),
-                      "build_keys": total_b, "query_keys": total_q,
-                      "throughput_keys_per_s": round((total_b + total_q) / span, 1)}
+    return {"workload": "serving: Poisson arrivals of %d builds (log-uniform 1e4..1e8 keys, b in {8,16}) and %d "
+                        "query batches (log-uniform 1e3..1e7 keys, half members) under a budget of 25%% of free "
+                        "device memory" % (nb, nq),
+            "requests": len(reqs), "builds": serve.percentiles(recs, "build"),
+            "queries": serve.percentiles(recs, "query"), "span_s": round(span, 3),
+            "arrival_rate_per_s": round(rate, 2), "budget_gb": round(free * 0.25 / 2**30, 1),
+            "build_keys": total_b, "query_keys": total_q,
+            "throughput_keys_per_s": round((total_b + total_q) / span, 1)}
+
+
+def _standalone(args, workload):
+    import torch
+
+    import paper_2503_18397_gb300 as vf
+    from paper_2503_18397_gb300 import build as vbuild
+
+    torch.cuda.set_device(0)
+    vbuild.build()
+    vf.lib()
+    return {"metric": METRIC, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[workload][4]}}
+
+
+def run_batch(args):
+    """Batched build of many uneven structures against the plain per-structure path."""
+    out = _standalone(args, "c4")
+    c4 = measure_c4(args.steps, args.warmup, args.n or 4096)
+    out.update({"value": c4["value"], "unit": "ns/key", "ms_per_step": c4["ms_per_batch"],
+                "gpu_launches": c4["gpu_launches"], "clocks": c4["clocks"], "c4": c4})
+    out["config"].update({"structures": c4["structures"], "total_keys": c4["total_keys"],
+                          "l2": "inputs larger than L2 (no flush)", "tuned": c4["tuned"]})
+    print(json.dumps(out), flush=True)
+
+
+def run_serving(args):
+    """Scale (one 5e9-key VFilter built by shard group) and serving (Poisson mix)."""
+    out = _standalone(args, "c5")
+    hbm, peak_kind = peaks()
+    sc = measure_c5_scale(args.n or 5_000_000_000, hbm, peak_kind)
+    out.update({"value": sc["value"], "unit": "ns/key", "ms_per_step": sc["build_ms"],
+                "gpu_launches": sc["gpu_launches"], "clocks": sc["clocks"], "scale": sc})
+    out["serving"] = measure_c5_serving()
     print(json.dumps(out), flush=True)
 
 
@@ -668,6 +824,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the batched (c4), scale and serving (c5) sub-measurements")
     ap.add_argument("--n", type=int, default=0, help="override the workload's key count (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -128,7 +128,16 @@ void vf_params_default(vf_params *p);
  * Scratch memory comes from the device's default stream-ordered pool; the
  * first build on a device sets that pool to keep up to min(1/8 of device
  * memory, 32 GiB) of freed memory cached for the process (release threshold).
- * Errors: VF_EINVAL, VF_ENOMEM, VF_EBUILD, VF_ETIMEOUT, VF_ECUDA, VF_ECAPACITY
+ * Repeated keys (Sec. 4.4: inside a shard, the local signature stands for
+ * the key; for 64-bit keys equal local signatures are exactly equal keys, for
+ * byte strings a collision of those 64 + h signature bits between different
+ * strings counts as a repeat): a filter keeps one copy, a function keeps one
+ * copy of each repeated (key, value) pair, and a function key given with two
+ * different values ends the build with VF_EDUP at the first attempt (no seed
+ * can solve it). vf_info.n_eff counts the keys kept; M counts every key given.
+ * Pointers may be host memory or device memory of the current device.
+ * Errors: VF_EINVAL (also: a pointer to another device's memory), VF_ENOMEM,
+ * VF_EBUILD, VF_EDUP, VF_ETIMEOUT, VF_ECUDA, VF_ECAPACITY
  * (a fuse shard above 2^27 keys; more than 2^30 keys with byte strings or in
  * the LGE regime; an LGE shard whose 2-core needs more active variables or
  * coefficient rows than the solver's per-shard pool: 4096 active variables
@@ -170,7 +179,11 @@ vf_status vf_load(const char *path, void *stream, vf_struct **out);
  * offset shard*cells with no offset array (Sec. 4), XOR of three cells; a
  * filter compares with the key's fingerprint (Sec. 3.1). For a key outside
  * the set a function returns an arbitrary but deterministic value (Problem 1).
- * Asynchronous on `stream` unless a host pointer is involved. */
+ * Asynchronous on `stream` unless a host pointer is involved. With 64-bit keys
+ * in host memory or a host output, the keys are processed in chunks of 2^23
+ * that alternate between two library-owned streams (copy in, probe, copy out
+ * per chunk), so transfers overlap the probes; `stream` is ordered before and
+ * after them, and the call returns once a host output is complete. */
 vf_status vf_query(const vf_struct *s, const void *keys, const uint64_t *offsets, uint64_t m,
                    void *out, void *stream);
 
@@ -259,10 +272,12 @@ vf_status vf_timing_read(double *ms, uint64_t *launches);
  * this entry point exists for callers that must not allocate device memory
  * during a build: code whose device memory is owned by its own pool or
  * arena, and latency-sensitive paths where a cudaMalloc/cudaFree could
- * synchronise the device or fail under memory pressure. It builds the same
- * structure vf_build builds for n <= 16384 64-bit keys with default shard
- * parameters: one shard, lazy-Gaussian-elimination regime (params->mode and
- * the LGE sizes are ignored), same hash, seed, retries and geometry.
+ * synchronise the device or fail under memory pressure. It builds one shard
+ * in the lazy-Gaussian-elimination regime (params->mode and the LGE sizes are
+ * ignored): the same hash, seed, retries and geometry as vf_build in mode
+ * VF_MODE_AUTO or VF_MODE_LGE with lge_target and lge_max_shard of at least
+ * n (the defaults for n <= 16384), which also build one LGE shard. The
+ * fail_attempts hook of vf_debug_faults applies to it as to vf_build.
  *  keys    device uint64_t[n]; values: device array of the value type of b
  *          (function) or NULL (filter); data: device buffer of at least
  *          data_capacity >= vf_info.data_bytes bytes (get it from vf_plan with
@@ -274,15 +289,18 @@ vf_status vf_timing_read(double *ms, uint64_t *launches);
  *  address; make it before any stream capture. All calls share the array,
  *  so calls that overlap on the GPU (other streams, other host threads) race
  *  and must be serialised by the caller. Waits for completion.
- *  Errors: VF_ECAPACITY (n > 16384), VF_EINVAL (host pointers, data buffer too
- *  small, byte-string keys, bad b/kind), VF_EBUILD, VF_ECUDA. */
+ *  A launch error left pending by the caller's earlier work is cleared on entry.
+ *  Errors: VF_ECAPACITY (n > 16384), VF_EINVAL (host pointers or another
+ *  device's memory, data buffer too small, byte-string keys, bad b/kind),
+ *  VF_EBUILD, VF_EDUP (a key given with two values), VF_ECUDA. */
 vf_status vf_build_static(const uint64_t *keys, const void *values, uint64_t n, const vf_params *params,
                           void *data, uint64_t data_capacity, vf_info *info, void *stream);
 
 /* Fault injection for tests of the failure paths (the paper has no
  * counterpart; its failure model is a failed attempt retried with the next
  * seed, Sec. 4). Process-wide, off by default (0, 0, 0); not for production.
- *   fail_attempts: the first fail_attempts attempts of every vf_build report
+ *   fail_attempts: the first fail_attempts attempts of every vf_build (and
+ *     vf_build_static) report
  *     failure after solving, so the build retries with seed+1, seed+2, ... as
  *     it does after a 2-core or an unsolvable system (VF_EBUILD once
  *     max_retries is exceeded).

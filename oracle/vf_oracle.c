@@ -579,6 +579,45 @@ static void *solve_worker(void *arg) {
     return NULL;
 }
 
+/* De-duplication of every shard, shards taken in turn by a pool of threads. */
+typedef struct {
+    int kind, b;
+    uint64_t shards;
+    const uint64_t *start, *cnt;
+    uint64_t *loc, *val, *meff;
+    pthread_mutex_t mu;
+    uint64_t next;
+    int conflict;
+} dedup_ctx;
+
+static void *dedup_worker(void *arg) {
+    dedup_ctx *c = arg;
+    for (;;) {
+        pthread_mutex_lock(&c->mu);
+        uint64_t s = c->next++;
+        pthread_mutex_unlock(&c->mu);
+        if (s >= c->shards) break;
+        int conflict = 0;
+        c->meff[s] = dedup_shard(c->kind, c->b, c->cnt[s], c->loc + c->start[s], c->val + c->start[s], &conflict);
+        if (conflict) {
+            pthread_mutex_lock(&c->mu);
+            c->conflict = 1;
+            pthread_mutex_unlock(&c->mu);
+        }
+    }
+    return NULL;
+}
+
+/* Runs fn(ctx) on t threads sharing one context (the calling thread is one of them). */
+static void run_shared(int t, void *(*fn)(void *), void *ctx) {
+    pthread_t th[256];
+    int started[256] = {0};
+    for (int k = 1; k < t; k++) started[k] = pthread_create(&th[k], NULL, fn, ctx) == 0;
+    fn(ctx);
+    for (int k = 1; k < t; k++)
+        if (started[k]) pthread_join(th[k], NULL);
+}
+
 /* Signatures of keys [i0, i1). */
 typedef struct {
     const orc_params *p;
@@ -682,11 +721,24 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
         /* Duplicates of every shard first, then the shards' systems. */
         uint64_t *meff = malloc(in.shards * sizeof(uint64_t));
         int conflict = 0;
-        in.n_eff = 0;
-        for (uint64_t s = 0; s < in.shards; s++) {
-            meff[s] = dedup_shard(p->kind, p->b, cnt[s], loc + start[s], val + start[s], &conflict);
-            in.n_eff += meff[s];
+        {
+            dedup_ctx dc;
+            memset(&dc, 0, sizeof dc);
+            dc.kind = p->kind;
+            dc.b = p->b;
+            dc.shards = in.shards;
+            dc.start = start;
+            dc.cnt = cnt;
+            dc.loc = loc;
+            dc.val = val;
+            dc.meff = meff;
+            pthread_mutex_init(&dc.mu, NULL);
+            run_shared(nt, dedup_worker, &dc);
+            pthread_mutex_destroy(&dc.mu);
+            conflict = dc.conflict;
         }
+        in.n_eff = 0;
+        for (uint64_t s = 0; s < in.shards; s++) in.n_eff += meff[s];
         uint8_t *data = NULL;
         int ok = 0;
         if (!conflict) {
@@ -702,16 +754,7 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
             pthread_mutex_init(&c.mu, NULL);
             pthread_mutex_init(&c.cell_mu, NULL);
             c.use_cell_mu = nt > 1 && !(p->b == 8 || p->b == 16 || p->b == 32 || p->b == 64);
-            if (nt == 1) {
-                solve_worker(&c);
-            } else {
-                pthread_t th[256];
-                int started[256] = {0};
-                for (int k = 1; k < nt; k++) started[k] = pthread_create(&th[k], NULL, solve_worker, &c) == 0;
-                solve_worker(&c);
-                for (int k = 1; k < nt; k++)
-                    if (started[k]) pthread_join(th[k], NULL);
-            }
+            run_shared(nt, solve_worker, &c);
             pthread_mutex_destroy(&c.mu);
             pthread_mutex_destroy(&c.cell_mu);
             ok = !c.failed;

@@ -328,6 +328,13 @@ def vf_plan(n: int, M: int, params: VfParams | None = None) -> VfInfo:
     return info
 
 
+def vf_data(s: Structure):
+    """(device address, bytes) of a structure's data array (owned by the structure)."""
+    ptr, nb = C.c_void_p(), C.c_uint64()
+    _check(lib().vf_data(s.handle, C.byref(ptr), C.byref(nb)))
+    return ptr.value or 0, nb.value
+
+
 def vf_export(s: Structure) -> np.ndarray:
     info = vf_get_info(s)
     buf = np.zeros(max(int(info.data_bytes), 1), dtype=np.uint8)

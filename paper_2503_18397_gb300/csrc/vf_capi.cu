@@ -91,15 +91,7 @@ void keep_pool_warm(int dev) {
     if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess) cudaGetLastError();
 }
 
-bool on_device(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool on_device(const void* p) { return vf::mem_where(p) == vf::MemWhere::kHere; }
 
 // ------------------------------------------------------------------ timing
 
@@ -476,11 +468,13 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
 }
 
 // One attempt of the fuse-regime solver: the asynchronous solver (default) or
-// the round-synchronous one. Reorders loc / val within each shard. A filter
-// whose peel fails is checked for duplicate local signatures among the unpeeled
-// edges (identical edges never peel); if there are any, one copy of each is
-// kept and the same attempt is solved again without the others (Sec. 4.5),
-// which *dropped reports.
+// the round-synchronous one. Reorders loc / val within each shard. A build
+// whose peel fails is checked for duplicate local signatures among the
+// unpeeled edges (identical edges never peel; Sec. 4.4: the local signature
+// stands for the key in its shard). A function key given with two values ends
+// the build with VF_EDUP (no seed can solve it); otherwise, if there are
+// duplicates, one copy of each is kept and the same attempt is solved again
+// without the others (Sec. 4.5), which *dropped reports.
 vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32_t* val,
                      const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
                      uint64_t* rounds_out, int solver, uint64_t* dropped, uint64_t cell_base = 0) {
@@ -496,7 +490,7 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32
     uint64_t ndrop = 0;
     for (int pass = 0;; pass++) {
         DevBuf claimed;
-        const bool dedup = g.kind == VF_FILTER && pass == 0;
+        const bool dedup = pass == 0;
         vf_status rs;
         if (solver == VF_SOLVER_FLOW) {
             *rounds_out = 0;
@@ -507,7 +501,7 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32
                               drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
         }
         if (rs != VF_EBUILD || !claimed.p) return rs;
-        // unpeeled edges of a failed filter attempt: any duplicates?
+        // unpeeled edges of a failed attempt: any duplicates?
         const uint64_t unpeeled = n - *peeled;
         uint64_t cap = 1024;
         while (cap < 2 * unpeeled) cap <<= 1;
@@ -517,13 +511,16 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32
         VF_CK(cudaMemsetAsync(table.p, 0, cap * 8, st));
         VF_CK(drop.alloc(words * 4, st));
         VF_CK(cudaMemsetAsync(drop.p, 0, words * 4, st));
-        VF_CK(cnt.alloc(8, st));
-        VF_CK(cudaMemsetAsync(cnt.p, 0, 8, st));
-        VF_CK(vf::launch_find_dups(loc, n, start, uint32_t(in.shards), claimed.as<uint32_t>(),
+        VF_CK(cnt.alloc(16, st));
+        VF_CK(cudaMemsetAsync(cnt.p, 0, 16, st));
+        VF_CK(vf::launch_find_dups(loc, val, n, start, uint32_t(in.shards), claimed.as<uint32_t>(),
                                    table.as<unsigned long long>(), cap, drop.as<uint32_t>(),
-                                   cnt.as<unsigned long long>(), nullptr, st));
-        VF_CK(cudaMemcpyAsync(&ndrop, cnt.p, 8, cudaMemcpyDeviceToHost, st));
+                                   cnt.as<unsigned long long>(), nullptr, cnt.as<unsigned long long>() + 1, st));
+        uint64_t c2[2] = {0, 0};
+        VF_CK(cudaMemcpyAsync(c2, cnt.p, 16, cudaMemcpyDeviceToHost, st));
         VF_CK(cudaStreamSynchronize(st));
+        ndrop = c2[0];
+        if (c2[1]) return fail(VF_EDUP, "a key was given twice with different values");
         if (ndrop == 0) return VF_EBUILD;  // a genuine 2-core
         *dropped = ndrop;
     }
@@ -614,6 +611,7 @@ vf_status solve_lge(const vf_info& in, const std::vector<unsigned long long>& st
     uint32_t err = 0;
     vf_status rs = run_lge_tasks(tasks, true, loc, val, nullptr, st, peeled, core, &err, dups);
     if (rs != VF_OK) return rs;
+    if (err & vf::kErrDupKey) return fail(VF_EDUP, "a key was given twice with different values");
     // A capacity failure is this solver's limit, not a property of the system:
     // it ends the build (a retry would give another seed than the method's).
     if (err & vf::kErrCapacity) return fail(VF_ECAPACITY, "LGE shard exceeds the per-CTA solver capacity");
@@ -856,6 +854,11 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     }
     VF_CK(cudaStreamSynchronize(st));
     for (uint32_t j = 0; j < P; j++) {
+        if (fail_bits[j] & vf::kErrDupKey) {
+            free_data();
+            return fail(VF_EDUP, "vf_build_batch: structure " + std::to_string(pending[j]) +
+                                     " has a key given twice with different values");
+        }
         if (fail_bits[j] & (vf::kErrCapacity | vf::kErrLgeSize)) {
             free_data();
             return fail(VF_ECAPACITY, "batched LGE shard exceeds the solver capacity");
@@ -1046,6 +1049,11 @@ vf_status build_impl(const void* keys, const uint64_t* offsets, const void* valu
     if (!(p.eps > 0.0) || !(p.eta > 0.0 && p.eta < 1.0) || p.max_retries < 0 || p.lge_target == 0 ||
         p.lge_max_shard < 2 || p.mode < VF_MODE_AUTO || p.mode > VF_MODE_MWHC)
         return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes / mode");
+    for (const auto& pw : {std::make_pair(keys, "keys"), std::make_pair(static_cast<const void*>(offsets), "offsets"),
+                           std::make_pair(values, "values")}) {
+        const vf_status cs = vf::check_here(pw.first, pw.second);
+        if (cs != VF_OK) return cs;
+    }
     // More than 2^30 keys: only 64-bit keys in the fuse or MWHC regime, built
     // one shard group (<= 2^30 keys) at a time.
     const bool big = n > (uint64_t(1) << 30);
@@ -1237,6 +1245,8 @@ vf_status build_wide(const void* keys, const uint64_t* offsets, const void* valu
                      void* stream, vf_struct** out) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int b = p.b, hb = b - 32;
+    vf_status cs = vf::check_here(values, "values");
+    if (cs != VF_OK) return cs;
     DevBuf v64, vlo, vhi;
     if (p.kind == VF_FUNC && n > 0) {
         const uint64_t* vdev = static_cast<const uint64_t*>(values);
@@ -1309,6 +1319,30 @@ vf_status build_wide(const void* keys, const uint64_t* offsets, const void* valu
 
 vf::Geom vf::geom_of(const vf_info& in) { return make_geom(in); }
 
+vf::MemWhere vf::mem_where(const void* p) {
+    if (!p) return MemWhere::kHost;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return MemWhere::kHost;
+    }
+    if (a.type == cudaMemoryTypeManaged) return MemWhere::kHere;
+    if (a.type != cudaMemoryTypeDevice) return MemWhere::kHost;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return MemWhere::kElsewhere;
+    }
+    return a.device == cur ? MemWhere::kHere : MemWhere::kElsewhere;
+}
+
+vf_status vf::check_here(const void* p, const char* what) {
+    if (mem_where(p) != MemWhere::kElsewhere) return VF_OK;
+    return fail(VF_EINVAL, std::string(what) + " is device memory of another device than the current one");
+}
+
+int vf::debug_fail_attempts() { return g_debug_fail_attempts.load(); }
+
 void vf::set_last_error(const char* msg) { g_last_error = msg; }
 
 extern "C" {
@@ -1369,18 +1403,100 @@ vf_status vf_build_resumable(const void* keys, const uint64_t* offsets, const vo
     return build_impl(keys, offsets, values, n, params, stream, out, &ro);
 }
 
+// Two non-blocking streams per host thread and device for pipelined queries.
+bool pipe_streams(cudaStream_t out[2]) {
+    thread_local std::map<int, std::pair<cudaStream_t, cudaStream_t>> streams;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    auto it = streams.find(dev);
+    if (it == streams.end()) {
+        cudaStream_t a = nullptr, b = nullptr;
+        if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) != cudaSuccess) return false;
+        if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaStreamDestroy(a);
+            return false;
+        }
+        it = streams.emplace(dev, std::make_pair(a, b)).first;
+    }
+    out[0] = it->second.first;
+    out[1] = it->second.second;
+    return true;
+}
+
+// Keys per chunk of a pipelined query (64 MB of 64-bit keys).
+constexpr uint64_t kPipeChunk = uint64_t(1) << 23;
+
+// Queries of 64-bit keys of which the keys or the outputs (or both) are host
+// memory: chunks of kPipeChunk keys alternate between two streams, each chunk
+// copied in (one cudaMemcpyAsync), probed, and copied out on its stream, so
+// the host-to-device copy of one chunk overlaps the probe of the previous one
+// and the device-to-host copy of the one before. Each stream reuses its own
+// staging slot, so stream order alone keeps a slot from being overwritten
+// while in use. Ordered after earlier work on `st`; `st` waits for both.
+vf_status query_pipelined(const vf_struct* s, const uint64_t* keys, bool keys_dev, uint64_t m, void* out,
+                          bool out_dev, size_t ob, cudaStream_t st) {
+    cudaStream_t q[2];
+    if (!pipe_streams(q)) return fail(VF_ECUDA, "vf_query: could not create the pipeline streams");
+    const uint64_t chunk = std::min(m, kPipeChunk);
+    DevBuf kb, obuf;
+    if (!keys_dev) VF_CK(kb.alloc(2 * chunk * 8, st));
+    if (!out_dev) VF_CK(obuf.alloc(2 * chunk * ob, st));
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (auto& e : ev) VF_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    auto destroy = [&]() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    cudaError_t e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q[0], ev[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q[1], ev[0], 0);
+    const uint64_t nchunks = (m + chunk - 1) / chunk;
+    {
+        PhaseTimer t(kPhQuery, st, int(nchunks));
+        for (uint64_t c = 0; c < nchunks && e == cudaSuccess; c++) {
+            const uint64_t i0 = c * chunk, len = std::min(chunk, m - i0);
+            const int j = int(c & 1);
+            const uint64_t* kd = keys_dev ? keys + i0 : kb.as<uint64_t>() + uint64_t(j) * chunk;
+            if (!keys_dev) e = cudaMemcpyAsync(const_cast<uint64_t*>(kd), keys + i0, len * 8, cudaMemcpyHostToDevice, q[j]);
+            uint8_t* od = out_dev ? static_cast<uint8_t*>(out) + i0 * ob : obuf.as<uint8_t>() + uint64_t(j) * chunk * ob;
+            if (e == cudaSuccess) e = vf::launch_query(VF_KEYS_U64, kd, nullptr, len, s->geom, s->data, od, q[j]);
+            if (e == cudaSuccess && !out_dev)
+                e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + i0 * ob, od, len * ob, cudaMemcpyDeviceToHost, q[j]);
+        }
+        // `st` (and with it the staging buffers' release) waits for both streams
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], q[0]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], q[1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[2], 0);
+    }
+    if (e == cudaSuccess && !out_dev) e = cudaStreamSynchronize(st);
+    destroy();
+    if (e != cudaSuccess) return fail(VF_ECUDA, std::string("vf_query (pipelined): ") + cudaGetErrorString(e));
+    return VF_OK;
+}
+
 vf_status vf_query(const vf_struct* s, const void* keys, const uint64_t* offsets, uint64_t m, void* out,
                    void* stream) {
     if (!s) return fail(VF_EINVAL, "vf_query: NULL structure");
     if (m == 0) return VF_OK;
     if (!keys || !out) return fail(VF_EINVAL, "vf_query: NULL keys or out");
     const int key_kind = offsets ? VF_KEYS_BYTES : VF_KEYS_U64;
+    for (const auto& pw : {std::make_pair(keys, "keys"), std::make_pair(static_cast<const void*>(offsets), "offsets"),
+                           std::make_pair(static_cast<const void*>(out), "out")}) {
+        const vf_status cs = vf::check_here(pw.first, pw.second);
+        if (cs != VF_OK) return cs;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t ob = s->info.kind == VF_FILTER ? 1 : value_bytes(s->info.b);
+    const bool out_dev = on_device(out);
+    if (key_kind == VF_KEYS_U64) {
+        const bool keys_dev = on_device(keys);
+        if (!keys_dev || !out_dev)
+            return query_pipelined(s, static_cast<const uint64_t*>(keys), keys_dev, m, out, out_dev, ob, st);
+    }
     Staged in_keys;
     vf_status rs = stage_keys(key_kind, keys, offsets, m, st, in_keys);
     if (rs != VF_OK) return rs;
-    const size_t ob = s->info.kind == VF_FILTER ? 1 : value_bytes(s->info.b);
-    const bool out_dev = on_device(out);
     DevBuf obuf;
     void* dout = out;
     if (!out_dev) {
@@ -1409,7 +1525,7 @@ vf_status vf_query_batch(const vf_query_req* reqs, uint32_t count, void* stream)
         if (!r.s) return fail(VF_EINVAL, "vf_query_batch: NULL structure");
         if (r.m == 0) continue;
         if (!on_device(r.keys) || !on_device(r.out))
-            return fail(VF_EINVAL, "vf_query_batch: keys and outputs must be device memory");
+            return fail(VF_EINVAL, "vf_query_batch: keys and outputs must be device memory of the current device");
         vf::QueryReq q;
         std::memset(&q, 0, sizeof q);
         q.g = r.s->geom;
@@ -1456,6 +1572,11 @@ vf_status vf_signatures(int key_kind, const void* keys, const uint64_t* offsets,
     if (n == 0) return VF_OK;
     if (!keys || !out || (key_kind == VF_KEYS_BYTES && !offsets)) return fail(VF_EINVAL, "vf_signatures: NULL");
     if (key_kind != VF_KEYS_U64 && key_kind != VF_KEYS_BYTES) return fail(VF_EINVAL, "bad key_kind");
+    for (const auto& pw : {std::make_pair(keys, "keys"), std::make_pair(static_cast<const void*>(offsets), "offsets"),
+                           std::make_pair(static_cast<const void*>(out), "out")}) {
+        const vf_status cs = vf::check_here(pw.first, pw.second);
+        if (cs != VF_OK) return cs;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Staged in_keys;
     vf_status rs = stage_keys(key_kind, keys, offsets, n, st, in_keys);
@@ -1533,6 +1654,9 @@ vf_status vf_build_batch(const vf_batch_item* items, uint32_t count, const vf_pa
         if (it.n > 0 && !it.keys) return fail(VF_EINVAL, "vf_build_batch: keys is NULL");
         if (it.kind == VF_FUNC && it.n > 0 && !it.values) return fail(VF_EINVAL, "vf_build_batch: a function needs values");
         if (it.n >= (uint64_t(1) << 32)) return fail(VF_ECAPACITY, "vf_build_batch: at most 2^32-1 keys per structure");
+        vf_status cs = vf::check_here(it.keys, "vf_build_batch: keys");
+        if (cs == VF_OK) cs = vf::check_here(it.values, "vf_build_batch: values");
+        if (cs != VF_OK) return cs;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;

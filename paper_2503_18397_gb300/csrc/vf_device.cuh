@@ -28,6 +28,7 @@ constexpr uint32_t kErrCapacity = 1u << 3;      // shard larger than the solver 
 constexpr uint32_t kErrUnsolvable = 1u << 4;    // a shard's system has no solution
 constexpr uint32_t kErrLgeSize = 1u << 5;       // LGE shard beyond the solver: active variables or coefficient rows
 constexpr uint32_t kErrLevel = 1u << 6;         // asynchronous peel: too many levels (use the round solver)
+constexpr uint32_t kErrDupKey = 1u << 7;        // a function was given one key with two different values
 
 // Stafford Mix13, the SplitMix64 output function.
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {

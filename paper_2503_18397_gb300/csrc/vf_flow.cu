@@ -493,19 +493,23 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_order(uint64_t* __restric
 
 // ------------------------------------------------- filter de-duplication
 
-// Duplicate local signatures within a shard (a filter given repeated keys, or
-// a 64-bit collision) are identical edges, which never peel: a filter build
-// with duplicates always leaves them unpeeled. After a failed peel the
-// unpeeled edges are inserted into an open-addressing table keyed by (shard,
-// local signature); every edge that finds its key already present is marked in
-// `drop` (one copy of each group survives, Sec. 4.5) and counted, in total and
-// per shard. Without `claimed` every edge is inserted (duplicate count only).
-__global__ void __launch_bounds__(kFT) k_find_dups(const uint64_t* __restrict__ loc, uint64_t n,
-                                                   const unsigned long long* __restrict__ start, uint32_t S,
-                                                   const uint32_t* __restrict__ claimed,
+// Duplicate local signatures within a shard (a key given twice, Sec. 4.4)
+// are identical edges, which never peel: a build with duplicates always leaves
+// them unpeeled. After a failed peel the unpeeled edges are inserted into an
+// open-addressing table keyed by (shard, local signature); every edge that
+// finds its key already present is marked in `drop` (one copy of each group
+// survives, Sec. 4.5) and counted, in total and per shard. With `val` (a
+// function) a copy whose value differs from the copy already in the table is
+// counted in *nconflict instead: if any copy differs from the first one, that
+// copy does, so every key given two values is found. Without `claimed` every
+// edge is inserted (duplicate count only).
+__global__ void __launch_bounds__(kFT) k_find_dups(const uint64_t* __restrict__ loc, const uint32_t* __restrict__ val,
+                                                   uint64_t n, const unsigned long long* __restrict__ start,
+                                                   uint32_t S, const uint32_t* __restrict__ claimed,
                                                    unsigned long long* __restrict__ table, uint64_t cap,
                                                    uint32_t* __restrict__ drop, unsigned long long* ndrop,
-                                                   unsigned long long* __restrict__ per_shard) {
+                                                   unsigned long long* __restrict__ per_shard,
+                                                   unsigned long long* nconflict) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t e = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; e < n; e += stride) {
         if (claimed && ((__ldg(claimed + (e >> 5)) >> (e & 31u)) & 1u)) continue;
@@ -517,6 +521,10 @@ __global__ void __launch_bounds__(kFT) k_find_dups(const uint64_t* __restrict__ 
             if (prev == 0) break;  // first copy
             const uint64_t o = prev - 1;
             if (__ldg(loc + o) == local && flow_shard_of_edge(start, S, o) == s) {
+                if (val && __ldg(val + o) != __ldg(val + e)) {
+                    atomicAdd(nconflict, 1ull);
+                    break;
+                }
                 if (drop) atomicOr(drop + (e >> 5), 1u << (e & 31u));
                 atomicAdd(ndrop, 1ull);
                 if (per_shard) atomicAdd(per_shard + s, 1ull);
@@ -623,11 +631,13 @@ cudaError_t launch_tile_order(uint64_t* loc, uint32_t* val, uint64_t n, const un
     return cudaGetLastError();
 }
 
-cudaError_t launch_find_dups(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
-                             const uint32_t* claimed, unsigned long long* table, uint64_t cap, uint32_t* drop,
-                             unsigned long long* ndrop, unsigned long long* per_shard, cudaStream_t st) {
+cudaError_t launch_find_dups(const uint64_t* loc, const uint32_t* val, uint64_t n, const unsigned long long* start,
+                             uint32_t S, const uint32_t* claimed, unsigned long long* table, uint64_t cap,
+                             uint32_t* drop, unsigned long long* ndrop, unsigned long long* per_shard,
+                             unsigned long long* nconflict, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    k_find_dups<<<grid_for(n), kFT, 0, st>>>(loc, n, start, S, claimed, table, cap, drop, ndrop, per_shard);
+    k_find_dups<<<grid_for(n), kFT, 0, st>>>(loc, val, n, start, S, claimed, table, cap, drop, ndrop, per_shard,
+                                             nconflict);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,16 @@ cudaError_t device_to_file(std::FILE* f, uint64_t off, const uint8_t* dev, uint6
 
 int num_sms();
 
+// Where a caller's pointer lives: host memory (or unknown to CUDA), device or
+// managed memory the current device can use, or device memory of another
+// device (which the kernels here cannot read without peer access).
+enum class MemWhere { kHost, kHere, kElsewhere };
+MemWhere mem_where(const void* p);
+// VF_EINVAL (with a message naming `what`) if p is device memory of another device.
+vf_status check_here(const void* p, const char* what);
+// Failure-injection hook of vf_debug_faults: attempts below this count fail.
+int debug_fail_attempts();
+
 // Message returned by vf_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
@@ -129,10 +139,12 @@ cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned l
 // Marks in `drop` (if given) every edge not set in `claimed` (if given) whose
 // (shard, local signature) an earlier such edge already has; table: cap (a
 // power of two, >= 2x the edges inserted) zeroed words; *ndrop counts the
-// marks, per_shard[s] (if given) those of shard s.
-cudaError_t launch_find_dups(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
-                             const uint32_t* claimed, unsigned long long* table, uint64_t cap, uint32_t* drop,
-                             unsigned long long* ndrop, unsigned long long* per_shard, cudaStream_t st);
+// marks, per_shard[s] (if given) those of shard s. With `val` (functions),
+// copies whose values differ are counted in *nconflict and not marked.
+cudaError_t launch_find_dups(const uint64_t* loc, const uint32_t* val, uint64_t n, const unsigned long long* start,
+                             uint32_t S, const uint32_t* claimed, unsigned long long* table, uint64_t cap,
+                             uint32_t* drop, unsigned long long* ndrop, unsigned long long* per_shard,
+                             unsigned long long* nconflict, cudaStream_t st);
 // Peels the shards in batches whose waves fit in L2 (flow_batches launches
 // of initial items + worklist peel), then counts the peeled edges.
 cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st);

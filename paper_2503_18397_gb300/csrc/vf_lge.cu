@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
     uint32_t* dense = scr + o.dense;
     uint32_t* lc = scr + o.lc;
     uint32_t* L = scr + o.L;
-    constexpr uint32_t kBad = kErrUnsolvable | kErrCapacity | kErrLgeSize | kErrDegOverflow;
+    constexpr uint32_t kBad = kErrUnsolvable | kErrCapacity | kErrLgeSize | kErrDegOverflow | kErrDupKey;
 
     // The large configuration behind a small one takes its tasks from the
     // spill list (written by the previous launch), otherwise from all tasks.
@@ -325,25 +325,41 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 inc_list[atomicAdd(&inc_cur[ev[2]], 1u)] = j;
             }
             __syncthreads();
-            // Filters drop duplicate local signatures (Sec. 4.5). Identical edges never
-            // peel, so every duplicate is in the core, next to its copies in the
-            // incidence list of its first vertex; the copy of smallest index stays.
-            if (task.kind == 1) {
-                for (uint32_t j = tid; j < C; j += T) {
-                    const uint32_t e = __ldcg(&core[j]);
-                    const uint64_t x = __ldg(a.loc + e0 + e);
-                    const uint32_t v = __ldcg(&cev[3 * e]);
-                    const uint32_t q1 = __ldcg(&inc_off[v + 1]);
-                    for (uint32_t q = __ldcg(&inc_off[v]); q < q1; q++) {
-                        const uint32_t e2 = __ldcg(&core[__ldcg(&inc_list[q])]);
-                        if (e2 < e && __ldg(a.loc + e0 + e2) == x) {
+            // Duplicate keys (Sec. 4.4-4.5): equal local signatures in a shard are
+            // the same key. Identical edges never peel, so every duplicate is in
+            // the core, next to its copies in the incidence list of its first
+            // vertex; the copy of smallest index stays. A filter's copies carry
+            // the same fingerprint, a function's copies are dropped when their
+            // values agree; a key with two values has no solution at any seed
+            // and ends the build (kErrDupKey). A copy that differs from the first
+            // copy differs from the earlier copy it meets, so one comparison each
+            // finds every conflict.
+            for (uint32_t j = tid; j < C; j += T) {
+                const uint32_t e = __ldcg(&core[j]);
+                const uint64_t x = __ldg(a.loc + e0 + e);
+                const uint32_t v = __ldcg(&cev[3 * e]);
+                const uint32_t q1 = __ldcg(&inc_off[v + 1]);
+                for (uint32_t q = __ldcg(&inc_off[v]); q < q1; q++) {
+                    const uint32_t e2 = __ldcg(&core[__ldcg(&inc_list[q])]);
+                    if (e2 < e && __ldg(a.loc + e0 + e2) == x) {
+                        if (task.kind == 0 && __ldg(a.val + e0 + e2) != __ldg(a.val + e0 + e)) {
+                            s_fail = 3;
+                        } else {
                             est[j] |= 4u;  // done: no equation of its own
                             atomicAdd(&s_dup, 1u);
-                            break;
                         }
+                        break;
                     }
                 }
+            }
+            __syncthreads();
+            if (s_fail == 3) {
+                if (tid == 0) {
+                    atomicOr(a.err, kErrDupKey);
+                    atomicOr(a.item_fail + task.item, kErrDupKey);
+                }
                 __syncthreads();
+                continue;
             }
             // The incidence offsets (at most 3C) go to shared memory as 16-bit
             // entries after the states when they fit: the elimination rounds then

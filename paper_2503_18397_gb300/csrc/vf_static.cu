@@ -36,15 +36,8 @@ vf_status fail_static(vf_status st, const char* msg) {
     return st;
 }
 
-bool is_device_pointer(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// Device (or managed) memory the current device can use.
+bool is_device_pointer(const void* p) { return mem_where(p) == MemWhere::kHere; }
 
 // Device address of g_static_scratch on the current device. In host code the
 // array's name is only a stand-in, so the address comes from
@@ -96,10 +89,12 @@ extern "C" vf_status vf_build_static(const uint64_t* keys, const void* values, u
     if (p.key_kind != VF_KEYS_U64) return fail_static(VF_EINVAL, "vf_build_static: 64-bit integer keys only");
     if (p.b < 1 || p.b > 32 || (p.kind != VF_FUNC && p.kind != VF_FILTER) || p.max_retries < 0)
         return fail_static(VF_EINVAL, "vf_build_static: bad b, kind or max_retries");
-    if (n > 0 && !is_device_pointer(keys)) return fail_static(VF_EINVAL, "vf_build_static: keys must be device memory");
+    if (n > 0 && !is_device_pointer(keys))
+        return fail_static(VF_EINVAL, "vf_build_static: keys must be device memory of the current device");
     if (p.kind == VF_FUNC && n > 0 && !is_device_pointer(values))
-        return fail_static(VF_EINVAL, "vf_build_static: values must be device memory");
-    if (!is_device_pointer(data)) return fail_static(VF_EINVAL, "vf_build_static: data must be device memory");
+        return fail_static(VF_EINVAL, "vf_build_static: values must be device memory of the current device");
+    if (!is_device_pointer(data))
+        return fail_static(VF_EINVAL, "vf_build_static: data must be device memory of the current device");
     // one shard in the LGE regime
     p.mode = VF_MODE_LGE;
     p.lge_target = kStaticMaxKeys;
@@ -113,6 +108,9 @@ extern "C" vf_status vf_build_static(const uint64_t* keys, const void* values, u
     uint32_t* base = nullptr;
     rs = static_scratch(&base);
     if (rs != VF_OK) return rs;
+    // A launch error left over from the caller's own work would otherwise be
+    // reported as this call's failure: drop it before the first launch.
+    (void)cudaGetLastError();
     uint32_t* misc = base;
     unsigned long long* start = reinterpret_cast<unsigned long long*>(base + kMiscWords);
     LgeTask* tasks_dev = reinterpret_cast<LgeTask*>(base + kMiscWords + kStartWords);
@@ -170,8 +168,10 @@ extern "C" vf_status vf_build_static(const uint64_t* keys, const void* values, u
         if (cudaMemcpyAsync(h, misc, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return fail_static(VF_ECUDA, "vf_build_static: reading the outcome failed");
+        if (h[0] & kErrDupKey) return fail_static(VF_EDUP, "vf_build_static: a key was given twice with different values");
         if (h[0] & (kErrCapacity | kErrLgeSize)) return fail_static(VF_ECAPACITY, "vf_build_static: shard exceeds the solver");
         if (h[0] & (kErrUnsolvable | kErrDegOverflow)) continue;
+        if (attempt < debug_fail_attempts()) continue;  // test hook of vf_debug_faults, as in vf_build
         in.peeled = h[4];
         in.core = h[5];
         in.rounds = 0;

@@ -152,3 +152,38 @@ def test_batch_filter_duplicate_keys(vf, orc):
         assert (info.seed, info.retries) == (oi.seed, oi.retries)
         assert _host(s.query(_dev(allk))).all()
         s.free()
+
+
+def test_batch_function_duplicates(vf, orc):
+    # functions with repeated (key, value) pairs inside a batch keep one copy
+    # (LGE solver and, above the threshold, the fuse solver); a key given with
+    # two values makes the whole batch call return VF_EDUP
+    rng = np.random.default_rng(32)
+    items, host = [], []
+    for i, n in enumerate([2000, 30_000, 900_000]):
+        keys = synth.u64_keys(i * 10_000_000, n, 32)
+        vals = synth.values(n, 16, 32 + i)
+        rep = rng.choice(n, size=n // 50, replace=False)
+        idx = np.concatenate([np.arange(n), rep])
+        idx = idx[rng.permutation(len(idx))]
+        items.append((_dev(keys[idx]), _dev(vals[idx]), 0, 16, 600 + i))
+        host.append((keys[idx], vals[idx], n))
+    structs = vf.vf_build_batch(items)
+    for s, (k, v, n) in zip(structs, host):
+        info = s.info
+        st, oi, _ = orc.build(orc.default_params(kind=orc.FUNC, b=16, seed=info.seed - info.retries), k, v)
+        assert st == orc.OK
+        assert info.n_eff == oi.n_eff == n
+        assert (info.seed, info.retries) == (oi.seed, oi.retries)
+        assert (_host(s.query(_dev(k))) == v).all()
+        s.free()
+    for j in (0, 2):  # a conflicting key in an LGE structure, then in a fuse one
+        bad = list(items)
+        k, v, n = host[j]
+        v2 = v.copy()
+        k2 = np.concatenate([k, k[:1]])
+        v2 = np.concatenate([v2, (v2[:1] ^ 3).astype(v2.dtype)])
+        bad[j] = (_dev(k2), _dev(v2), 0, 16, 600 + j)
+        with pytest.raises(vf.VFError) as e:
+            vf.vf_build_batch(bad)
+        assert e.value.status == 4, str(e.value)

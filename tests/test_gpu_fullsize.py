@@ -1,7 +1,8 @@
 """Full-size builds of the benchmark's workloads, in its parameters and seeds.
 
-The 2^20-key VFunc is compared with a complete oracle build. The larger ones
-are checked on sampled outputs: every (sampled) member is accepted or decodes
+The 2^20-key VFunc and the 10^8-key VFilter (the benchmark's headline
+workload) are compared with complete oracle builds and every query. The
+larger ones are checked on sampled outputs: every (sampled) member is accepted or decodes
 to its value, the false-positive rate is 2^-b within 5 sigma, the oracle's
 query on the GPU-built data array equals the GPU query for sampled members and
 non-members, the plan equals the oracle's, and (LGE regime) sampled shards'
@@ -61,14 +62,47 @@ def _check_sampled(vf, orc, s, keys, n, seed, b):
     assert (gq == oq).all()
 
 
-def test_vfilter_1e8_sampled(vf, orc):
+GEOMETRY = ("regime", "h", "h_bb", "h_dup", "shards", "M", "c", "lg_seg", "seg", "l", "T", "cells", "total_cells",
+            "data_bytes", "seed", "retries", "n_eff")
+
+
+def test_vfilter_1e8_complete(vf, orc):
+    # The benchmark's headline workload exactly: 10^8 keys from its generator
+    # and seed, b = 8, the seed of its first step. A complete oracle build
+    # (shards on a pool of host threads) gives the plan, largest shard,
+    # geometry, seed, retries and n_eff; every one of the 10^8 members and
+    # 10^8 disjoint keys is queried on the GPU and by the oracle on the
+    # GPU-built array, byte for byte.
+    import os
+
     n = 100_000_000
-    keys = _keys(n, 0xC2)
+    threads = max(1, min(32, os.cpu_count() or 1))
+    keys = _keys(n, 0x5EED)
     s = vf.vf_build(keys, None, params=vf.vf_params_default(kind=vf.FILTER, b=8, seed=1))
     info = s.info
+    hkeys = synth.u64_keys(0, n, 0x5EED)
+    assert (keys[:1000].cpu().numpy().view(np.uint64) == hkeys[:1000]).all()
+    st, oi, _ = orc.build(orc.default_params(kind=orc.FILTER, b=8, seed=1, threads=threads), hkeys)
+    assert st == orc.OK
+    for f in GEOMETRY:
+        assert getattr(info, f) == getattr(oi, f), f
+    assert info.peeled == oi.peeled == n
     assert info.h == 3 and info.c == 1.105 and info.lg_seg == 15
     assert 0.104 < info.total_cells / n - 1 < 0.108  # Sec. 5: ~10.5% overhead
-    _check_sampled(vf, orc, s, keys, n, 1, 8)
+    data = vf.vf_export(s)
+    oinfo = orc.Info()
+    for f, _ in orc.Info._fields_:
+        setattr(oinfo, f, getattr(info, f))
+    gm = s.query(keys).cpu().numpy()
+    assert gm.all()
+    assert (orc.query(oinfo, data, hkeys, threads=threads) == gm).all()
+    del keys, gm
+    others_h = synth.u64_keys(n, n, 0x5EED)
+    others = torch.from_numpy(others_h.view(np.int64)).cuda()
+    go = s.query(others).cpu().numpy()
+    assert (orc.query(oinfo, data, others_h, threads=threads) == go).all()
+    p = 2.0**-8
+    assert abs(go.mean() - p) < 5 * math.sqrt(p * (1 - p) / n)  # FPR 2^-b (Sec. 3.1)
     s.free()
 
 

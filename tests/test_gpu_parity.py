@@ -366,6 +366,88 @@ def test_filter_duplicate_keys_sharded_fuse(vf, orc):
     assert info.h >= 1 and info.n_eff == oi.n_eff == 2_000_000
 
 
+def with_repeated_pairs(n, frac, seed, b):
+    """n distinct keys with values, plus copies of a random subset (same values,
+    a few in triplicate), shuffled; also returns the distinct keys and values."""
+    keys = synth.u64_keys(0, n, seed)
+    vals = synth.values(n, b, seed)
+    rng = np.random.default_rng(seed)
+    rep = rng.choice(n, size=int(n * frac), replace=False)
+    idx = np.concatenate([np.arange(n), rep, rep[: len(rep) // 4]])
+    idx = idx[rng.permutation(len(idx))]
+    return keys[idx], vals[idx], keys, vals
+
+
+DUP_REGIMES = {
+    "fuse": (1_000_000, dict(seed=3)),
+    "fuse_rounds": (1_000_000, dict(seed=3, fuse_solver=1)),
+    "sharded_fuse": (2_000_000, dict(mode=1, eps=0.01, seed=6)),
+    "lge": (60_000, dict(seed=4)),
+    "lge_unsharded": (10_000, dict(seed=5)),
+    "mwhc": (300_000, dict(mode=3, eps=0.01, eta=1e-3, seed=7)),
+}
+
+
+@pytest.mark.parametrize("regime", sorted(DUP_REGIMES))
+def test_function_repeated_pairs_are_dropped(vf, orc, regime):
+    # Sec. 4.4: a (key, value) pair given several times is one equation: the
+    # copies are dropped (fuse and MWHC regimes: found among the unpeeled edges
+    # of the failed first peel; LGE: in the core), n_eff equals the oracle's
+    n, kw = DUP_REGIMES[regime]
+    dk, dv, keys, vals = with_repeated_pairs(n, 0.02, 31, 8)
+    s, info, oi = check_build(vf, orc, dk, dv, n_other=20_000, **kw)
+    assert info.n_eff == oi.n_eff == n < len(dk)
+    assert (host(s.query(dev(keys))) == vals).all()
+
+
+@pytest.mark.parametrize("regime", sorted(DUP_REGIMES))
+def test_function_key_with_two_values_is_vf_edup(vf, orc, regime):
+    # a key given with two different values has no solution at any seed: the
+    # build stops at its first attempt with VF_EDUP, as the oracle does
+    n, kw = DUP_REGIMES[regime]
+    keys = synth.u64_keys(0, n, 32)
+    vals = synth.values(n, 8, 32)
+    dk = np.concatenate([keys, keys[n // 3: n // 3 + 1]])
+    dv = np.concatenate([vals, (vals[n // 3: n // 3 + 1] ^ 5).astype(vals.dtype)])
+    p = vf.vf_params_default(kind=vf.FUNC, **kw)
+    with pytest.raises(vf.VFError) as e:
+        vf.vf_build(dev(dk), dev(dv), params=p)
+    assert e.value.status == 4, str(e.value)  # VF_EDUP
+    st, oi, _ = orc.build(orc.default_params(kind=orc.FUNC, **{k: v for k, v in kw.items() if k != "fuse_solver"}),
+                          dk, dv)
+    assert st == orc.EDUP and oi.retries == 0
+
+
+def test_function_duplicates_byte_strings_and_wide_values(vf, orc):
+    # byte strings in the LGE regime; 40-bit values (two 32-bit slices): a key
+    # whose two values differ only in the high slice is still VF_EDUP
+    data_, offs = synth.byte_strings(0, 30_000, 33)
+    strs = [bytes(data_[offs[i]:offs[i + 1]]) for i in range(30_000)]
+    vals = synth.values(30_000, 16, 33)
+    s2 = strs + strs[:100]
+    v2 = np.concatenate([vals, vals[:100]])
+    o2 = np.zeros(len(s2) + 1, dtype=np.uint64)
+    o2[1:] = np.cumsum([len(x) for x in s2])
+    buf = np.frombuffer(b"".join(s2), dtype=np.uint8).copy()
+    s, info, oi = check_build(vf, orc, buf, v2, offsets=o2, b=16, seed=2)
+    assert info.n_eff == oi.n_eff == 30_000
+    v2[-1] ^= 1
+    with pytest.raises(vf.VFError) as e:
+        vf.vf_build(dev(buf), dev(v2), offsets=dev(o2), params=vf.vf_params_default(b=16, key_kind=vf.KEYS_BYTES))
+    assert e.value.status == 4
+    n = 50_000
+    keys = synth.u64_keys(0, n, 34)
+    vals = synth.values(n, 40, 34)
+    dk = np.concatenate([keys, keys[:10]])
+    dv = np.concatenate([vals, vals[:10]])
+    s, info, oi = check_build(vf, orc, dk, dv, b=40, seed=3)
+    assert info.n_eff == oi.n_eff == n
+    dv[-1] ^= np.uint64(1 << 37)
+    with pytest.raises(vf.VFError) as e:
+        vf.vf_build(dev(dk), dev(dv), params=vf.vf_params_default(b=40))
+    assert e.value.status == 4
+
+
 def test_query_stream_async_and_reuse(vf, orc):
     n = 100_000
     keys = synth.u64_keys(0, n, 12)
@@ -388,3 +470,37 @@ def test_invalid_arguments(vf):
     with pytest.raises(vf.VFError) as e:
         vf.vf_build(keys, None, params=vf.vf_params_default(kind=vf.FUNC))
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("b,kind", [(8, "filter"), (16, "func"), (13, "func"), (40, "func")])
+def test_query_host_buffers_pipelined(vf, orc, b, kind):
+    # 64-bit keys or outputs in host memory go through the chunked two-stream
+    # pipeline (chunks of 2^23 keys; here 2 full chunks and a ragged third):
+    # every combination of host/device keys and outputs, pinned and pageable
+    # host memory, equals the device-resident query and the oracle's query
+    n = 200_000
+    keys = synth.u64_keys(0, n, 51)
+    vals = synth.values(n, b, 51) if kind == "func" else None
+    s = vf.vf_build(dev(keys), None if vals is None else dev(vals),
+                    params=vf.vf_params_default(kind=vf.FUNC if kind == "func" else vf.FILTER, b=b, seed=2))
+    m = 2 * (1 << 23) + 12_345
+    q = np.concatenate([keys, synth.u64_keys(n, m - n, 51)])
+    qd = dev(q)
+    want = host(s.query(qd))
+    info = s.info
+    ref = orc.query(oracle_info(orc, info), vf.vf_export(s), q[:300_000])
+    assert (want[:300_000] == ref).all()
+    pinned = torch.from_numpy(q.view(np.int64)).pin_memory()
+    tdt = s.query(qd[:1]).dtype
+    cases = [
+        (q, None),                                          # pageable keys, host output
+        (pinned, None),                                     # pinned keys, host output (CPU tensor)
+        (q, torch.empty(m, dtype=tdt, device="cuda")),      # host keys, device output
+        (qd, np.empty(m, dtype=want.dtype)),                # device keys, pageable host output
+        (qd, torch.empty(m, dtype=tdt).pin_memory()),       # device keys, pinned host output
+    ]
+    for kin, out in cases:
+        res = vf.vf_query(s, kin, out=out)
+        got = res if isinstance(res, np.ndarray) else host(res)
+        assert got.dtype == want.dtype and (got == want).all()
+    s.free()
