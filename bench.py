@@ -383,14 +383,8 @@ def run_gpu(args):
     qps = 2 * n * world / (q_ms * 1e-3)
     q_hbm = random_sector_roofline(qps / world, b, kind, hbm, peak_kind)
     out["query"]["roofline"] = {"hbm": q_hbm}
-    if info.data_bytes <= L2_BYTES:
-        l2 = l2_sector_rate(int(info.data_bytes), kd.device)
-        got = 3 * qps / world
-        out["query"]["roofline"]["l2"] = {
-            "bound": "l2", "unit": "G sectors/s", "achieved": round(got / 1e9, 3),
-            "peak": round(l2["sectors_per_s"] / 1e9, 3), "frac": round(got / l2["sectors_per_s"], 4),
-            "peak_source": "measured in this run: " + l2["source"],
-            "data_bytes": int(info.data_bytes), "l2_bytes": L2_BYTES}
+    out["query"]["roofline"]["sectors"] = sector_roofline(
+        qps / world, int(info.data_bytes), "l2" if info.data_bytes <= L2_BYTES else "hbm")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on every host core over the whole workload, and on one
         # core over a bounded sample
@@ -641,31 +635,25 @@ def random_sector_roofline(qps: float, b: int, kind: str, hbm: float, peak_kind:
             "bytes_per_query": per_q}
 
 
-def l2_sector_rate(table_bytes: int, device) -> dict:
-    """Random 32-byte sector reads per second that torch.take sustains from an
-    L2-resident table of `table_bytes` (one random 4-byte element per index,
-    indices streamed from HBM): the L2 denominator of an L2-resident query."""
-    import torch
+def sector_rate(table_bytes: int) -> dict:
+    """Random 32-byte sector reads per second that the device delivers from a
+    table of `table_bytes` (the library's probe: 12 independent random 4-byte
+    loads per thread, best of six launches)."""
+    import paper_2503_18397_gb300 as vf
 
-    n = max(1 << 20, table_bytes // 4)
-    table = torch.arange(n, dtype=torch.int32, device=device)
-    m = 1 << 27
-    idx = torch.randint(0, n, (m,), device=device, dtype=torch.int64)
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    best = 0.0
-    for it in range(6):
-        torch.take(table, idx[: 1 << 20])  # touch the table: it stays in L2
-        e0.record(st)
-        out = torch.take(table, idx)
-        e1.record(st)
-        torch.cuda.synchronize()
-        if it > 0:
-            best = max(best, m / (e0.elapsed_time(e1) * 1e-3))
-    del table, idx, out
-    torch.cuda.empty_cache()
-    return {"sectors_per_s": best, "source": f"torch.take of 2^27 random 4-byte elements from a "
-                                             f"{table_bytes / 1e6:.1f} MB int32 table (best of 5)"}
+    r = vf.vf_sector_rate(int(table_bytes))
+    return {"sectors_per_s": r, "source": f"measured in this run: vf_sector_rate over a {table_bytes / 1e6:.1f} MB "
+                                         f"table (random 4-byte loads, one 32-byte sector each)"}
+
+
+def sector_roofline(qps: float, table_bytes: int, bound: str) -> dict:
+    """Three random sectors per query against the device's measured random-
+    sector rate for a table the size of the data array."""
+    pk = sector_rate(table_bytes)
+    got = 3 * qps
+    return {"bound": bound, "unit": "G sectors/s", "achieved": round(got / 1e9, 3),
+            "peak": round(pk["sectors_per_s"] / 1e9, 3), "frac": round(got / pk["sectors_per_s"], 4),
+            "peak_source": pk["source"], "data_bytes": int(table_bytes)}
 
 
 def measure_c5_scale(n: int, hbm: float, peak_kind: str) -> dict:
@@ -716,7 +704,8 @@ def measure_c5_scale(n: int, hbm: float, peak_kind: str) -> dict:
            "shards": int(info.shards), "cells_per_shard": int(info.cells), "lg_seg": int(info.lg_seg), "c": info.c,
            "data_bytes": int(info.data_bytes), "space_overhead": round(info.total_cells / n - 1, 4),
            "retries": int(info.retries), "query_gqps": round(qps / 1e9, 3),
-           "query_roofline": random_sector_roofline(qps, 8, "filter", hbm, peak_kind),
+           "query_roofline": {"hbm": random_sector_roofline(qps, 8, "filter", hbm, peak_kind),
+                              "sectors": sector_roofline(qps, int(info.data_bytes), "hbm")},
            "members_ok": bool(o1.bool().all().item()), "fpr": float(o2.float().mean().item()),
            "phases": {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in phases.items() if v[1]},
            "gpu_launches": int(sum(v[1] for v in phases.values())), "clocks": clk}

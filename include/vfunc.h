@@ -51,13 +51,20 @@ enum { VF_FUNC = 0, VF_FILTER = 1 };
 enum { VF_KEYS_U64 = 0, VF_KEYS_BYTES = 1 };
 enum { VF_MODE_AUTO = 0, VF_MODE_FUSE = 1, VF_MODE_LGE = 2, VF_MODE_MWHC = 3 };
 enum { VF_REGIME_FUSE = 1, VF_REGIME_LGE = 2, VF_REGIME_MWHC = 3 };
-/* Fuse-regime solver. Both peel the same hypergraph (Sec. 4.3) and give the
+/* Fuse-regime solver. All peel the same hypergraph (Sec. 4.3) and give the
  * same query results; they differ in how the work is scheduled on the GPU.
- * VF_SOLVER_FLOW: asynchronous worklist peeling that records peeled edges in
- * an order whose reverse is a valid assignment order, then a dataflow
- * assignment. VF_SOLVER_ROUNDS: peeling in synchronous rounds with a grid
- * barrier, assignment in reverse rounds. */
-enum { VF_SOLVER_FLOW = 0, VF_SOLVER_ROUNDS = 1 };
+ * VF_SOLVER_FLOW (default): asynchronous worklist peeling that records
+ * peeled edges in an order whose reverse is a valid assignment order, then a
+ * dataflow assignment. VF_SOLVER_ROUNDS: peeling in synchronous rounds with
+ * a grid barrier, assignment in reverse rounds. VF_SOLVER_WAVE: vertex words
+ * that sum the degree, the other two vertices and the value of the incident
+ * edges, so a peeling step is one fetch-and-add per vertex; grid-wide rounds
+ * for the initial cascades, then one CTA per shard for the waves that sweep
+ * its segments (Sec. 4.5); assignment in reverse rounds. It needs fuse graphs
+ * with b <= 57 - 2 lg_seg and at most 1024 shards; other structures, and
+ * shards whose waves outgrow its per-round capacity, are solved by
+ * VF_SOLVER_FLOW. */
+enum { VF_SOLVER_FLOW = 0, VF_SOLVER_ROUNDS = 1, VF_SOLVER_WAVE = 2 };
 
 /* Build parameters. vf_params_default() fills the paper's defaults. */
 typedef struct {
@@ -87,7 +94,7 @@ typedef struct {
                                 (24576); larger shards are solved too (up to 65535
                                 cells per shard), with a per-shard pool that grows
                                 with the shard (see VF_ECAPACITY under vf_build) */
-    int fuse_solver;         /* VF_SOLVER_FLOW (default) or VF_SOLVER_ROUNDS */
+    int fuse_solver;         /* VF_SOLVER_FLOW (default), VF_SOLVER_ROUNDS or VF_SOLVER_WAVE */
 } vf_params;
 
 /* Geometry and outcome of a built structure. */
@@ -110,8 +117,9 @@ typedef struct {
     uint64_t seed;           /* seed of the successful attempt */
     int retries;             /* failed attempts before it */
     uint64_t peeled, core;   /* edges peeled / edges solved by elimination (last attempt) */
-    uint64_t rounds;         /* fuse regime, VF_SOLVER_ROUNDS: synchronous peeling rounds of
-                                the last attempt, summed over shard groups; 0 otherwise */
+    uint64_t rounds;         /* fuse regime, VF_SOLVER_ROUNDS and VF_SOLVER_WAVE: synchronous
+                                peeling rounds of the last attempt (wave: grid-wide rounds plus
+                                the most rounds of a shard), summed over shard groups; 0 otherwise */
 } vf_info;
 
 void vf_params_default(vf_params *p);
@@ -310,6 +318,18 @@ vf_status vf_build_static(const uint64_t *keys, const void *values, uint64_t n, 
  *     runs out; the build returns VF_ETIMEOUT and the CUDA context stays usable.
  * Errors: VF_EINVAL (fail_attempts < 0). */
 vf_status vf_debug_faults(int fail_attempts, uint32_t assign_poll_limit, int stall_assign);
+
+/* Random 32-byte sector reads per second that this device delivers from a
+ * table of table_bytes bytes (the paper has no counterpart; a measurement
+ * aid for the query's roofline). A query reads three cells at random
+ * positions of a data array, one sector each; small arrays are served from
+ * L2, large ones from HBM, whose rate for scattered sectors is far below its
+ * copy bandwidth. The probe allocates the table on the current device,
+ * issues 12 independent random 4-byte loads per thread over a grid of 8
+ * blocks of 256 threads per SM, reports the best of six timed launches and
+ * frees everything. Waits for completion. Errors: VF_EINVAL (NULL result,
+ * table below 4096 bytes), VF_ENOMEM, VF_ECUDA. */
+vf_status vf_sector_rate(uint64_t table_bytes, void *stream, double *sectors_per_s);
 
 /* Release a structure (NULL is accepted). */
 vf_status vf_free(vf_struct *s);

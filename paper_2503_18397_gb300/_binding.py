@@ -25,7 +25,7 @@ FUNC, FILTER = 0, 1
 KEYS_U64, KEYS_BYTES = 0, 1
 MODE_AUTO, MODE_FUSE, MODE_LGE, MODE_MWHC = 0, 1, 2, 3
 REGIME_FUSE, REGIME_LGE, REGIME_MWHC = 1, 2, 3
-SOLVER_FLOW, SOLVER_ROUNDS = 0, 1
+SOLVER_FLOW, SOLVER_ROUNDS, SOLVER_WAVE = 0, 1, 2
 STATUS = {0: "VF_OK", 1: "VF_EINVAL", 2: "VF_ENOMEM", 3: "VF_EBUILD", 4: "VF_EDUP", 5: "VF_ETIMEOUT",
           6: "VF_ECUDA", 7: "VF_ECAPACITY", 8: "VF_EAGAIN", 9: "VF_EIO"}
 EAGAIN, EIO = 8, 9
@@ -114,6 +114,7 @@ def lib():
         L.vf_query_batch.restype = C.c_int
         L.vf_timing_enable.argtypes = [i32]
         L.vf_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(u64)]
+        L.vf_sector_rate.argtypes = [u64, vp, C.POINTER(C.c_double)]
         L.vf_build_resumable.argtypes = [vp, vp, vp, u64, C.POINTER(VfParams), C.c_char_p, u64, C.c_uint32, vp,
                                          C.POINTER(vp)]
         L.vf_serialize.argtypes = [vp, vp, u64, C.POINTER(u64)]
@@ -424,6 +425,13 @@ def vf_timing_enable(on: bool = True):
 def vf_debug_faults(fail_attempts: int = 0, assign_poll_limit: int = 0, stall_assign: bool = False):
     """Fault injection for tests (process-wide; all zero = off)."""
     _check(lib().vf_debug_faults(int(fail_attempts), int(assign_poll_limit), 1 if stall_assign else 0))
+
+
+def vf_sector_rate(table_bytes: int, stream=None) -> float:
+    """Random 32-byte sector reads per second from a table of table_bytes bytes."""
+    r = C.c_double()
+    _check(lib().vf_sector_rate(table_bytes, _stream(stream), C.byref(r)))
+    return r.value
 
 
 def vf_timing_read() -> dict:

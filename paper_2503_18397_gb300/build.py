@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvfunc.so")
-SOURCES = ["vf_build.cu", "vf_peel.cu", "vf_flow.cu", "vf_query.cu", "vf_lge.cu", "vf_batch.cu", "vf_capi.cu", "vf_static.cu", "vf_store.cu", "vf_wide.cu"]
+SOURCES = ["vf_build.cu", "vf_peel.cu", "vf_flow.cu", "vf_query.cu", "vf_lge.cu", "vf_batch.cu", "vf_capi.cu", "vf_static.cu", "vf_store.cu", "vf_wide.cu", "vf_wave.cu", "vf_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -467,6 +468,125 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     return VF_OK;
 }
 
+// One attempt of the wave solver (csrc/vf_wave.cu). Returns VF_OK, VF_EBUILD
+// (peel failed: retry) or an error; *fallback: the shards exceeded the wave
+// phase's capacities and the attempt must be solved by another solver (the
+// data array is untouched then).
+vf_status solve_wave(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
+                     const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
+                     uint64_t* rounds_out, uint64_t cell_base, const uint32_t* drop, uint64_t ndrop,
+                     DevBuf* claimed_out, bool* fallback) {
+    *fallback = false;
+    const uint64_t n = in.n_eff;
+    const uint64_t V = in.total_cells;
+    const uint32_t S = uint32_t(in.shards);
+    const uint64_t fcap = V / 2 + 4096;
+    // phase II spill area per shard and frontier buffer: a quarter of its cells, at most 2^20 entries
+    const uint64_t scap = std::min<uint64_t>(in.cells / 4 + 64, uint64_t(1) << 20);
+    DevBuf W, stamp, fv, fw, sv, sw, rec, off1, off2, per, ctr;
+    VF_CK(W.alloc(V * 8, st));
+    VF_CK(cudaMemsetAsync(W.p, 0, V * 8, st));
+    VF_CK(stamp.alloc(V * 4, st));
+    VF_CK(cudaMemsetAsync(stamp.p, 0, V * 4, st));
+    VF_CK(fv.alloc(2 * fcap * 4, st));
+    VF_CK(fw.alloc(2 * fcap * 8, st));
+    VF_CK(sv.alloc(2 * uint64_t(S) * scap * 4, st));
+    VF_CK(sw.alloc(2 * uint64_t(S) * scap * 8, st));
+    VF_CK(rec.alloc(std::max<uint64_t>(n, 1) * 16, st));
+    VF_CK(off1.alloc(264 * 4, st));
+    VF_CK(cudaMemsetAsync(off1.p, 0, 264 * 4, st));
+    VF_CK(off2.alloc(uint64_t(S) * vf::kWRCap * 4, st));
+    // per shard: phase II rounds (u32), base2 (u64), peel1 (u32), front1 (u32)
+    VF_CK(per.alloc(uint64_t(S) * 20, st));
+    VF_CK(cudaMemsetAsync(per.p, 0, uint64_t(S) * 20, st));
+    const size_t ctr_bytes = vf::kWaveCtrWords * 4 + sizeof(vf::Bar2);
+    VF_CK(ctr.alloc(ctr_bytes, st));
+    VF_CK(cudaMemsetAsync(ctr.p, 0, ctr_bytes, st));
+    const uint32_t one = 1;
+    VF_CK(cudaMemcpyAsync(ctr.as<uint32_t>() + vf::kWaveCtrR0, &one, 4, cudaMemcpyHostToDevice, st));
+    vf::WaveArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.loc = loc;
+    a.val = val;
+    a.start = start;
+    a.drop = drop;
+    a.S = S;
+    a.g = g;
+    a.n = n;
+    a.W = W.as<unsigned long long>();
+    a.stamp = stamp.as<uint32_t>();
+    a.fv[0] = fv.as<uint32_t>();
+    a.fv[1] = fv.as<uint32_t>() + fcap;
+    a.fw[0] = fw.as<unsigned long long>();
+    a.fw[1] = fw.as<unsigned long long>() + fcap;
+    a.fcap = fcap;
+    a.sfv = sv.as<uint32_t>();
+    a.sfw = sw.as<unsigned long long>();
+    a.scap = scap;
+    a.rec = rec.as<uint4>();
+    a.off1 = off1.as<uint32_t>();
+    a.off2 = off2.as<uint32_t>();
+    a.base2 = per.as<unsigned long long>();
+    a.rounds2 = reinterpret_cast<uint32_t*>(per.as<uint8_t>() + uint64_t(S) * 8);
+    a.peel1 = a.rounds2 + S;
+    a.front1 = a.peel1 + S;
+    a.ctr = ctr.as<uint32_t>();
+    a.bar = reinterpret_cast<vf::Bar2*>(a.ctr + vf::kWaveCtrWords);
+    a.data = data;
+    a.cell_base = cell_base;
+    {
+        PhaseTimer t(kPhAccum, st, 2);  // incidence, round-1 frontier
+        VF_CK(vf::launch_wave_incidence(a, st));
+    }
+    {
+        PhaseTimer t(kPhPeel, st);
+        VF_CK(vf::launch_wave_peel(a, st));
+    }
+    std::vector<uint32_t> h(vf::kWaveCtrWords);
+    VF_CK(cudaMemcpyAsync(h.data(), a.ctr, vf::kWaveCtrWords * 4, cudaMemcpyDeviceToHost, st));
+    std::vector<uint32_t> r2(S);
+    VF_CK(cudaMemcpyAsync(r2.data(), a.rounds2, uint64_t(S) * 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaStreamSynchronize(st));
+    const uint32_t err = h[vf::kWaveCtrErr], count = h[vf::kWaveCtrPeeled], r0 = h[vf::kWaveCtrR0];
+    *peeled = count;
+    *rounds_out = (r0 ? r0 - 1 : 0) + (S ? *std::max_element(r2.begin(), r2.end()) : 0);
+    if (err & vf::kErrTimeout) return fail(VF_ETIMEOUT, "wave solver: grid barrier timed out");
+    if (err & (vf::kErrFrontier | vf::kErrCapacity)) {  // beyond the wave phase's capacities
+        *fallback = true;
+        return VF_EBUILD;
+    }
+    if (err & vf::kErrDegOverflow) return VF_EBUILD;
+    if (count != n - ndrop) {  // non-empty 2-core
+        if (claimed_out) {
+            VF_CK(claimed_out->alloc(std::max<uint64_t>((n + 31) / 32, 1) * 4, st));
+            VF_CK(vf::launch_wave_claimed(a, claimed_out->as<uint32_t>(), st));
+        }
+        return VF_EBUILD;
+    }
+    {
+        PhaseTimer t(kPhAssign, st, 2);  // phase II rounds per shard, then phase I rounds
+        VF_CK(vf::launch_wave_assign(a, st));
+        VF_CK(cudaMemsetAsync(a.bar, 0, sizeof(vf::Bar2), st));
+        vf::FuseSolveArgs f;
+        std::memset(&f, 0, sizeof f);
+        f.S = S;
+        f.g = g;
+        f.rec = a.rec;
+        f.round_off = a.off1;
+        f.rounds = r0 > 1 ? r0 - 1 : 0;
+        f.bar = a.bar;
+        f.err = a.ctr + vf::kWaveCtrErr;
+        f.data = data;
+        f.cell_base = cell_base;
+        VF_CK(vf::launch_assign(f, st));
+    }
+    uint32_t e2 = 0;
+    VF_CK(cudaMemcpyAsync(&e2, a.ctr + vf::kWaveCtrErr, 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaStreamSynchronize(st));
+    if (e2 & vf::kErrTimeout) return fail(VF_ETIMEOUT, "wave solver: assignment barrier timed out");
+    return VF_OK;
+}
+
 // One attempt of the fuse-regime solver: the asynchronous solver (default) or
 // the round-synchronous one. Reorders loc / val within each shard. A build
 // whose peel fails is checked for duplicate local signatures among the
@@ -491,12 +611,18 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32
     for (int pass = 0;; pass++) {
         DevBuf claimed;
         const bool dedup = pass == 0;
-        vf_status rs;
-        if (solver == VF_SOLVER_FLOW) {
+        vf_status rs = VF_EINVAL;
+        bool fallback = solver == VF_SOLVER_WAVE && !vf::wave_eligible(g, uint32_t(in.shards));
+        if (solver == VF_SOLVER_WAVE && !fallback) {
+            rs = solve_wave(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base, drop.as<uint32_t>(),
+                            ndrop, dedup ? &claimed : nullptr, &fallback);
+            if (fallback) claimed.release();
+        }
+        if (solver == VF_SOLVER_FLOW || fallback) {
             *rounds_out = 0;
             rs = solve_flow(in, g, loc, val, start, data, st, peeled, cell_base,
                             drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
-        } else {
+        } else if (solver == VF_SOLVER_ROUNDS) {
             rs = solve_rounds(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base,
                               drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
         }
@@ -1047,8 +1173,9 @@ vf_status build_impl(const void* keys, const uint64_t* offsets, const void* valu
     if (p.key_kind == VF_KEYS_BYTES && !offsets) return fail(VF_EINVAL, "offsets is NULL");
     if (p.kind == VF_FUNC && n > 0 && !values) return fail(VF_EINVAL, "a function needs values");
     if (!(p.eps > 0.0) || !(p.eta > 0.0 && p.eta < 1.0) || p.max_retries < 0 || p.lge_target == 0 ||
-        p.lge_max_shard < 2 || p.mode < VF_MODE_AUTO || p.mode > VF_MODE_MWHC)
-        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes / mode");
+        p.lge_max_shard < 2 || p.mode < VF_MODE_AUTO || p.mode > VF_MODE_MWHC || p.fuse_solver < VF_SOLVER_FLOW ||
+        p.fuse_solver > VF_SOLVER_WAVE)
+        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes / mode / fuse solver");
     for (const auto& pw : {std::make_pair(keys, "keys"), std::make_pair(static_cast<const void*>(offsets), "offsets"),
                            std::make_pair(values, "values")}) {
         const vf_status cs = vf::check_here(pw.first, pw.second);
@@ -1641,8 +1768,9 @@ vf_status vf_build_batch(const vf_batch_item* items, uint32_t count, const vf_pa
                          const vf_batch_opts* opts, void* stream, vf_struct** out) {
     g_last_error.clear();
     if (!common || !out || (count > 0 && !items)) return fail(VF_EINVAL, "vf_build_batch: NULL argument");
-    if (common->mode < VF_MODE_AUTO || common->mode > VF_MODE_MWHC)
-        return fail(VF_EINVAL, "vf_build_batch: bad mode");
+    if (common->mode < VF_MODE_AUTO || common->mode > VF_MODE_MWHC || common->fuse_solver < VF_SOLVER_FLOW ||
+        common->fuse_solver > VF_SOLVER_WAVE)
+        return fail(VF_EINVAL, "vf_build_batch: bad mode or fuse solver");
     vf_batch_opts o;
     if (opts) o = *opts; else vf_batch_opts_default(&o);
     if (o.lge_target == 0) return fail(VF_EINVAL, "vf_build_batch: lge_target must be positive");

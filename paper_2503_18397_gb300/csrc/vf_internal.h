@@ -155,6 +155,53 @@ cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st);
 cudaError_t launch_tile_order(uint64_t* loc, uint32_t* val, uint64_t n, const unsigned long long* start,
                               uint32_t S, const Geom& g, cudaStream_t st);
 
+// Fuse-regime wave solver (csrc/vf_wave.cu): 64-bit vertex words that hold the
+// degree, the other two vertices and the value of the edges' sum; phase I in
+// grid-wide rounds, phase II with one CTA per shard; records assigned in
+// reverse rounds.
+constexpr uint32_t kWFCap = 8192;       // phase II frontier entries per round in shared memory
+constexpr uint32_t kWRCap = 1u << 16;   // phase II rounds per shard
+constexpr uint32_t kWMaxShards = 1024;
+struct WaveArgs {
+    const uint64_t* loc;              // bucketed local signatures
+    const uint32_t* val;              // bucketed values, NULL for a filter
+    const unsigned long long* start;  // S+1 shard starts
+    const uint32_t* drop;             // edges left out (duplicates), or NULL
+    uint32_t S;
+    Geom g;
+    uint64_t n;                       // edges
+    unsigned long long* W;            // S*cells vertex words
+    uint32_t* stamp;                  // S*cells: bits 0..15 round a vertex entered the frontier, 16..31 round it died
+    uint32_t* fv[2];                  // phase I frontier: vertex
+    unsigned long long* fw[2];        //   and its word at degree one
+    uint64_t fcap;
+    uint32_t* sfv;                    // phase II spill areas: shard s, frontier buffer k at (2s+k)*scap
+    unsigned long long* sfw;
+    uint64_t scap;
+    uint4* rec;                       // records {peeled vertex, other, other, value}: phase I, then per-shard regions
+    uint32_t* off1;                   // phase I: records of round r are [off1[r-1], off1[r])
+    uint32_t* off2;                   // phase II: shard s, round k: [off2[s*kWRCap+k], off2[s*kWRCap+k+1]) after base2[s]
+    uint32_t* rounds2;                // phase II rounds per shard
+    unsigned long long* base2;        // first record of each shard's phase II region
+    uint32_t* peel1;                  // per shard: edges peeled in phase I
+    uint32_t* front1;                 // per shard: phase I frontier entries of the next round
+    uint32_t* ctr;                    // counter words (csrc/vf_wave.cu)
+    Bar2* bar;
+    uint8_t* data;                    // assignment target
+    uint64_t cell_base;               // cell of the first vertex (shard groups)
+};
+bool wave_eligible(const Geom& g, uint32_t S);
+// Incidence (64-bit words) and the round-1 frontier of every degree-one vertex.
+cudaError_t launch_wave_incidence(const WaveArgs& a, cudaStream_t st);
+// The cooperative peeling kernel: phase I, then phase II.
+cudaError_t launch_wave_peel(WaveArgs a, cudaStream_t st);
+// Phase II records of every shard in reverse rounds (phase I: launch_assign).
+cudaError_t launch_wave_assign(const WaveArgs& a, cudaStream_t st);
+// After a failed peel: claim bits of every edge outside the 2-core.
+cudaError_t launch_wave_claimed(const WaveArgs& a, uint32_t* claimed, cudaStream_t st);
+constexpr uint32_t kWaveCtrWords = 224;
+constexpr uint32_t kWaveCtrErr = 192, kWaveCtrPeeled = 96, kWaveCtrR0 = 128, kWaveCtrRec = 64;
+
 // LGE regime: one CTA per shard (peel + lazy Gaussian elimination + assign).
 // A task is one shard of one structure; a launch may mix structures.
 struct LgeTask {

@@ -66,7 +66,7 @@ def test_injected_failures_retry_with_the_next_seeds(vf, orc):
 def test_assignment_wait_runs_out_and_the_context_stays_usable(vf):
     n = 1 << 20  # one fuse shard: the flow solver and its dataflow assignment
     keys, vals = synth.u64_keys(0, n, 62), synth.values(n, 8, 62)
-    p = vf.vf_params_default(kind=vf.FUNC, b=8, seed=5)
+    p = vf.vf_params_default(kind=vf.FUNC, b=8, seed=5, fuse_solver=vf.SOLVER_FLOW)
     try:
         vf.vf_debug_faults(assign_poll_limit=4096, stall_assign=True)
         with pytest.raises(vf.VFError) as ei:

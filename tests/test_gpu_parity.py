@@ -196,7 +196,7 @@ def test_lge_host_inputs(vf, orc):
 
 # both fuse-regime solvers (asynchronous worklist, round-synchronous) must give
 # the oracle's outcome; SOLVER values are 0 (flow) and 1 (rounds)
-SOLVERS = pytest.mark.parametrize("solver", [0, 1], ids=["flow", "rounds"])
+SOLVERS = pytest.mark.parametrize("solver", [0, 1, 2], ids=["flow", "rounds", "wave"])
 
 
 @SOLVERS
@@ -205,8 +205,10 @@ def test_function_fuse_unsharded_2pow20(vf, orc, solver):
     keys = synth.u64_keys(0, n, 1)
     vals = synth.values(n, 8, 1)
     s, info, _ = check_build(vf, orc, keys, vals, seed=1, n_other=1 << 18, fuse_solver=solver)
+    if solver != 0:
+        assert info.rounds > 0  # the round and wave solvers ran (no fallback to the worklist solver)
     assert info.regime == vf.REGIME_FUSE and info.h == 0 and info.lg_seg == 13
-    assert (0 < info.rounds < n) if solver == 1 else info.rounds == 0
+    assert (0 < info.rounds < n) if solver != 0 else info.rounds == 0
 
 
 @SOLVERS
@@ -381,6 +383,7 @@ def with_repeated_pairs(n, frac, seed, b):
 DUP_REGIMES = {
     "fuse": (1_000_000, dict(seed=3)),
     "fuse_rounds": (1_000_000, dict(seed=3, fuse_solver=1)),
+    "fuse_flow": (1_000_000, dict(seed=3, fuse_solver=0)),
     "sharded_fuse": (2_000_000, dict(mode=1, eps=0.01, seed=6)),
     "lge": (60_000, dict(seed=4)),
     "lge_unsharded": (10_000, dict(seed=5)),
