@@ -29,7 +29,7 @@ class Params(C.Structure):
         ("kind", C.c_int), ("b", C.c_int), ("key_kind", C.c_int), ("mode", C.c_int),
         ("max_retries", C.c_int), ("seed", C.c_uint64), ("eps", C.c_double), ("eta", C.c_double),
         ("lge_threshold", C.c_uint64), ("lge_target", C.c_uint64), ("lge_max_shard", C.c_uint64),
-        ("threads", C.c_int),
+        ("threads", C.c_int), ("arity", C.c_int),
     ]
 
 
@@ -40,7 +40,7 @@ class Info(C.Structure):
         ("shards", C.c_uint64), ("M", C.c_uint64), ("c", C.c_double), ("lg_seg", C.c_int),
         ("seg", C.c_uint64), ("l", C.c_uint64), ("T", C.c_uint64), ("cells", C.c_uint64),
         ("total_cells", C.c_uint64), ("data_bytes", C.c_uint64), ("seed", C.c_uint64),
-        ("retries", C.c_int), ("peeled", C.c_uint64), ("core", C.c_uint64),
+        ("retries", C.c_int), ("peeled", C.c_uint64), ("core", C.c_uint64), ("k", C.c_int),
     ]
 
     def as_dict(self):
@@ -90,6 +90,9 @@ def lib():
         L.orc_peel.restype = u64
         L.orc_peel.argtypes = [u64, u64, vp, vp, vp]
         L.orc_gf2_solve.argtypes = [u64, u64, vp, vp, vp]
+        L.orc_peel_k.restype = u64
+        L.orc_peel_k.argtypes = [u64, u64, i32, vp, vp, vp]
+        L.orc_gf2_solve_k.argtypes = [u64, u64, i32, vp, vp, vp]
         L.orc_sigs.argtypes = [i32, vp, vp, u64, u64, vp]
         L.orc_edges_of.argtypes = [C.POINTER(Info), vp, u64, vp]
         L.orc_params_default.argtypes = [C.POINTER(Params)]
@@ -130,16 +133,16 @@ def plan_h(params: Params, n: int):
     return h, reg.value, hbb.value, hdup.value
 
 
-def geometry(regime: int, h: int, M: int, b: int = 8, kind: int = FUNC) -> Info:
+def geometry(regime: int, h: int, M: int, b: int = 8, kind: int = FUNC, k: int = 3) -> Info:
     info = Info()
-    info.regime, info.h, info.shards, info.M, info.b, info.kind = regime, h, 1 << h, M, b, kind
+    info.regime, info.h, info.shards, info.M, info.b, info.kind, info.k = regime, h, 1 << h, M, b, kind, k
     lib().orc_geometry(C.byref(info))
     return info
 
 
 def edges_of(info: Info, locals_: np.ndarray) -> np.ndarray:
     locals_ = np.ascontiguousarray(locals_, dtype=np.uint64)
-    out = np.zeros((len(locals_), 3), dtype=np.uint64)
+    out = np.zeros((len(locals_), 4 if info.k == 4 else 3), dtype=np.uint64)
     lib().orc_edges_of(C.byref(info), _ptr(locals_), len(locals_), _ptr(out))
     return out
 
@@ -198,17 +201,21 @@ def query(info: Info, data: np.ndarray, keys, offsets=None, threads: int = 1) ->
 
 
 def peel(V: int, edges: np.ndarray):
+    """Stack peel of an (m, k) edge array (k = 3 or 4)."""
     edges = np.ascontiguousarray(edges, dtype=np.uint32)
     m = len(edges)
+    k = edges.shape[1] if edges.ndim == 2 else 3
     order = np.zeros(max(m, 1), dtype=np.uint32)
     side = np.zeros(max(m, 1), dtype=np.uint8)
-    ne = lib().orc_peel(V, m, _ptr(edges), _ptr(order), _ptr(side))
+    ne = lib().orc_peel_k(V, m, k, _ptr(edges), _ptr(order), _ptr(side))
     return ne, order[:ne], side[:ne]
 
 
 def gf2_solve(V: int, edges: np.ndarray, rhs: np.ndarray):
+    """Plain GF(2) elimination of an (m, k) edge system (k = 3 or 4)."""
     edges = np.ascontiguousarray(edges, dtype=np.uint32)
     rhs = np.ascontiguousarray(rhs, dtype=np.uint64)
+    k = edges.shape[1] if edges.ndim == 2 else 3
     w = np.zeros(max(V, 1), dtype=np.uint64)
-    ok = lib().orc_gf2_solve(V, len(edges), _ptr(edges), _ptr(rhs), _ptr(w))
+    ok = lib().orc_gf2_solve_k(V, len(edges), k, _ptr(edges), _ptr(rhs), _ptr(w))
     return bool(ok), w[:V]

@@ -58,6 +58,7 @@ void orc_params_default(orc_params *p) {
     p->lge_target = 16384;
     p->lge_max_shard = 24576;
     p->threads = 1;
+    p->arity = 3;
 }
 
 /* ------------------------------------------------------------------ hashing */
@@ -165,6 +166,13 @@ int orc_plan_h(const orc_params *p, uint64_t n, int *regime, int *h_bb, int *h_d
         *h_bb = orc_h_ballsbins(n, p->eps);
         *h_dup = orc_h_dupmwhc(n, p->eta, 1.23);
         h = *h_bb < *h_dup ? *h_bb : *h_dup;
+    } else if (reg == ORC_REGIME_FUSE && p->arity == 4) {
+        /* 4-uniform fuse graphs: Sec. 4.2's estimate of duplicate edges with
+         * k = 4, exp(-m / (2 c s^3)), is negligible at every shard size that
+         * eq. (logballsbins) allows, so that bound alone sets the shards. */
+        *h_bb = orc_h_ballsbins(n, p->eps);
+        *h_dup = -1;
+        h = *h_bb;
     } else if (reg == ORC_REGIME_FUSE) {
         /* Sec. 4.2: the number of shards is the smaller of the two bounds. */
         *h_bb = orc_h_ballsbins(n, p->eps);
@@ -207,6 +215,25 @@ void orc_geometry(orc_info *in) {
          * share an edge (the expansion factor grows for small sizes, Sec. 4.2) */
         uint64_t cells = (uint64_t)ceil(in->c * Mf);
         in->cells = cells < 32 ? 32 : cells;
+    } else if (in->k == 4) {
+        /* 4-uniform fuse graph (Sec. 4.2 with k = 4: l + 3 segments). The
+         * paper gives no expansion factor or segment size for k = 4; it builds
+         * on Graf and Lemire's fuse-graph estimates (eq. (ln) is their k = 3
+         * segment law), whose k = 4 forms are taken as they stand:
+         * c = max(1.075, 0.77 + 0.305 ln(600000) / ln M), segment size
+         * 2^floor(ln M / ln 2.91 - 0.5). Parity unpinned: no value of the
+         * paper fixes them. */
+        double c = 0.77 + 0.305 * log(600000.0) / log(Mf > 2.0 ? Mf : 2.0);
+        in->c = c > 1.075 ? c : 1.075;
+        double lg = floor(log(Mf) / log(2.91) - 0.5);
+        if (lg < 0) lg = 0;
+        if (lg > 32) lg = 32;
+        in->lg_seg = (int)lg;
+        in->seg = 1ULL << in->lg_seg;
+        uint64_t T = (uint64_t)ceil(in->c * Mf / (double)in->seg);
+        in->T = T < 4 ? 4 : T;
+        in->l = in->T - 3;
+        in->cells = in->T * in->seg;
     } else {
         double lg;
         if (in->h > 0 && in->M >= 10000000ULL) {
@@ -244,8 +271,19 @@ uint64_t orc_local(const uint64_t sig[2], int h) {
     return h == 0 ? sig[0] : (sig[0] << h) | (sig[1] >> (64 - h));
 }
 
-void orc_edge(const orc_info *in, uint64_t local, uint64_t v[3]) {
-    if (in->regime == ORC_REGIME_FUSE) {
+void orc_edge(const orc_info *in, uint64_t local, uint64_t v[4]) {
+    if (in->regime == ORC_REGIME_FUSE && in->k == 4) {
+        /* 4-uniform fuse graph: one vertex in each of segments s..s+3; the
+         * fourth offset comes from a second remix of the local signature. */
+        uint64_t v0 = orc_mulhi(local, in->l * in->seg);
+        uint64_t s = v0 / in->seg;
+        uint64_t r = orc_mix64(local ^ ORC_C_EDGE);
+        uint64_t q = orc_mix64(local ^ ORC_C_EDGE2);
+        v[0] = v0;
+        v[1] = (s + 1) * in->seg + (r % in->seg);
+        v[2] = (s + 2) * in->seg + ((r >> 32) % in->seg);
+        v[3] = (s + 3) * in->seg + (q % in->seg);
+    } else if (in->regime == ORC_REGIME_FUSE) {
         /* Fuse graph (Sec. 4.2): a start segment s in [0, l) and one vertex in
          * each of segments s, s+1, s+2. The first vertex (and with it the
          * segment) comes from the top bits of the local signature by fixed-point
@@ -322,15 +360,15 @@ static void cell_set(uint8_t *data, int b, uint64_t i, uint64_t v) {
  * its degree and the XOR of the indices of its incident edges. Vertices are
  * scanned in order; degree-one vertices go on the stack S; each popped vertex
  * of degree one has its only edge removed and pushed (with the vertex's side)
- * on E; popped vertices of degree zero are discarded. */
-uint64_t orc_peel(uint64_t V, uint64_t m, const uint32_t *edges, uint32_t *order, uint8_t *side) {
+ * on E; popped vertices of degree zero are discarded. Edges have k vertices. */
+uint64_t orc_peel_k(uint64_t V, uint64_t m, int k, const uint32_t *edges, uint32_t *order, uint8_t *side) {
     uint32_t *deg = calloc(V ? V : 1, sizeof *deg);
     uint64_t *xr = calloc(V ? V : 1, sizeof *xr);
     uint64_t *stack = malloc((V ? V : 1) * sizeof *stack);
     for (uint64_t e = 0; e < m; e++)
-        for (int k = 0; k < 3; k++) {
-            deg[edges[3 * e + k]]++;
-            xr[edges[3 * e + k]] ^= e;
+        for (int j = 0; j < k; j++) {
+            deg[edges[(uint64_t)k * e + j]]++;
+            xr[edges[(uint64_t)k * e + j]] ^= e;
         }
     uint64_t sp = 0, ne = 0;
     for (uint64_t v0 = 0; v0 < V; v0++) {
@@ -341,13 +379,13 @@ uint64_t orc_peel(uint64_t V, uint64_t m, const uint32_t *edges, uint32_t *order
             if (deg[v] == 0) continue;
             uint64_t e = xr[v];
             int sd = 0;
-            for (int k = 0; k < 3; k++)
-                if (edges[3 * e + k] == v) sd = k;
+            for (int j = 0; j < k; j++)
+                if (edges[(uint64_t)k * e + j] == v) sd = j;
             if (order) order[ne] = (uint32_t)e;
             if (side) side[ne] = (uint8_t)sd;
             ne++;
-            for (int k = 0; k < 3; k++) {
-                uint32_t w = edges[3 * e + k];
+            for (int j = 0; j < k; j++) {
+                uint32_t w = edges[(uint64_t)k * e + j];
                 deg[w]--;
                 xr[w] ^= e;
                 if (w != v && deg[w] == 1) stack[sp++] = w;
@@ -360,13 +398,17 @@ uint64_t orc_peel(uint64_t V, uint64_t m, const uint32_t *edges, uint32_t *order
     return ne;
 }
 
+uint64_t orc_peel(uint64_t V, uint64_t m, const uint32_t *edges, uint32_t *order, uint8_t *side) {
+    return orc_peel_k(V, m, 3, edges, order, side);
+}
+
 /* Plain Gaussian elimination over GF(2) with b-bit right-hand sides. Rows are
  * bit vectors over the V variables. Each row is reduced by the existing pivot
  * rows (pivot = lowest set bit) until it becomes a new pivot row, or zero; a
  * zero row with a non-zero right-hand side makes the system inconsistent.
  * Back-substitution runs over pivot columns from the highest down; variables
  * without a pivot are set to 0. */
-int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint64_t *rhs, uint64_t *w) {
+int orc_gf2_solve_k(uint64_t V, uint64_t m, int k, const uint32_t *edges, const uint64_t *rhs, uint64_t *w) {
     uint64_t W = (V + 63) / 64;
     if (W == 0) W = 1;
     uint64_t *rows = calloc((m ? m : 1) * W, sizeof(uint64_t));
@@ -378,8 +420,8 @@ int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint64_t 
     for (uint64_t c = 0; c < V; c++) pivot[c] = -1;
     for (uint64_t e = 0; e < m && ok; e++) {
         memset(cur, 0, W * sizeof(uint64_t));
-        for (int k = 0; k < 3; k++) {
-            uint32_t v = edges[3 * e + k];
+        for (int j = 0; j < k; j++) {
+            uint32_t v = edges[(uint64_t)k * e + j];
             cur[v / 64] ^= 1ULL << (v % 64);
         }
         uint64_t cr = rhs[e];
@@ -420,6 +462,10 @@ int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint64_t 
     return ok;
 }
 
+int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint64_t *rhs, uint64_t *w) {
+    return orc_gf2_solve_k(V, m, 3, edges, rhs, w);
+}
+
 /* ------------------------------------------------------------------- build */
 
 static int u64_cmp(const void *a, const void *b) {
@@ -441,15 +487,16 @@ static uint64_t value_at(const void *values, int b, uint64_t i) {
 static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, const uint64_t *val,
                        uint8_t *data, uint64_t base, uint64_t *peeled_out, pthread_mutex_t *cell_mu) {
     uint64_t V = in->cells;
-    uint32_t *edges = malloc((m ? m : 1) * 3 * sizeof(uint32_t));
+    const int k = in->k == 4 ? 4 : 3;
+    uint32_t *edges = malloc((m ? m : 1) * (uint64_t)k * sizeof(uint32_t));
     uint32_t *order = malloc((m ? m : 1) * sizeof(uint32_t));
     uint8_t *side = malloc(m ? m : 1);
     for (uint64_t e = 0; e < m; e++) {
-        uint64_t v[3];
+        uint64_t v[4];
         orc_edge(in, loc[e], v);
-        for (int k = 0; k < 3; k++) edges[3 * e + k] = (uint32_t)v[k];
+        for (int j = 0; j < k; j++) edges[(uint64_t)k * e + j] = (uint32_t)v[j];
     }
-    uint64_t ne = orc_peel(V, m, edges, order, side);
+    uint64_t ne = orc_peel_k(V, m, k, edges, order, side);
     *peeled_out = ne;
     uint64_t *w = calloc(V, sizeof(uint64_t));
     int ok = 1;
@@ -460,14 +507,14 @@ static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, cons
             uint8_t *is_peeled = calloc(m, 1);
             for (uint64_t i = 0; i < ne; i++) is_peeled[order[i]] = 1;
             uint64_t nc = 0;
-            uint32_t *ce = malloc((m - ne) * 3 * sizeof(uint32_t));
+            uint32_t *ce = malloc((m - ne) * (uint64_t)k * sizeof(uint32_t));
             uint64_t *cr = malloc((m - ne) * sizeof(uint64_t));
             for (uint64_t e = 0; e < m; e++) {
                 if (is_peeled[e]) continue;
-                memcpy(ce + 3 * nc, edges + 3 * e, 3 * sizeof(uint32_t));
+                memcpy(ce + (uint64_t)k * nc, edges + (uint64_t)k * e, (uint64_t)k * sizeof(uint32_t));
                 cr[nc++] = val[e];
             }
-            ok = orc_gf2_solve(V, nc, ce, cr, w);
+            ok = orc_gf2_solve_k(V, nc, k, ce, cr, w);
             free(is_peeled);
             free(ce);
             free(cr);
@@ -480,9 +527,9 @@ static int solve_shard(const orc_info *in, uint64_t m, const uint64_t *loc, cons
             uint32_t e = order[i];
             int sd = side[i];
             uint64_t x = val[e];
-            for (int k = 0; k < 3; k++)
-                if (k != sd) x ^= w[edges[3 * e + k]];
-            w[edges[3 * e + sd]] = x;
+            for (int j = 0; j < k; j++)
+                if (j != sd) x ^= w[edges[(uint64_t)k * e + j]];
+            w[edges[(uint64_t)k * e + sd]] = x;
         }
         /* cells of a bit array can share bytes with the neighbouring shard's */
         if (cell_mu) pthread_mutex_lock(cell_mu);
@@ -661,6 +708,7 @@ static void run_threads(int t, void *(*fn)(void *), void *ctx, size_t ctx_size) 
 int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
               const void *values, uint64_t n, orc_info *info, uint8_t **data_out) {
     if (p->b < 1 || p->b > 64 || (p->kind != ORC_FUNC && p->kind != ORC_FILTER)) return ORC_EINVAL;
+    if (p->arity != 3 && p->arity != 4) return ORC_EINVAL;
     if (p->key_kind != ORC_KEYS_U64 && p->key_kind != ORC_KEYS_BYTES) return ORC_EINVAL;
     if (n > 0 && keys == NULL) return ORC_EINVAL;
     if (p->key_kind == ORC_KEYS_BYTES && offsets == NULL) return ORC_EINVAL;
@@ -694,6 +742,7 @@ int orc_build(const orc_params *p, const void *keys, const uint64_t *offsets,
             run_threads(nt, sig_worker, sc, sizeof sc[0]);
         }
         in.h = orc_plan_h(p, n, &in.regime, &in.h_bb, &in.h_dup);
+        in.k = (in.regime == ORC_REGIME_FUSE && p->arity == 4) ? 4 : 3;
         uint64_t *cnt = NULL;
         for (;;) {
             in.shards = 1ULL << in.h;
@@ -805,11 +854,12 @@ void orc_query(const orc_info *in, const uint8_t *data, int key_kind, const void
             orc_sig_bytes((const uint8_t *)keys + offsets[i], offsets[i + 1] - offsets[i], in->seed, sig);
         uint64_t s = orc_shard(sig, in->h);
         uint64_t local = orc_local(sig, in->h);
-        uint64_t v[3];
+        uint64_t v[4];
         orc_edge(in, local, v);
         uint64_t base = s * in->cells;
         uint64_t x = orc_cell_get(data, in->b, base + v[0]) ^ orc_cell_get(data, in->b, base + v[1]) ^
                      orc_cell_get(data, in->b, base + v[2]);
+        if (in->k == 4) x ^= orc_cell_get(data, in->b, base + v[3]);
         if (in->kind == ORC_FILTER) {
             ((uint8_t *)out)[i] = x == orc_fingerprint(local, in->b);
         } else if (in->b <= 8) {
@@ -877,5 +927,10 @@ void orc_sigs(int key_kind, const void *keys, const uint64_t *offsets, uint64_t 
 }
 
 void orc_edges_of(const orc_info *in, const uint64_t *locals, uint64_t n, uint64_t *out) {
-    for (uint64_t i = 0; i < n; i++) orc_edge(in, locals[i], out + 3 * i);
+    const int k = in->k == 4 ? 4 : 3;
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t v[4];
+        orc_edge(in, locals[i], v);
+        for (int j = 0; j < k; j++) out[(uint64_t)k * i + j] = v[j];
+    }
 }

@@ -46,6 +46,7 @@ typedef struct {
     uint64_t lge_max_shard;  /* LGE regime: largest allowed shard */
     int threads;          /* signatures and shards computed by this many threads (1: one after the other);
                            * shards are independent, so the result does not depend on it */
+    int arity;            /* fuse regime: 3 (default) or 4 vertices per edge; other regimes are 3-uniform */
 } orc_params;
 
 typedef struct {
@@ -65,6 +66,7 @@ typedef struct {
     uint64_t seed;        /* seed of the successful attempt */
     int retries;          /* failed attempts before it */
     uint64_t peeled, core;/* edges peeled / left in 2-cores (last attempt) */
+    int k;                /* vertices per edge (3, or 4 for 4-uniform fuse graphs) */
 } orc_info;
 
 void orc_params_default(orc_params *p);
@@ -93,13 +95,14 @@ double orc_no_repeat_prob(double n, uint64_t t);
 
 /* Shard bits for n keys (before the largest shard is known). */
 int orc_plan_h(const orc_params *p, uint64_t n, int *regime, int *h_bb, int *h_dup);
-/* Fill c, lg_seg, seg, l, T, cells of info from regime and M (Sec. 4.2). */
+/* Fill c, lg_seg, seg, l, T, cells of info from regime, k and M (Sec. 4.2).
+ * Parity unpinned for k = 4 (the paper prints no arity-4 parameters). */
 void orc_geometry(orc_info *info);
 
 /* Shard, local signature, edge and fingerprint of a signature. */
 uint64_t orc_shard(const uint64_t sig[2], int h);
 uint64_t orc_local(const uint64_t sig[2], int h);
-void orc_edge(const orc_info *info, uint64_t local, uint64_t v[3]);
+void orc_edge(const orc_info *info, uint64_t local, uint64_t v[4]);  /* info->k vertices */
 uint64_t orc_fingerprint(uint64_t local, int b);
 
 /* Build. keys: uint64 array (ORC_KEYS_U64) or packed bytes with offsets[n+1].
@@ -128,11 +131,14 @@ uint64_t orc_cell_get(const uint8_t *data, int b, uint64_t i);
  * orc_gf2_solve: plain GE; returns 1 if solvable and writes w[V]. */
 uint64_t orc_peel(uint64_t V, uint64_t m, const uint32_t *edges, uint32_t *order, uint8_t *side);
 int orc_gf2_solve(uint64_t V, uint64_t m, const uint32_t *edges, const uint64_t *rhs, uint64_t *w);
+/* The same for edges of k vertices each. */
+uint64_t orc_peel_k(uint64_t V, uint64_t m, int k, const uint32_t *edges, uint32_t *order, uint8_t *side);
+int orc_gf2_solve_k(uint64_t V, uint64_t m, int k, const uint32_t *edges, const uint64_t *rhs, uint64_t *w);
 
 /* Batch forms of orc_sig_* and orc_edge used by the tests. */
 void orc_sigs(int key_kind, const void *keys, const uint64_t *offsets, uint64_t n, uint64_t seed,
               uint64_t *out);
-void orc_edges_of(const orc_info *in, const uint64_t *locals, uint64_t n, uint64_t *out);
+void orc_edges_of(const orc_info *in, const uint64_t *locals, uint64_t n, uint64_t *out);  /* n x in->k */
 
 #ifdef __cplusplus
 }

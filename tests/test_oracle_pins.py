@@ -713,3 +713,122 @@ def test_wide_filter_fingerprints_and_no_false_negatives(orc):
         assert orc.query(info, data, keys).all() and orc.query(info, data, other).sum() == 0
         f = orc.fingerprint(int(keys[0]), b)
         assert f >> b == 0 and orc.fingerprint(int(keys[0]), 32) == f >> (b - 32)
+
+
+# ------------------------------------------- 4-uniform fuse graphs (Sec. 4.2, k = 4)
+
+def _random_hypergraph_k(rng, V, m, k):
+    return np.array([rng.choice(V, size=k, replace=False) for _ in range(m)], dtype=np.uint32).reshape(m, k)
+
+
+def test_peel4_matches_bruteforce_2core(orc):
+    rng = np.random.default_rng(13)
+    for trial in range(250):
+        V = int(rng.integers(5, 10))
+        m = int(rng.integers(1, 11))
+        edges = _random_hypergraph_k(rng, V, m, 4)
+        ne, order, side = orc.peel(V, edges)
+        core = _brute_core(V, edges.tolist())
+        assert m - ne == len(core)
+        peeled = [int(e) for e in order]
+        for i, e in enumerate(peeled):
+            v = int(edges[e][side[i]])
+            later = peeled[i + 1:] + sorted(core)
+            assert all(v not in edges[f].tolist() for f in later)
+
+
+def test_gf2_solve4_matches_bruteforce(orc):
+    rng = np.random.default_rng(14)
+    for trial in range(200):
+        V = int(rng.integers(4, 9))
+        m = int(rng.integers(1, 12))
+        edges = _random_hypergraph_k(rng, V, m, 4)
+        rhs = rng.integers(0, 2, size=m).astype(np.uint64)
+        ok, w = orc.gf2_solve(V, edges, rhs)
+        found = any(all((sum(assign[v] for v in edges[i]) & 1) == rhs[i] for i in range(m))
+                    for assign in itertools.product((0, 1), repeat=V))
+        assert ok == found
+        if ok:
+            for i in range(m):
+                assert (int(w[edges[i][0]]) ^ int(w[edges[i][1]]) ^ int(w[edges[i][2]]) ^ int(w[edges[i][3]])) == rhs[i]
+
+
+def test_fuse4_edges_in_four_consecutive_segments(orc):
+    # Sec. 4.2's fuse graph of arity k = 4: a start segment s in [0, l) and
+    # one vertex in each of segments s, s+1, s+2, s+3 (l + 3 segments)
+    info = orc.geometry(orc.REGIME_FUSE, 0, 200_000, k=4)
+    assert info.k == 4 and info.T == info.l + 3 and info.cells == info.T * info.seg
+    loc = np.sort(synth.u64_keys(0, 60_000, 15))
+    e = orc.edges_of(info, loc).astype(np.int64)
+    assert e.shape == (60_000, 4)
+    seg = int(info.seg)
+    s = e[:, 0] // seg
+    assert (s < info.l).all() and (e < info.cells).all()
+    for k in range(1, 4):
+        assert ((e[:, k] // seg) == s + k).all()
+    assert (np.diff(e[:, 0]) >= 0).all()  # monotone in the local signature (Sec. 4.5)
+    for cnt, n_bins in ((np.bincount(s, minlength=info.l), info.l), (np.bincount(e[:, 3] % seg, minlength=seg), seg)):
+        exp_ = len(loc) / n_bins
+        assert ((cnt - exp_) ** 2 / exp_).sum() < (n_bins - 1) + 6 * math.sqrt(2 * (n_bins - 1))
+
+
+def test_fuse4_duplicate_edge_rate_matches_paper_estimate(orc):
+    # Sec. 4.2's count of possible edges with k = 4: about l * s^4, so the
+    # expected number of duplicate pairs is m (m - 1) / 2 / (l s^4); Monte Carlo
+    # with tiny segments
+    m = 2000
+    info = orc.geometry(orc.REGIME_FUSE, 0, m, k=4)
+    info.lg_seg, info.seg = 2, 4
+    info.T = math.ceil(1.1 * m / 4)
+    info.l = info.T - 3
+    info.cells = info.T * 4
+    trials, dups = 60, []
+    for t in range(trials):
+        e = orc.edges_of(info, synth.u64_keys(t * m, m, 16))
+        _, c = np.unique(e, axis=0, return_counts=True)
+        dups.append(int((c * (c - 1) // 2).sum()))
+    lam = m * (m - 1) / 2 / (info.l * 4**4)
+    assert abs(np.mean(dups) - lam) < 5 * math.sqrt(lam / trials), (np.mean(dups), lam)
+
+
+def test_fuse4_shards_by_ballsbins_and_uses_less_space(orc):
+    # k = 4: duplicate edges (exp(-m / (2 c s^3))) never bind, so the shard bits
+    # are eq. (logballsbins)'s; the space overhead is below the 3-uniform one at
+    # the same shard size (Sec. 7: one more probe for a smaller overhead)
+    p3, p4 = orc.default_params(mode=orc.MODE_FUSE), orc.default_params(mode=orc.MODE_FUSE, arity=4)
+    for n in (10**8, 10**10, 10**12):
+        h3, _, hbb, _ = orc.plan_h(p3, n)
+        h4, reg, hbb4, hdup4 = orc.plan_h(p4, n)
+        assert reg == orc.REGIME_FUSE and h4 == hbb4 == hbb and hdup4 == -1 and h4 >= h3
+    for M in (200_000, 12_500_000, 100_000_000):
+        g3 = orc.geometry(orc.REGIME_FUSE, 3, M)
+        g4 = orc.geometry(orc.REGIME_FUSE, 3, M, k=4)
+        assert g4.total_cells < g3.total_cells, M
+        info = orc.geometry(orc.REGIME_FUSE, 3, M, k=4)
+        s = info.seg
+        # the shard's cells are c M rounded up to whole segments
+        assert info.c * M <= info.cells < info.c * M + s + 1
+
+
+@pytest.mark.parametrize("kind,b,n,kw", [("func", 8, 300_000, {}), ("func", 13, 300_000, {}),
+                                         ("filter", 8, 2_000_000, {}), ("func", 16, 3_000_000, {"eps": 0.01})])
+def test_build_fuse4_decodes(orc, kind, b, n, kw):
+    # Problem 1 / Problem 2 with 4-uniform fuse graphs: every key decodes, no
+    # false negatives, FPR ~ 2^-b on disjoint keys; eps = 0.01 shards the keys
+    keys = synth.u64_keys(0, n, 17)
+    vals = synth.values(n, b, 17) if kind == "func" else None
+    p = orc.default_params(kind=orc.FUNC if kind == "func" else orc.FILTER, b=b, mode=orc.MODE_FUSE, arity=4,
+                           seed=3, threads=4, **kw)
+    st, info, data = orc.build(p, keys, vals)
+    assert st == orc.OK and info.k == 4 and info.regime == orc.REGIME_FUSE and info.core == 0
+    if "eps" in kw:
+        assert info.h > 0
+    out = orc.query(info, data, keys)
+    if kind == "func":
+        assert (out == vals).all()
+    else:
+        assert out.all()
+        other = synth.u64_keys(n, 1_000_000, 17)
+        fpr = orc.query(info, data, other).mean()
+        pb = 2.0**-b
+        assert abs(fpr - pb) < 5 * math.sqrt(pb * (1 - pb) / len(other))
