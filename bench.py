@@ -8,7 +8,7 @@ the 10^8 members and 10^8 disjoint non-members (false-positive rate ~ 2^-8).
 CUDA events on the launching stream); the query rate is reported next to it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                    [--workload c2|c1|c3|c4|c5|mwhc] [--no-extras] [--no-cpu-baseline]
+                    [--workload c2|c1|c3|c4|c5|mwhc|fuse4] [--no-extras] [--no-cpu-baseline]
 
 The default run also carries the rest of the metric as sub-objects, each
 measured after the headline: "c4" (4096 uneven structures, one batched
@@ -62,6 +62,9 @@ WORKLOADS = {
     "c3": ("func", 16, 10_000_000, "bytes",
            "VFunc n=1e7 byte strings (length 8..64), 16-bit values, LGE regime shards; "
            "query 1e7 members + 1e7 disjoint strings", {"mode": "lge"}),
+    "fuse4": ("filter", 8, 100_000_000, "u64",
+              "VFilter n=1e8 uniform 64-bit keys, b=8, 4-uniform fuse graphs (one more probe per query, "
+              "c = 1.075); query 1e8 members + 1e8 disjoint keys", {"mode": "fuse", "arity": 4}),
     "mwhc": ("filter", 8, 100_000_000, "u64",
              "VFilter n=1e8 uniform 64-bit keys, b=8, MWHC construction (3-partite random 3-hypergraphs, "
              "c=1.23, eps=0.01, eta=1e-3: 64 shards); query 1e8 members + 1e8 disjoint keys",
@@ -88,7 +91,7 @@ ALGO_BYTES = {
     "peel": lambda b, kind: 3 * 64.0,
     "assign": lambda b, kind: _vb(b, kind) + 4 * 64.0 + 1.105 * b / 8,
     "lge": lambda b, kind: 8.0 + _vb(b, kind) + 1.12 * b / 8,   # shard state on chip
-    "query": lambda b, kind: 8.0 + 3 * 32.0 + (1.0 if kind == "filter" else max(1.0, b / 8)),
+    "query": lambda b, kind, k=3: 8.0 + k * 32.0 + (1.0 if kind == "filter" else max(1.0, b / 8)),
 }
 
 # The same phases counted by what the kernels here move (the tile sort's extra
@@ -101,7 +104,7 @@ KERNEL_BYTES = {
     "peel": lambda b, kind: 8 + (0 if kind == "filter" else 4) + 2 * 32 + 16 + 16,
     "assign": lambda b, kind: 16 + 2 * 32 + 32 + 32,
     "lge": lambda b, kind: 8.0 + 8.0 * 3,
-    "query": lambda b, kind: 8.0 + 3 * 32.0 + 1.0,
+    "query": lambda b, kind, k=3: 8.0 + k * 32.0 + 1.0,
 }
 
 
@@ -345,7 +348,7 @@ def run_gpu(args):
 
     hbm, peak_kind = peaks()
     per_phase, dom, roof = phase_table(phases, n, args.steps, b, kind, hbm, peak_kind, args.workload,
-                                       info.regime == vf.REGIME_FUSE)
+                                       info.regime == vf.REGIME_FUSE, int(info.k))
     launches = sum(v[1] for v in phases.values())
     build_ns, qgps = job_rates(b_ms, q_ms, n, world)
     e2e_ns, e2e_qgps = job_rates(e2e_b_ms, e2e_q_ms, n, world)
@@ -381,10 +384,10 @@ def run_gpu(args):
     # the query's bound: its three random sectors come from L2 while the data
     # array fits there (the key stream and the output from HBM), else from HBM
     qps = 2 * n * world / (q_ms * 1e-3)
-    q_hbm = random_sector_roofline(qps / world, b, kind, hbm, peak_kind)
+    q_hbm = random_sector_roofline(qps / world, b, kind, hbm, peak_kind, int(info.k))
     out["query"]["roofline"] = {"hbm": q_hbm}
     out["query"]["roofline"]["sectors"] = sector_roofline(
-        qps / world, int(info.data_bytes), "l2" if info.data_bytes <= L2_BYTES else "hbm")
+        qps / world, int(info.data_bytes), "l2" if info.data_bytes <= L2_BYTES else "hbm", int(info.k))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on every host core over the whole workload, and on one
         # core over a bounded sample
@@ -410,7 +413,11 @@ def run_gpu(args):
 # Build attempts run hash+histogram once each; every attempt passes the keys
 # through scatter, incidence and peel (or the LGE solver); a successful one also
 # through assignment; every step queries 2n keys.
-def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse):
+def _algo(ph, b, kind, k):
+    return ALGO_BYTES[ph](b, kind, k) if ph == "query" else ALGO_BYTES[ph](b, kind)
+
+
+def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse, k=3):
     attempts = max(1, phases.get("hash_hist", (0, 0))[1])
     units = {"hash_hist": n * attempts, "scatter": n * attempts, "incidence": n * attempts,
              "peel": n * attempts, "lge": n * attempts, "assign": n * steps, "query": 2 * n * steps}
@@ -426,7 +433,7 @@ def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse):
             kb += 16.0 + (0 if kind == "filter" else 8.0)
         per_phase[ph] = {"ms_total": round(ms, 3), "kernels": cnt, "passes": passes[ph],
                          "ms_per_pass": round(ms / passes[ph], 4), "share": round(ms / total, 4),
-                         "achieved_gbs": round(ALGO_BYTES[ph](b, kind) * units[ph] / (ms * 1e-3) / 1e9, 2),
+                         "achieved_gbs": round(_algo(ph, b, kind, k) * units[ph] / (ms * 1e-3) / 1e9, 2),
                          "kernel_model_gbs": round(kb * units[ph] / (ms * 1e-3) / 1e9, 2)}
     dom = max(per_phase, key=lambda k: per_phase[k]["share"]) if per_phase else None
     roof = None
@@ -435,7 +442,7 @@ def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse):
         kb = KERNEL_BYTES[dom](b, kind) + (16.0 + (0 if kind == "filter" else 8.0) if dom == "scatter" and fuse else 0)
         roof = {"bound": "hbm", "kernel": dom, "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": round(d["achieved_gbs"] / hbm, 4), "traffic": TRAFFIC.get((workload, dom)),
-                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_unit": ALGO_BYTES[dom](b, kind),
+                "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_unit": _algo(dom, b, kind, k),
                 "kernel_model": {"bytes_per_unit": kb, "achieved": d["kernel_model_gbs"],
                                  "frac": round(d["kernel_model_gbs"] / hbm, 4)}}
     return per_phase, dom, roof
@@ -624,11 +631,12 @@ def measure_c4(steps: int, warmup: int, count: int = 4096) -> dict:
     }
 
 
-def random_sector_roofline(qps: float, b: int, kind: str, hbm: float, peak_kind: str) -> dict:
-    """A query against a data array larger than L2: three random 32-byte
-    sectors from HBM per key, plus its 8-byte key and its output."""
-    per_q = ALGO_BYTES["query"](b, kind)
-    sectors = 3 * qps
+def random_sector_roofline(qps: float, b: int, kind: str, hbm: float, peak_kind: str, k: int = 3) -> dict:
+    """A query against a data array larger than L2: k random 32-byte sectors
+    from HBM per key (k = 3, or 4 for 4-uniform fuse graphs), plus its 8-byte
+    key and its output."""
+    per_q = ALGO_BYTES["query"](b, kind, k)
+    sectors = k * qps
     return {"bound": "hbm", "unit": "GB/s", "achieved": round(per_q * qps / 1e9, 2), "peak": hbm,
             "frac": round(per_q * qps / 1e9 / hbm, 4), "peak_source": f"{peak_kind} hbm_gbs",
             "sectors_per_s": round(sectors / 1e9, 3), "sector_peak_per_s": round(hbm / 32, 3),
@@ -646,11 +654,11 @@ def sector_rate(table_bytes: int) -> dict:
                                          f"table (random 4-byte loads, one 32-byte sector each)"}
 
 
-def sector_roofline(qps: float, table_bytes: int, bound: str) -> dict:
-    """Three random sectors per query against the device's measured random-
-    sector rate for a table the size of the data array."""
+def sector_roofline(qps: float, table_bytes: int, bound: str, k: int = 3) -> dict:
+    """k random sectors per query against the device's measured random-sector
+    rate for a table the size of the data array."""
     pk = sector_rate(table_bytes)
-    got = 3 * qps
+    got = k * qps
     return {"bound": bound, "unit": "G sectors/s", "achieved": round(got / 1e9, 3),
             "peak": round(pk["sectors_per_s"] / 1e9, 3), "frac": round(got / pk["sectors_per_s"], 4),
             "peak_source": pk["source"], "data_bytes": int(table_bytes)}

@@ -95,6 +95,10 @@ typedef struct {
                                 cells per shard), with a per-shard pool that grows
                                 with the shard (see VF_ECAPACITY under vf_build) */
     int fuse_solver;         /* VF_SOLVER_FLOW (default), VF_SOLVER_ROUNDS or VF_SOLVER_WAVE */
+    int arity;               /* vertices per edge of a fuse-regime structure: 3 (default) or 4
+                                (4-uniform fuse graphs, Sec. 4.2 with k = 4: one more probe per
+                                query for less space; solved by VF_SOLVER_ROUNDS). The LGE and
+                                MWHC regimes are 3-uniform whatever this says. */
 } vf_params;
 
 /* Geometry and outcome of a built structure. */
@@ -120,6 +124,7 @@ typedef struct {
     uint64_t rounds;         /* fuse regime, VF_SOLVER_ROUNDS and VF_SOLVER_WAVE: synchronous
                                 peeling rounds of the last attempt (wave: grid-wide rounds plus
                                 the most rounds of a shard), summed over shard groups; 0 otherwise */
+    int k;                   /* vertices per edge: 3, or 4 for a 4-uniform fuse graph */
 } vf_info;
 
 void vf_params_default(vf_params *p);
@@ -170,7 +175,7 @@ vf_status vf_build_resumable(const void *keys, const uint64_t *offsets, const vo
                              uint32_t max_groups, void *stream, vf_struct **out);
 
 /* Serialized form: a 4096-byte header of little-endian fields (magic
- * "VFSTORE1", version 1, the vf_info of the build, group progress, digests)
+ * "VFSTORE1", version 2, the vf_info of the build, group progress, digests)
  * followed at byte 4096 by the data array in its device layout (shard s owns
  * cells [s*cells, (s+1)*cells); b in {8,16,32} native, else a bit array plus
  * one pad word), so a file can be mapped and its cells read in place.

@@ -21,11 +21,16 @@
  *   shard bits         pinned (Table 1 shard counts; eq. dupmwhc worked example,
  *                      through the planner in MWHC mode)
  *   geometry           pinned (space overhead of Sec. 5; closed forms; MWHC's
- *                      23% overhead and 3-partite cells)
+ *                      23% overhead and 3-partite cells); for 4-uniform fuse
+ *                      graphs the expansion factor and segment size are
+ *                      PARITY UNPINNED (the paper prints no arity-4 values;
+ *                      Graf and Lemire's arity-4 estimates are used as they
+ *                      stand), the rest of the k = 4 construction is pinned
  *   MWHC edges         pinned (one vertex per part, uniform; duplicate rate
  *                      against m^2 / (2 (cm/3)^3) of Sec. 4.1)
- *   peel               pinned (brute-force 2-core on tiny hypergraphs)
- *   GF(2) solve        pinned (brute force over all assignments on tiny systems)
+ *   peel               pinned (brute-force 2-core on tiny 3- and 4-hypergraphs)
+ *   GF(2) solve        pinned (brute force over all assignments on tiny systems,
+ *                      3 and 4 variables per equation)
  *   build / query      pinned (Problem 1: every key decodes to its value;
  *                      Problem 2: no false negatives, FPR ~ 2^-b)
  */

@@ -42,7 +42,7 @@ class VfParams(C.Structure):
         ("kind", C.c_int), ("b", C.c_int), ("key_kind", C.c_int), ("mode", C.c_int),
         ("max_retries", C.c_int), ("seed", C.c_uint64), ("eps", C.c_double), ("eta", C.c_double),
         ("lge_threshold", C.c_uint64), ("lge_target", C.c_uint64), ("lge_max_shard", C.c_uint64),
-        ("fuse_solver", C.c_int),
+        ("fuse_solver", C.c_int), ("arity", C.c_int),
     ]
 
 
@@ -54,6 +54,7 @@ class VfInfo(C.Structure):
         ("seg", C.c_uint64), ("l", C.c_uint64), ("T", C.c_uint64), ("cells", C.c_uint64),
         ("total_cells", C.c_uint64), ("data_bytes", C.c_uint64), ("seed", C.c_uint64),
         ("retries", C.c_int), ("peeled", C.c_uint64), ("core", C.c_uint64), ("rounds", C.c_uint64),
+        ("k", C.c_int),
     ]
 
     def as_dict(self):

@@ -180,11 +180,11 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const uint64_t* __restr
         if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;  // dropped duplicate
         uint32_t s = shard_of_edge(start, S, e);
         uint32_t el = uint32_t(e - start[s]);
-        uint64_t v[3];
+        uint64_t v[4];
         edge_of(g, __ldg(loc + e), v);
         uint64_t base = uint64_t(s) * g.cells;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
+        const int kk = g.k == 4 ? 4 : 3;
+        for (int k = 0; k < kk; k++) {
             uint32_t* w = W + base + v[k];
             uint32_t old = atomicAdd(w, 1u);
             atomicXor(w, el << 5);

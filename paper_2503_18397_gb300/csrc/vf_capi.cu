@@ -179,7 +179,13 @@ void plan_h(const vf_params& p, uint64_t n, vf_info& in) {
     }
     const bool lge = p.mode == VF_MODE_LGE || (p.mode == VF_MODE_AUTO && n < p.lge_threshold);
     in.regime = lge ? VF_REGIME_LGE : VF_REGIME_FUSE;
-    if (!lge) {
+    if (!lge && p.arity == 4) {
+        // 4-uniform fuse graphs: Sec. 4.2's duplicate-edge estimate with k = 4,
+        // exp(-m / (2 c s^3)), never binds, so eq. (logballsbins) sets the shards
+        in.h_bb = h_ballsbins(n, p.eps);
+        in.h_dup = -1;
+        in.h = in.h_bb;
+    } else if (!lge) {
         in.h_bb = h_ballsbins(n, p.eps);
         in.h_dup = h_dupfuse(n, p.eta, 1.105);
         in.h = std::min(in.h_bb, in.h_dup);
@@ -208,6 +214,19 @@ void geometry(vf_info& in) {
         in.seg = in.l = in.T = 0;
         uint64_t cells = uint64_t(std::ceil(in.c * Mf));
         in.cells = std::max<uint64_t>(cells, 32);
+    } else if (in.k == 4) {
+        // 4-uniform fuse graph (Sec. 4.2, l + 3 segments): the paper gives no
+        // arity-4 parameters; Graf and Lemire's arity-4 estimates as they stand
+        const double c = 0.77 + 0.305 * std::log(600000.0) / std::log(std::max(Mf, 2.0));
+        in.c = std::max(1.075, c);
+        double lg = std::floor(std::log(Mf) / std::log(2.91) - 0.5);
+        lg = std::min(32.0, std::max(0.0, lg));
+        in.lg_seg = int(lg);
+        in.seg = uint64_t(1) << in.lg_seg;
+        uint64_t T = uint64_t(std::ceil(in.c * Mf / double(in.seg)));
+        in.T = std::max<uint64_t>(T, 4);
+        in.l = in.T - 3;
+        in.cells = in.T * in.seg;
     } else {
         double lg;
         if (in.h > 0 && in.M >= 10000000ull) {
@@ -247,6 +266,7 @@ vf::Geom make_geom(const vf_info& in, int fpb = 0, int fps = 0) {
     g.kind = in.kind;
     g.fpb = fpb;
     g.fps = fps;
+    g.k = in.k == 4 ? 4 : 3;
     return g;
 }
 
@@ -316,7 +336,7 @@ vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc
                        DevBuf* claimed_out) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
-    DevBuf W, claimed, f0, f1, rec, roff, ctr;
+    DevBuf W, claimed, f0, f1, rec, rec3, roff, ctr;
     VF_CK(W.alloc(V * 4, st));
     VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
     VF_CK(claimed.alloc(((n + 31) / 32) * 4, st));
@@ -327,6 +347,7 @@ vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc
     VF_CK(f0.alloc(V * 8, st));
     VF_CK(f1.alloc(V * 8, st));
     VF_CK(rec.alloc(std::max<uint64_t>(n, 1) * 16, st));
+    if (g.k == 4) VF_CK(rec3.alloc(std::max<uint64_t>(n, 1) * 4, st));
     const uint32_t round_cap = uint32_t(std::min<uint64_t>(n + 1, uint64_t(1) << 22));
     VF_CK(roff.alloc((uint64_t(round_cap) + 1) * 4, st));
     VF_CK(cudaMemsetAsync(roff.p, 0, 4, st));
@@ -348,6 +369,7 @@ vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc
     a.front[1] = f1.as<uint2>();
     a.front_cap = V;
     a.rec = rec.as<uint4>();
+    a.rec3 = rec3.as<uint32_t>();
     a.round_off = roff.as<uint32_t>();
     a.round_cap = round_cap;
     a.ctr = c32;
@@ -612,17 +634,19 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32
         DevBuf claimed;
         const bool dedup = pass == 0;
         vf_status rs = VF_EINVAL;
-        bool fallback = solver == VF_SOLVER_WAVE && !vf::wave_eligible(g, uint32_t(in.shards));
-        if (solver == VF_SOLVER_WAVE && !fallback) {
+        // 4-uniform fuse graphs are peeled by the round solver
+        const int use = g.k == 4 ? VF_SOLVER_ROUNDS : solver;
+        bool fallback = use == VF_SOLVER_WAVE && !vf::wave_eligible(g, uint32_t(in.shards));
+        if (use == VF_SOLVER_WAVE && !fallback) {
             rs = solve_wave(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base, drop.as<uint32_t>(),
                             ndrop, dedup ? &claimed : nullptr, &fallback);
             if (fallback) claimed.release();
         }
-        if (solver == VF_SOLVER_FLOW || fallback) {
+        if (use == VF_SOLVER_FLOW || fallback) {
             *rounds_out = 0;
             rs = solve_flow(in, g, loc, val, start, data, st, peeled, cell_base,
                             drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
-        } else if (solver == VF_SOLVER_ROUNDS) {
+        } else if (use == VF_SOLVER_ROUNDS) {
             rs = solve_rounds(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base,
                               drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
         }
@@ -788,6 +812,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
         in.seed = it.seed + attempt[pending[j]];
         in.retries = int(attempt[pending[j]]);
         plan_h(pi, it.n, in);
+        in.k = (in.regime == VF_REGIME_FUSE && pi.arity == 4) ? 4 : 3;
         key_off[j + 1] = key_off[j] + it.n;
     }
     const uint64_t total = key_off[P];
@@ -1034,7 +1059,7 @@ uint64_t params_digest(const vf_params& p, uint64_t group_keys) {
     std::memcpy(&e, &p.eps, 8);
     std::memcpy(&t, &p.eta, 8);
     const uint64_t w[] = {uint64_t(p.kind), uint64_t(p.b), uint64_t(p.key_kind), uint64_t(p.mode), e, t,
-                          p.lge_threshold, p.lge_target, p.lge_max_shard, group_keys};
+                          p.lge_threshold, p.lge_target, p.lge_max_shard, group_keys, uint64_t(p.arity)};
     return digest_words(w, sizeof w / sizeof w[0]);
 }
 
@@ -1077,6 +1102,7 @@ struct Checkpoint {
                               old.info.n == in.n && old.info.kind == in.kind && old.info.b == in.b &&
                               old.info.regime == in.regime && old.info.h == in.h && old.info.M == in.M &&
                               old.info.cells == in.cells && old.info.data_bytes == in.data_bytes &&
+                              old.info.k == in.k &&
                               old.counts_digest == cd && old.params_digest == pd &&
                               old.groups_total == group.size() - 1 && old.key_kind == p.key_kind &&
                               old.groups_done < old.groups_total;
@@ -1174,8 +1200,8 @@ vf_status build_impl(const void* keys, const uint64_t* offsets, const void* valu
     if (p.kind == VF_FUNC && n > 0 && !values) return fail(VF_EINVAL, "a function needs values");
     if (!(p.eps > 0.0) || !(p.eta > 0.0 && p.eta < 1.0) || p.max_retries < 0 || p.lge_target == 0 ||
         p.lge_max_shard < 2 || p.mode < VF_MODE_AUTO || p.mode > VF_MODE_MWHC || p.fuse_solver < VF_SOLVER_FLOW ||
-        p.fuse_solver > VF_SOLVER_WAVE)
-        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes / mode / fuse solver");
+        p.fuse_solver > VF_SOLVER_WAVE || (p.arity != 3 && p.arity != 4))
+        return fail(VF_EINVAL, "bad eps / eta / retries / LGE sizes / mode / fuse solver / arity");
     for (const auto& pw : {std::make_pair(keys, "keys"), std::make_pair(static_cast<const void*>(offsets), "offsets"),
                            std::make_pair(values, "values")}) {
         const vf_status cs = vf::check_here(pw.first, pw.second);
@@ -1219,6 +1245,7 @@ vf_status build_impl(const void* keys, const uint64_t* offsets, const void* valu
         in.seed = p.seed + uint64_t(attempt);
         in.retries = attempt;
         plan_h(p, n, in);
+        in.k = (in.regime == VF_REGIME_FUSE && p.arity == 4) ? 4 : 3;
         std::vector<uint32_t> counts;
         for (;;) {
             in.shards = uint64_t(1) << in.h;
@@ -1489,6 +1516,7 @@ void vf_params_default(vf_params* p) {
     p->lge_target = 16384;
     p->lge_max_shard = 24576;
     p->fuse_solver = VF_SOLVER_FLOW;
+    p->arity = 3;
 }
 
 const char* vf_last_error(void) { return g_last_error.c_str(); }
@@ -1502,7 +1530,9 @@ vf_status vf_plan(const vf_params* p, uint64_t n, uint64_t M, vf_info* out) {
     in.kind = p->kind;
     in.b = p->b;
     in.seed = p->seed;
+    if (p->arity != 3 && p->arity != 4) return fail(VF_EINVAL, "vf_plan: arity must be 3 or 4");
     plan_h(*p, n, in);
+    in.k = (in.regime == VF_REGIME_FUSE && p->arity == 4) ? 4 : 3;
     in.shards = uint64_t(1) << in.h;
     in.M = M;
     geometry(in);
@@ -1769,8 +1799,8 @@ vf_status vf_build_batch(const vf_batch_item* items, uint32_t count, const vf_pa
     g_last_error.clear();
     if (!common || !out || (count > 0 && !items)) return fail(VF_EINVAL, "vf_build_batch: NULL argument");
     if (common->mode < VF_MODE_AUTO || common->mode > VF_MODE_MWHC || common->fuse_solver < VF_SOLVER_FLOW ||
-        common->fuse_solver > VF_SOLVER_WAVE)
-        return fail(VF_EINVAL, "vf_build_batch: bad mode or fuse solver");
+        common->fuse_solver > VF_SOLVER_WAVE || (common->arity != 3 && common->arity != 4))
+        return fail(VF_EINVAL, "vf_build_batch: bad mode, fuse solver or arity");
     vf_batch_opts o;
     if (opts) o = *opts; else vf_batch_opts_default(&o);
     if (o.lge_target == 0) return fail(VF_EINVAL, "vf_build_batch: lge_target must be positive");

@@ -51,6 +51,7 @@ struct Geom {
     int32_t kind;         // 0 function, 1 filter
     int32_t fpb;          // filter: bits of the full fingerprint (0: b); a structure wider than 32 bits
     int32_t fps;          //   is built as 32-bit slices, this one holding fingerprint bits [fps, fps + b)
+    int32_t k;            // vertices per edge: 3, or 4 (4-uniform fuse graph)
 };
 
 // ----------------------------------------------------------------- signatures
@@ -112,11 +113,12 @@ __device__ __forceinline__ uint64_t local_of(const Sig& s, int h) {
     return h == 0 ? s.hi : (s.hi << h) | (s.lo >> (64 - h));
 }
 
-// Vertices of a key's 3-hyperedge inside its shard.
+// Vertices of a key's hyperedge inside its shard (g.k of them, 3 or 4).
 //  fuse: first vertex by fixed-point inversion of the local signature over
-//  l*seg (monotone), then one vertex in each of the next two segments;
+//  l*seg (monotone), then one vertex in each of the next k-1 segments (the
+//  fourth offset of a 4-uniform fuse graph from a second remix);
 //  LGE regime: three distinct uniform vertices over the shard's cells.
-__device__ __forceinline__ void edge_of(const Geom& g, uint64_t local, uint64_t v[3]) {
+__device__ __forceinline__ void edge_of(const Geom& g, uint64_t local, uint64_t v[4]) {
     if (g.regime == kRegimeFuse) {
         uint64_t v0 = mulhi(local, g.span);
         uint64_t s = v0 >> g.lg_seg;
@@ -125,6 +127,7 @@ __device__ __forceinline__ void edge_of(const Geom& g, uint64_t local, uint64_t 
         v[0] = v0;
         v[1] = ((s + 1) << g.lg_seg) + (r & mask);
         v[2] = ((s + 2) << g.lg_seg) + ((r >> 32) & mask);
+        if (g.k == 4) v[3] = ((s + 3) << g.lg_seg) + (mix64(local ^ kEdgeSalt2) & mask);
     } else if (g.regime == kRegimeMwhc) {
         // MWHC (Sec. 4.1, k-partite): one uniform vertex in each third of the shard
         const uint64_t P = g.span;

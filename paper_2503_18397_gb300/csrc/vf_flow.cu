@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
         if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
         const uint32_t s = flow_shard_of_edge(start, S, e);
         const uint32_t inc = 1u + (uint32_t(e - __ldg(start + s)) << 5);
-        uint64_t v[3];
+        uint64_t v[4];
         edge_of(g, __ldg(loc + e), v);
         const uint64_t base = uint64_t(s) * g.cells;
         uint32_t old[3];
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
                     const uint32_t base = s * cells;
                     const unsigned long long st0 = __ldg(a.start + s);
                     const uint32_t dec = 1u + (uint32_t(e - st0) << 5);
-                    uint64_t vv[3];
+                    uint64_t vv[4];
                     edge_of(a.g, local, vv);
                     const uint32_t lv = v - base;
                     const uint32_t c0 = uint32_t(vv[0]), c1 = uint32_t(vv[1]), c2 = uint32_t(vv[2]);

@@ -75,6 +75,7 @@ struct FuseSolveArgs {
     uint2* front[2];                  // frontier entries (vertex, edge)
     uint64_t front_cap;
     uint4* rec;                       // assignment records, one per peeled edge
+    uint32_t* rec3;                   // 4-uniform: each record's third other vertex (NULL when k = 3)
     uint32_t* round_off;              // round r's records: rec[round_off[r] .. round_off[r+1])
     uint32_t round_cap;
     uint32_t* ctr;                    // [0],[1] frontier sizes, [2] records, [3] rounds

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
         for (uint32_t i = tid; i < pw; i += T) sm[i] = 0;
         __syncthreads();
         for (uint32_t e = tid; e < m; e += T) {
-            uint64_t v[3];
+            uint64_t v[4];
             edge_of(gg, __ldg(a.loc + e0 + e), v);
 #pragma unroll
             for (int k = 0; k < 3; k++) {

@@ -77,8 +77,10 @@ __global__ void __launch_bounds__(kPT, 1) k_peel2(FuseSolveArgs a) {
             const uint64_t i = i0 + lane;
             bool peel = false;
             uint4 rec = make_uint4(0, 0, 0, 0);
-            uint2 push0 = make_uint2(0, 0), push1 = make_uint2(0, 0);
+            uint32_t other3 = 0;
+            uint2 push[3] = {make_uint2(0, 0), make_uint2(0, 0), make_uint2(0, 0)};
             uint32_t np = 0;
+            const int kk = a.g.k == 4 ? 4 : 3;
             if (i < sz) {
                 const uint2 fe = __ldcg(F + i);
                 const uint32_t v = fe.x, e = fe.y;
@@ -91,43 +93,42 @@ __global__ void __launch_bounds__(kPT, 1) k_peel2(FuseSolveArgs a) {
                     const uint32_t base = s * cells;
                     const unsigned long long st0 = shard_start(a, sst, s);
                     const uint32_t el = uint32_t(e - st0);
-                    uint64_t vv[3];
+                    uint64_t vv[4];
                     edge_of(a.g, local, vv);
                     const uint32_t lv = v - base;
-                    const uint32_t side = (vv[0] == lv) ? 0u : (vv[1] == lv) ? 1u : 2u;
-                    uint32_t other[2];
+                    uint32_t side = 0;
+                    for (int k = 0; k < kk; k++)
+                        if (uint32_t(vv[k]) == lv) side = uint32_t(k);
+                    uint32_t other[3] = {0, 0, 0};
                     int o = 0;
-#pragma unroll
-                    for (int k = 0; k < 3; k++)
+                    for (int k = 0; k < kk; k++)
                         if (uint32_t(k) != side) other[o++] = base + uint32_t(vv[k]);
-                    uint32_t old[2] = {__ldcg(a.W + other[0]), __ldcg(a.W + other[1])};
-#pragma unroll
-                    for (int k = 0; k < 2; k++) {
+                    for (int k = 0; k < kk - 1; k++) {
                         uint32_t* wp = a.W + other[k];
+                        uint32_t old = __ldcg(wp);
                         for (;;) {
-                            const uint32_t nw = ((old[k] ^ (el << 5)) & ~31u) | ((old[k] & 31u) - 1u);
-                            const uint32_t got = atomicCAS(wp, old[k], nw);
-                            if (got == old[k]) {
-                                if ((nw & 31u) == 1u) {
-                                    const uint2 pe = make_uint2(other[k], uint32_t(st0 + (nw >> 5)));
-                                    if (np == 0) push0 = pe; else push1 = pe;
-                                    np++;
-                                }
+                            const uint32_t nw = ((old ^ (el << 5)) & ~31u) | ((old & 31u) - 1u);
+                            const uint32_t got = atomicCAS(wp, old, nw);
+                            if (got == old) {
+                                if ((nw & 31u) == 1u) push[np++] = make_uint2(other[k], uint32_t(st0 + (nw >> 5)));
                                 break;
                             }
-                            old[k] = got;
+                            old = got;
                         }
                     }
                     rec = make_uint4(v, other[0], other[1], a.val ? value : fingerprint_slice(local, a.g.b, a.g.fpb, a.g.fps));
+                    other3 = other[2];
                 }
             }
             const uint32_t slot = warp_reserve(&a.ctr[2], peel ? 1u : 0u);
-            if (peel) a.rec[slot] = rec;
+            if (peel) {
+                a.rec[slot] = rec;
+                if (a.rec3) a.rec3[slot] = other3;
+            }
             const uint32_t fs = warp_reserve(&a.ctr[nxt], np);
             if (np) {
                 if (fs + np <= a.front_cap) {
-                    G[fs] = push0;
-                    if (np > 1) G[fs + 1] = push1;
+                    for (uint32_t k = 0; k < np; k++) G[fs + k] = push[k];
                 } else {
                     atomicOr(a.err, kErrFrontier);
                 }
@@ -153,8 +154,9 @@ __global__ void __launch_bounds__(kPT, 1) k_assign2(FuseSolveArgs a) {
         const uint32_t lo = __ldg(a.round_off + r), hi = __ldg(a.round_off + r + 1);
         for (uint64_t i = lo + tid; i < hi; i += nthreads) {
             const uint4 rec = __ldg(a.rec + i);
-            const uint32_t x =
+            uint32_t x =
                 rec.w ^ cell_get_cg(a.data, b, a.cell_base + rec.y) ^ cell_get_cg(a.data, b, a.cell_base + rec.z);
+            if (a.rec3) x ^= cell_get_cg(a.data, b, a.cell_base + __ldg(a.rec3 + i));
             cell_put_zero(a.data, b, a.cell_base + rec.x, x);
         }
         if (r > 0 && !bar2(a.bar, nblocks, a.err, [] {})) return;

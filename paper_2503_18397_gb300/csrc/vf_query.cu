@@ -20,14 +20,15 @@ __device__ __forceinline__ uint32_t cell_q(const uint8_t* data, int b, uint64_t 
     else return cell_get_nc(data, b, i);
 }
 
-template <int WIDTH, bool FILTER, bool BYTES>
+// K: vertices per edge (3, or 4 for a 4-uniform fuse graph).
+template <int WIDTH, bool FILTER, bool BYTES, int K>
 __global__ void __launch_bounds__(kQThreads) k_query(const void* __restrict__ keys, const uint64_t* __restrict__ offs,
                                                      uint64_t m, Geom g, const uint8_t* __restrict__ data,
                                                      void* __restrict__ out) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const uint64_t total = BYTES ? __ldg(offs + m) : 0;
     for (uint64_t i0 = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i0 < m; i0 += stride * kQ) {
-        uint64_t idx[kQ], loc[kQ], cell[kQ][3];
+        uint64_t idx[kQ], loc[kQ], cell[kQ][K];
         bool ok[kQ];
 #pragma unroll
         for (int k = 0; k < kQ; k++) {
@@ -45,21 +46,21 @@ __global__ void __launch_bounds__(kQThreads) k_query(const void* __restrict__ ke
             }
             uint64_t base = shard_of(s, g.h) * g.cells;
             loc[k] = local_of(s, g.h);
-            uint64_t v[3];
+            uint64_t v[4];
             edge_of(g, loc[k], v);
-            cell[k][0] = base + v[0];
-            cell[k][1] = base + v[1];
-            cell[k][2] = base + v[2];
+#pragma unroll
+            for (int j = 0; j < K; j++) cell[k][j] = base + v[j];
         }
-        uint32_t x[kQ][3];
+        uint32_t x[kQ][K];
 #pragma unroll
         for (int k = 0; k < kQ; k++)
 #pragma unroll
-            for (int j = 0; j < 3; j++) x[k][j] = ok[k] ? cell_q<WIDTH>(data, g.b, cell[k][j]) : 0u;
+            for (int j = 0; j < K; j++) x[k][j] = ok[k] ? cell_q<WIDTH>(data, g.b, cell[k][j]) : 0u;
 #pragma unroll
         for (int k = 0; k < kQ; k++) {
             if (!ok[k]) continue;
             uint32_t r = x[k][0] ^ x[k][1] ^ x[k][2];
+            if constexpr (K == 4) r ^= x[k][3];
             if constexpr (FILTER) {
                 static_cast<uint8_t*>(out)[idx[k]] = uint8_t(r == fingerprint(loc[k], g.b));
             } else {
@@ -78,10 +79,16 @@ static void launch_q(bool bytes, const void* keys, const uint64_t* offs, uint64_
     uint64_t cap = uint64_t(num_sms()) * 16;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    if (bytes)
-        k_query<WIDTH, FILTER, true><<<unsigned(blocks), kQThreads, 0, st>>>(keys, offs, m, g, data, out);
-    else
-        k_query<WIDTH, FILTER, false><<<unsigned(blocks), kQThreads, 0, st>>>(keys, offs, m, g, data, out);
+    if (g.k == 4) {
+        if (bytes)
+            k_query<WIDTH, FILTER, true, 4><<<unsigned(blocks), kQThreads, 0, st>>>(keys, offs, m, g, data, out);
+        else
+            k_query<WIDTH, FILTER, false, 4><<<unsigned(blocks), kQThreads, 0, st>>>(keys, offs, m, g, data, out);
+    } else if (bytes) {
+        k_query<WIDTH, FILTER, true, 3><<<unsigned(blocks), kQThreads, 0, st>>>(keys, offs, m, g, data, out);
+    } else {
+        k_query<WIDTH, FILTER, false, 3><<<unsigned(blocks), kQThreads, 0, st>>>(keys, offs, m, g, data, out);
+    }
 }
 
 template <bool FILTER>
@@ -122,17 +129,19 @@ __global__ void __launch_bounds__(kQThreads) k_query_batch(const QueryReq* __res
         const Sig s = sig_u64(__ldg(r.keys + i), r.g.kh, r.g.kl);
         const uint64_t base = shard_of(s, r.g.h) * r.g.cells;
         const uint64_t local = local_of(s, r.g.h);
-        uint64_t v[3];
+        uint64_t v[4];
         edge_of(r.g, local, v);
         if (r.g.b > 32) {  // values wider than 32 bits
-            const uint64_t y = cell_get64(r.data, r.g.b, base + v[0]) ^ cell_get64(r.data, r.g.b, base + v[1]) ^
-                               cell_get64(r.data, r.g.b, base + v[2]);
+            uint64_t y = cell_get64(r.data, r.g.b, base + v[0]) ^ cell_get64(r.data, r.g.b, base + v[1]) ^
+                         cell_get64(r.data, r.g.b, base + v[2]);
+            if (r.g.k == 4) y ^= cell_get64(r.data, r.g.b, base + v[3]);
             if (r.g.kind == 1) static_cast<uint8_t*>(r.out)[i] = uint8_t(y == fingerprint64(local, r.g.b));
             else static_cast<uint64_t*>(r.out)[i] = y;
             continue;
         }
-        const uint32_t x = cell_get_nc(r.data, r.g.b, base + v[0]) ^ cell_get_nc(r.data, r.g.b, base + v[1]) ^
-                           cell_get_nc(r.data, r.g.b, base + v[2]);
+        uint32_t x = cell_get_nc(r.data, r.g.b, base + v[0]) ^ cell_get_nc(r.data, r.g.b, base + v[1]) ^
+                     cell_get_nc(r.data, r.g.b, base + v[2]);
+        if (r.g.k == 4) x ^= cell_get_nc(r.data, r.g.b, base + v[3]);
         if (r.g.kind == 1) static_cast<uint8_t*>(r.out)[i] = uint8_t(x == fingerprint(local, r.g.b));
         else if (r.g.b <= 8) static_cast<uint8_t*>(r.out)[i] = uint8_t(x);
         else if (r.g.b <= 16) static_cast<uint16_t*>(r.out)[i] = uint16_t(x);

@@ -40,7 +40,7 @@ uint32_t get_u32(const uint8_t* p) {
 }
 
 const char kMagic[8] = {'V', 'F', 'S', 'T', 'O', 'R', 'E', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;  // 2: the arity k follows the key kind
 
 // Sequential field writer / reader over the header.
 struct Cursor {
@@ -86,6 +86,7 @@ void store_encode(const StoreHeader& h, uint8_t* out) {
     c.u64(i.seg), c.u64(i.l), c.u64(i.T), c.u64(i.cells), c.u64(i.total_cells), c.u64(i.data_bytes);
     c.u64(i.seed), c.i32(i.retries), c.u64(i.peeled), c.u64(i.core), c.u64(i.rounds);
     c.u64(h.dropped), c.i32(h.key_kind);
+    c.i32(i.k);
 }
 
 static uint64_t data_bytes_of(const vf_info& i) {
@@ -112,6 +113,7 @@ bool store_decode(const uint8_t* in, uint64_t avail, StoreHeader& h) {
     i.data_bytes = c.ru64();
     i.seed = c.ru64(), i.retries = c.ri32(), i.peeled = c.ru64(), i.core = c.ru64(), i.rounds = c.ru64();
     h.dropped = c.ru64(), h.key_kind = c.ri32();
+    i.k = c.ri32();
     // consistency: a corrupt or foreign file is rejected, never half-used
     if (get_u64(in + 24) != i.data_bytes) return false;
     if (i.kind != VF_FUNC && i.kind != VF_FILTER) return false;
@@ -119,8 +121,9 @@ bool store_decode(const uint8_t* in, uint64_t avail, StoreHeader& h) {
     if (i.regime != VF_REGIME_FUSE && i.regime != VF_REGIME_LGE && i.regime != VF_REGIME_MWHC) return false;
     if (i.shards != (uint64_t(1) << i.h) || i.cells == 0 || i.cells >= (uint64_t(1) << 32)) return false;
     if (i.total_cells != i.shards * i.cells || i.data_bytes != data_bytes_of(i)) return false;
+    if (i.k != 3 && !(i.k == 4 && i.regime == VF_REGIME_FUSE)) return false;
     if (i.regime == VF_REGIME_FUSE &&
-        (i.lg_seg < 0 || i.lg_seg > 31 || i.seg != (uint64_t(1) << i.lg_seg) || i.T != i.l + 2 ||
+        (i.lg_seg < 0 || i.lg_seg > 31 || i.seg != (uint64_t(1) << i.lg_seg) || i.T != i.l + uint64_t(i.k) - 1 ||
          i.cells != i.T * i.seg))
         return false;
     if (i.regime == VF_REGIME_MWHC && i.cells % 3 != 0) return false;

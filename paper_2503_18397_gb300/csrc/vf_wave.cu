@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_wave_incidence(WaveArgs a) {
         if (a.drop && ((__ldg(a.drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
         const uint32_t s = wave_shard_of(a.start, a.S, e);
         const uint64_t local = __ldg(a.loc + e);
-        uint64_t v[3];
+        uint64_t v[4];
         edge_of(a.g, local, v);
         const uint32_t x = a.val ? __ldg(a.val + e) : fingerprint_slice(local, a.g.b, a.g.fpb, a.g.fps);
         const uint32_t o0 = uint32_t(v[0]) & m, o1 = uint32_t(v[1]) & m, o2 = uint32_t(v[2]) & m;
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(256) k_wave_claimed(WaveArgs a, uint32_t* clai
                 c = true;
             } else {
                 const uint32_t s = wave_shard_of(a.start, a.S, e);
-                uint64_t v[3];
+                uint64_t v[4];
                 edge_of(a.g, __ldg(a.loc + e), v);
                 const uint64_t base = uint64_t(s) * a.g.cells;
                 uint32_t dmin = 31;
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(256) k_wave_claimed(WaveArgs a, uint32_t* clai
 // ---------------------------------------------------------------- launches
 
 bool wave_eligible(const Geom& g, uint32_t S) {
-    if (g.regime != kRegimeFuse || g.lg_seg < 1 || g.lg_seg > 26 || S > kWMaxShards) return false;
+    if (g.regime != kRegimeFuse || g.k != 3 || g.lg_seg < 1 || g.lg_seg > 26 || S > kWMaxShards) return false;
     const int vbits = 64 - 7 - 2 * g.lg_seg;
     return g.b <= vbits && g.cells < (uint64_t(1) << 31);
 }

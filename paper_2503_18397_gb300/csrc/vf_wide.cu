@@ -72,10 +72,11 @@ __global__ void __launch_bounds__(kWT) k_query_wide(const void* __restrict__ key
         }
         const uint64_t base = shard_of(s, g.h) * g.cells;
         const uint64_t local = local_of(s, g.h);
-        uint64_t v[3];
+        uint64_t v[4];
         edge_of(g, local, v);
-        const uint64_t x = cell_get64(data, g.b, base + v[0]) ^ cell_get64(data, g.b, base + v[1]) ^
-                           cell_get64(data, g.b, base + v[2]);
+        uint64_t x = cell_get64(data, g.b, base + v[0]) ^ cell_get64(data, g.b, base + v[1]) ^
+                     cell_get64(data, g.b, base + v[2]);
+        if (g.k == 4) x ^= cell_get64(data, g.b, base + v[3]);
         if (g.kind == 1) static_cast<uint8_t*>(out)[i] = uint8_t(x == fingerprint64(local, g.b));
         else static_cast<uint64_t*>(out)[i] = x;
     }

@@ -56,7 +56,8 @@ def _plan_pair(vf, orc, n, M, **kw):
     info = vf.vf_plan(n, M, p)
     op = orc.default_params(**kw)
     h, regime, h_bb, h_dup = orc.plan_h(op, n)
-    g = orc.geometry(regime, h, M, b=kw.get("b", 8))
+    k = 4 if kw.get("arity") == 4 and regime == orc.REGIME_FUSE else 3
+    g = orc.geometry(regime, h, M, b=kw.get("b", 8), k=k)
     return info, (h, regime, h_bb, h_dup), g
 
 
@@ -104,6 +105,23 @@ def test_plan_matches_oracle_mwhc(vf, orc):
     p = vf.vf_params_default(mode=7)
     with pytest.raises(vf.VFError):
         vf.vf_plan(10, 10, p)
+
+
+def test_plan_matches_oracle_arity4(vf, orc):
+    # 4-uniform fuse graphs: shard bits from eq. (logballsbins) alone, l + 3
+    # segments of the arity-4 size; the LGE regime stays 3-uniform
+    rng = np.random.default_rng(2)
+    ns = sorted(set([0, 1, 2, 1000, 800_000, 10**8, 10**12] + [int(10 ** x) for x in rng.uniform(0, 13, 200)]))
+    for n in ns:
+        info, (h, regime, h_bb, h_dup), _ = _plan_pair(vf, orc, n, 1, arity=4)
+        assert (info.h, info.regime, info.h_bb, info.h_dup) == (h, regime, h_bb, h_dup), n
+        M = int(n / (1 << h) + math.sqrt(max(n / (1 << h), 1)) * 3)
+        info, _, g = _plan_pair(vf, orc, n, M, arity=4)
+        assert info.k == (4 if regime == vf.REGIME_FUSE else 3)
+        for f in FIELDS:
+            assert getattr(info, f) == getattr(g, f), (n, f)
+    with pytest.raises(vf.VFError):
+        vf.vf_plan(10, 10, vf.vf_params_default(arity=5))
 
 
 def test_serialized_form_rejects_foreign_bytes(vf, tmp_path):

@@ -73,7 +73,7 @@ def check_build(vf, orc, keys, vals, offsets=None, n_other=20_000, **kw):
     st, oi, odata = orc.build(op, keys, vals, offsets=offsets)
     assert st == orc.OK
     for f in ("regime", "h", "h_bb", "h_dup", "shards", "M", "c", "lg_seg", "seg", "l", "T", "cells",
-              "total_cells", "data_bytes", "seed", "retries", "n_eff"):
+              "total_cells", "data_bytes", "seed", "retries", "n_eff", "k"):
         assert getattr(info, f) == getattr(oi, f), f
     if info.regime == vf.REGIME_FUSE:
         assert info.peeled == oi.peeled == info.n_eff
@@ -507,3 +507,79 @@ def test_query_host_buffers_pipelined(vf, orc, b, kind):
         got = res if isinstance(res, np.ndarray) else host(res)
         assert got.dtype == want.dtype and (got == want).all()
     s.free()
+
+
+# ------------------------------------------------ 4-uniform fuse graphs (k = 4)
+
+@pytest.mark.parametrize("b", [1, 8, 13, 16, 32])
+def test_fuse4_function(vf, orc, b):
+    n = 1_000_000
+    keys = synth.u64_keys(0, n, 71)
+    vals = synth.values(n, b, 71)
+    s, info, oi = check_build(vf, orc, keys, vals, b=b, mode=vf.MODE_FUSE, arity=4, seed=2, n_other=100_000)
+    assert info.k == oi.k == 4 and info.T == info.l + 3 and info.peeled == oi.peeled == n
+    assert info.rounds > 0  # the round solver peels 4-uniform graphs
+
+
+def test_fuse4_filter_sharded_and_strings(vf, orc):
+    n = 3_000_000
+    keys = synth.u64_keys(0, n, 72)
+    s, info, oi = check_build(vf, orc, keys, None, b=8, mode=vf.MODE_FUSE, arity=4, eps=0.01, seed=3,
+                              n_other=200_000)
+    assert info.k == 4 and info.h > 0 and info.h_dup == -1
+    other = synth.u64_keys(n, 2_000_000, 72)
+    fpr = host(s.query(dev(other))).mean()
+    assert abs(fpr - 2.0**-8) < 5 * math.sqrt(2.0**-8 / len(other))
+    data, offs = synth.byte_strings(0, 400_000, 73)
+    vals = synth.values(400_000, 16, 73)
+    check_build(vf, orc, data, vals, offsets=offs, b=16, mode=vf.MODE_FUSE, arity=4, eps=0.02, seed=1,
+                n_other=20_000)
+
+
+def test_fuse4_duplicates_retries_and_wide(vf, orc):
+    # duplicates are dropped (filter) or kept once (function pairs); a key with two
+    # values is VF_EDUP; retries equal the oracle's; 40-bit values in two slices
+    keys = with_repeats(500_000, 0.02, 74, triples=True)
+    s, info, oi = check_build(vf, orc, keys, None, mode=vf.MODE_FUSE, arity=4, seed=4, n_other=20_000)
+    assert info.n_eff == oi.n_eff == 500_000
+    dk, dv, _, _ = with_repeated_pairs(300_000, 0.01, 75, 8)
+    s, info, oi = check_build(vf, orc, dk, dv, mode=vf.MODE_FUSE, arity=4, seed=5, n_other=0)
+    assert info.n_eff == oi.n_eff == 300_000
+    bad = dv.copy()
+    first = {}
+    for i, k in enumerate(dk.tolist()):
+        if k in first:
+            bad[i] ^= 1
+            break
+        first[k] = i
+    with pytest.raises(vf.VFError) as e:
+        vf.vf_build(dev(dk), dev(bad), params=vf.vf_params_default(mode=vf.MODE_FUSE, arity=4))
+    assert e.value.status == 4
+    seen = 0
+    for seed in range(12):
+        keys = synth.u64_keys(0, 3000, 80 + seed)
+        vals = synth.values(3000, 8, 80 + seed)
+        s, info, oi = check_build(vf, orc, keys, vals, mode=vf.MODE_FUSE, arity=4, seed=seed, max_retries=40,
+                                  n_other=0)
+        seen += info.retries > 0
+    assert seen > 0  # small 4-uniform fuse graphs need retries, equal to the oracle's
+    keys = synth.u64_keys(0, 200_000, 76)
+    vals = synth.values(200_000, 40, 76)
+    check_build(vf, orc, keys, vals, b=40, mode=vf.MODE_FUSE, arity=4, seed=6, n_other=20_000)
+
+
+def test_fuse4_serialized_and_batched_queries(vf, orc):
+    n = 400_000
+    keys = synth.u64_keys(0, n, 77)
+    vals = synth.values(n, 8, 77)
+    s = vf.vf_build(dev(keys), dev(vals), params=vf.vf_params_default(mode=vf.MODE_FUSE, arity=4, seed=2))
+    t = vf.vf_deserialize(vf.vf_serialize(s))
+    assert t.info.k == 4 and (host(t.query(dev(keys))) == vals).all()
+    other = synth.u64_keys(n, 50_000, 77)
+    q = np.concatenate([keys[:50_000], other])
+    outs = vf.vf_query_batch([(s, dev(q), None)])
+    torch.cuda.synchronize()
+    assert (host(outs[0]) == orc.query(oracle_info(orc, s.info), vf.vf_export(s), q)).all()
+    assert (vf.vf_query(s, q) == host(outs[0])).all()  # host keys: the pipelined query
+    s.free()
+    t.free()
