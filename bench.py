@@ -346,6 +346,8 @@ def run_gpu(args):
     d2h = 2 * n * outh.element_size()
     e2e_b_ms, e2e_q_ms = reduce_max([statistics.mean(e2e_b), statistics.mean(e2e_q)], dist, "cuda")
 
+    # the host link bounds the end-to-end queries: every key crosses it once
+    h2d_gbs = host_to_device_gbs(torch)
     hbm, peak_kind = peaks()
     per_phase, dom, roof = phase_table(phases, n, args.steps, b, kind, hbm, peak_kind, args.workload,
                                        info.regime == vf.REGIME_FUSE, int(info.k))
@@ -374,7 +376,12 @@ def run_gpu(args):
         "build_ms": round(b_ms, 3),
         "query": {"gqps": round(qgps, 3), "ms_per_2n": round(q_ms, 3)},
         "e2e": {"value": round(e2e_ns, 4), "unit": "ns/key", "query_gqps": round(e2e_qgps, 3),
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "query_link_bound": {"h2d_gbs": round(h2d_gbs, 1),
+                                     "gqps": round(h2d_gbs / (key_bytes / n), 3),
+                                     "frac": round(e2e_qgps / (h2d_gbs / (key_bytes / n)), 4),
+                                     "what": "pinned host-to-device copy rate measured in this run, divided by "
+                                             "the bytes of one key: queries from host memory cannot go faster"}},
         "gpu_launches": int(launches),
         "phases": per_phase,
         "roofline": roof,
@@ -641,6 +648,23 @@ def random_sector_roofline(qps: float, b: int, kind: str, hbm: float, peak_kind:
             "frac": round(per_q * qps / 1e9 / hbm, 4), "peak_source": f"{peak_kind} hbm_gbs",
             "sectors_per_s": round(sectors / 1e9, 3), "sector_peak_per_s": round(hbm / 32, 3),
             "bytes_per_query": per_q}
+
+
+def host_to_device_gbs(torch) -> float:
+    """Pinned host-to-device copy bandwidth (GB/s), best of four 1 GiB copies."""
+    src = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    dst = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 0.0
+    for _ in range(4):
+        e0.record(st)
+        dst.copy_(src, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        best = max(best, (1 << 30) / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    del src, dst
+    return best
 
 
 def sector_rate(table_bytes: int) -> dict:

@@ -610,23 +610,33 @@ vf_status solve_wave(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
 }
 
 // One attempt of the fuse-regime solver: the asynchronous solver (default) or
-// the round-synchronous one. Reorders loc / val within each shard. A build
+// the round-synchronous one. The solvers see each shard's edges sorted by the
+// segment of their first vertex (a copy of loc / val). A build
 // whose peel fails is checked for duplicate local signatures among the
 // unpeeled edges (identical edges never peel; Sec. 4.4: the local signature
 // stands for the key in its shard). A function key given with two values ends
 // the build with VF_EDUP (no seed can solve it); otherwise, if there are
 // duplicates, one copy of each is kept and the same attempt is solved again
 // without the others (Sec. 4.5), which *dropped reports.
-vf_status solve_fuse(const vf_info& in, const vf::Geom& g, uint64_t* loc, uint32_t* val,
+vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc_in, const uint32_t* val_in,
                      const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
                      uint64_t* rounds_out, int solver, uint64_t* dropped, uint64_t cell_base = 0) {
-    // edges of each tile in the order of their first vertex's segment (locality
-    // of the peeling wave); the solvers only see edge indices within a shard
-    {
-        PhaseTimer t(kPhScatter, st);
-        VF_CK(vf::launch_tile_order(loc, val, in.n_eff, start, uint32_t(in.shards), g, st));
-    }
+    // each shard's edges in the order of their first vertex's segment (locality
+    // of the peeling waves); the solvers only see edge indices within a shard
     const uint64_t n = in.n_eff;
+    DevBuf sloc, sval, bins;
+    const uint64_t* loc = loc_in;
+    const uint32_t* val = val_in;
+    if (g.regime == VF_REGIME_FUSE && n > 0) {
+        PhaseTimer t(kPhScatter, st, 3);  // count, scan, scatter
+        VF_CK(sloc.alloc(n * 8, st));
+        if (val_in) VF_CK(sval.alloc(n * 4, st));
+        VF_CK(bins.alloc(vf::segment_order_bins(g, uint32_t(in.shards)) * 8, st));
+        VF_CK(vf::launch_segment_order(loc_in, val_in, n, start, uint32_t(in.shards), g,
+                                       bins.as<unsigned long long>(), sloc.as<uint64_t>(), sval.as<uint32_t>(), st));
+        loc = sloc.as<uint64_t>();
+        val = val_in ? sval.as<uint32_t>() : nullptr;
+    }
     *dropped = 0;
     DevBuf drop;
     uint64_t ndrop = 0;

@@ -21,6 +21,16 @@
 // records in decreasing slot order are a reverse peeling order, the order in
 // which assignment must run (each peeled vertex is assigned after the vertices
 // its value depends on). Items whose claim failed leave an empty slot.
+// Why "before" holds on the hardware and not only in program order: the slot
+// fetch-and-add is issued by one lane, and the whole warp then executes a
+// warp-synchronous shuffle of its returned value (every lane's slot comes from
+// it) before reaching the removals. The shuffle cannot execute before that
+// value has returned, a warp issues its instructions in order, and a
+// fetch-and-add returns only once it has been performed at L2; so the slot is
+// taken, at L2, before either removal of the step is even issued, and a later
+// peel of a vertex the removal freed takes its slot from the same counter
+// afterwards. The compiler barrier keeps the compiler from moving the
+// removals above the shuffle.
 //
 // Assignment is a dataflow in decreasing slot order: once final, a vertex's
 // value word (64 bits, in the queue's memory) holds its value with bit 32 set (vertices no edge was peeled from are
@@ -417,75 +427,163 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
 
 // ----------------------------------------------------- segment order (locality)
 
-// Edges of a fuse shard are peeled as a wave that sweeps the segments, and the
-// first vertex of an edge fixes its segment (v0 = mulhi(local, l*seg) grows
-// with the local signature). Sorting every tile of kTile consecutive edges by
-// (shard, segment) in shared memory puts the edges the wave touches at one
-// time into runs of consecutive entries, so their signatures, values and claim
-// bits are read as whole sectors. A tile that spans more than two shards (tiny
-// shards) is left as it is.
+// Edges of a fuse shard are peeled as two waves that sweep the segments, and
+// the first vertex of an edge fixes its segment (v0 = mulhi(local, l*seg)
+// grows with the local signature). A counting sort of each shard's edges by
+// that segment (groups of 2^sshift segments when a shard has more than
+// kSegBins) puts the edges the waves touch at one time next to each other, so
+// incidence accumulates into a few segments' vertex words at a time and a
+// peeling step's signature, value and claim bit share cache lines with its
+// neighbours'. Bins are (shard, segment group); tiles of kTile consecutive
+// edges (in one or two shards after the shard scatter) count and scatter
+// their bins in shared memory and reserve each bin's range with one global
+// atomic.
 constexpr int kTile = 4096;
 constexpr int kTileThreads = 256;
-constexpr uint32_t kTileBins = 4096;  // (shard, segment group) bins per tile
+constexpr uint32_t kSegBins = 2048;  // segment groups per shard
 
-__global__ void __launch_bounds__(kTileThreads) k_tile_order(uint64_t* __restrict__ loc, uint32_t* __restrict__ val,
-                                                             uint64_t n, const unsigned long long* __restrict__ start,
-                                                             uint32_t S, Geom g, uint32_t nb, uint32_t sshift) {
-    extern __shared__ unsigned long long smem_tile[];
-    uint64_t* s_loc = reinterpret_cast<uint64_t*>(smem_tile);
-    uint32_t* s_val = reinterpret_cast<uint32_t*>(s_loc + kTile);
-    uint32_t* s_cnt = s_val + kTile;  // 2 * nb
-    __shared__ uint32_t s_split, s_skip, s_warp[kTileThreads / 32];
-    const uint32_t nbins = 2 * nb;
+__device__ __forceinline__ uint32_t seg_bin(uint64_t x, const Geom& g, uint32_t sshift) {
+    return uint32_t(mulhi(x, g.span) >> g.lg_seg) >> sshift;
+}
+
+// Per tile: its first shard f, the first key of shard f + 1 (relative), and
+// whether it spans more than two shards (then it is counted key by key).
+__device__ __forceinline__ void tile_shards(const unsigned long long* start, uint32_t S, uint64_t t0, uint32_t m,
+                                            uint32_t& f, uint32_t& split, bool& many) {
+    f = flow_shard_of_edge(start, S, t0);
+    const uint32_t l = flow_shard_of_edge(start, S, t0 + m - 1);
+    many = l - f > 1;
+    const unsigned long long sp = __ldg(start + f + 1) - t0;
+    split = sp < m ? uint32_t(sp) : m;
+}
+
+// counts[s * nb + bin] += edges of shard s in segment group bin.
+__global__ void __launch_bounds__(kTileThreads) k_seg_count(const uint64_t* __restrict__ loc, uint64_t n,
+                                                             const unsigned long long* __restrict__ start, uint32_t S,
+                                                             Geom g, uint32_t nb, uint32_t sshift,
+                                                             unsigned long long* __restrict__ counts) {
+    extern __shared__ __align__(16) uint32_t s_cnt[];  // 2 * nb
+    __shared__ uint32_t s_f, s_split;
+    __shared__ bool s_many;
     for (uint64_t t0 = uint64_t(blockIdx.x) * kTile; t0 < n; t0 += uint64_t(gridDim.x) * kTile) {
         const uint32_t m = n - t0 < uint64_t(kTile) ? uint32_t(n - t0) : uint32_t(kTile);
         if (threadIdx.x == 0) {
-            const uint32_t f = flow_shard_of_edge(start, S, t0), l = flow_shard_of_edge(start, S, t0 + m - 1);
-            s_skip = l - f > 1;
-            const unsigned long long sp = __ldg(start + f + 1) - t0;  // first key of shard f+1
-            s_split = sp < m ? uint32_t(sp) : m;
+            uint32_t f, sp;
+            bool many;
+            tile_shards(start, S, t0, m, f, sp, many);
+            s_f = f, s_split = sp, s_many = many;
         }
-        for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) s_cnt[i] = 0;
+        for (uint32_t i = threadIdx.x; i < 2 * nb; i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
-        if (s_skip) {
-            __syncthreads();
-            continue;
-        }
+        const uint32_t f = s_f, split = s_split;
         for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-            const uint64_t x = loc[t0 + i];
-            s_loc[i] = x;
-            if (val) s_val[i] = val[t0 + i];
-            const uint32_t bin = (i >= s_split ? nb : 0u) + (uint32_t(mulhi(x, g.span) >> g.lg_seg) >> sshift);
-            atomicAdd(&s_cnt[bin], 1u);
+            const uint64_t x = __ldg(loc + t0 + i);
+            if (s_many) {
+                const uint32_t s = flow_shard_of_edge(start, S, t0 + i);
+                atomicAdd(counts + uint64_t(s) * nb + seg_bin(x, g, sshift), 1ull);
+            } else {
+                atomicAdd(&s_cnt[(i >= split ? nb : 0u) + seg_bin(x, g, sshift)], 1u);
+            }
         }
         __syncthreads();
-        // exclusive scan of the bin counts: each thread owns a run of consecutive bins
-        const uint32_t per = (nbins + blockDim.x - 1) / blockDim.x;
-        const uint32_t b0 = min(nbins, threadIdx.x * per), b1 = min(nbins, b0 + per);
-        uint32_t sum = 0;
-        for (uint32_t i = b0; i < b1; i++) sum += s_cnt[i];
-        uint32_t incl = sum;
+        if (!s_many)
+            for (uint32_t i = threadIdx.x; i < 2 * nb; i += blockDim.x) {
+                const uint32_t c = s_cnt[i];
+                const uint32_t s = f + (i >= nb ? 1u : 0u);
+                if (c && s < S) atomicAdd(counts + uint64_t(s) * nb + (i >= nb ? i - nb : i), (unsigned long long)c);
+            }
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of the bin counts into cursors, starting at each shard's
+// first key (one block).
+__global__ void __launch_bounds__(1024) k_seg_scan(unsigned long long* __restrict__ counts, uint64_t nbins,
+                                                    const unsigned long long* __restrict__ start, uint32_t nb) {
+    __shared__ unsigned long long s_part[1024];
+    const uint32_t T = blockDim.x, tid = threadIdx.x;
+    const uint64_t per = (nbins + T - 1) / T;
+    const uint64_t b0 = min(nbins, uint64_t(tid) * per), b1 = min(nbins, b0 + per);
+    unsigned long long sum = 0;
+    for (uint64_t i = b0; i < b1; i++) sum += counts[i];
+    s_part[tid] = sum;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long run = 0;
+        for (uint32_t t = 0; t < T; t++) {
+            const unsigned long long x = s_part[t];
+            s_part[t] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    unsigned long long run = s_part[tid];
+    for (uint64_t i = b0; i < b1; i++) {
+        const unsigned long long c = counts[i];
+        counts[i] = run;  // the shards are contiguous, so the running sum is also each shard's start
+        run += c;
+    }
+}
+
+// Scatter every edge (signature and value) to its bin's next slot.
+__global__ void __launch_bounds__(kTileThreads) k_seg_scatter(const uint64_t* __restrict__ loc,
+                                                               const uint32_t* __restrict__ val, uint64_t n,
+                                                               const unsigned long long* __restrict__ start,
+                                                               uint32_t S, Geom g, uint32_t nb, uint32_t sshift,
+                                                               unsigned long long* __restrict__ cursor,
+                                                               uint64_t* __restrict__ loc_out,
+                                                               uint32_t* __restrict__ val_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* s_base = reinterpret_cast<unsigned long long*>(smem);  // 2 * nb
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_base + 2 * nb);             // 2 * nb
+    __shared__ uint32_t s_f, s_split;
+    __shared__ bool s_many;
+    for (uint64_t t0 = uint64_t(blockIdx.x) * kTile; t0 < n; t0 += uint64_t(gridDim.x) * kTile) {
+        const uint32_t m = n - t0 < uint64_t(kTile) ? uint32_t(n - t0) : uint32_t(kTile);
+        if (threadIdx.x == 0) {
+            uint32_t f, sp;
+            bool many;
+            tile_shards(start, S, t0, m, f, sp, many);
+            s_f = f, s_split = sp, s_many = many;
+        }
+        for (uint32_t i = threadIdx.x; i < 2 * nb; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        const uint32_t f = s_f, split = s_split;
+        constexpr int kPer = kTile / kTileThreads;
+        uint64_t xs[kPer];
+        uint32_t rk[kPer], bn[kPer];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (lane32() >= unsigned(d)) incl += y;
+        for (int j = 0; j < kPer; j++) {
+            const uint32_t i = threadIdx.x + uint32_t(j) * kTileThreads;
+            bn[j] = 0xFFFFFFFFu;
+            if (i < m) {
+                xs[j] = __ldg(loc + t0 + i);
+                if (s_many) {
+                    const uint32_t s = flow_shard_of_edge(start, S, t0 + i);
+                    const unsigned long long pos = atomicAdd(cursor + uint64_t(s) * nb + seg_bin(xs[j], g, sshift), 1ull);
+                    loc_out[pos] = xs[j];
+                    if (val) val_out[pos] = __ldg(val + t0 + i);
+                } else {
+                    bn[j] = (i >= split ? nb : 0u) + seg_bin(xs[j], g, sshift);
+                    rk[j] = atomicAdd(&s_cnt[bn[j]], 1u);
+                }
+            }
         }
-        if (lane32() == 31) s_warp[threadIdx.x >> 5] = incl;
         __syncthreads();
-        uint32_t off = incl - sum;
-        for (uint32_t w = 0; w < (threadIdx.x >> 5); w++) off += s_warp[w];
-        for (uint32_t i = b0; i < b1; i++) {
-            const uint32_t c = s_cnt[i];
-            s_cnt[i] = off;
-            off += c;
-        }
+        if (!s_many)
+            for (uint32_t i = threadIdx.x; i < 2 * nb; i += blockDim.x) {
+                const uint32_t c = s_cnt[i];
+                const uint32_t s = f + (i >= nb ? 1u : 0u);
+                if (c && s < S) s_base[i] = atomicAdd(cursor + uint64_t(s) * nb + (i >= nb ? i - nb : i),
+                                                      (unsigned long long)c);
+            }
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-            const uint64_t x = s_loc[i];
-            const uint32_t bin = (i >= s_split ? nb : 0u) + (uint32_t(mulhi(x, g.span) >> g.lg_seg) >> sshift);
-            const uint32_t pos = atomicAdd(&s_cnt[bin], 1u);
-            loc[t0 + pos] = x;
-            if (val) val[t0 + pos] = s_val[i];
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            if (bn[j] == 0xFFFFFFFFu) continue;
+            const unsigned long long pos = s_base[bn[j]] + rk[j];
+            loc_out[pos] = xs[j];
+            if (val) val_out[pos] = __ldg(val + t0 + threadIdx.x + uint32_t(j) * kTileThreads);
         }
         __syncthreads();
     }
@@ -605,30 +703,32 @@ cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_order(uint64_t* loc, uint32_t* val, uint64_t n, const unsigned long long* start,
-                              uint32_t S, const Geom& g, cudaStream_t st) {
-    if (n == 0 || g.regime != kRegimeFuse) return cudaSuccess;  // only fuse graphs have segments
+cudaError_t launch_segment_order(const uint64_t* loc, const uint32_t* val, uint64_t n,
+                                 const unsigned long long* start, uint32_t S, const Geom& g, unsigned long long* counts,
+                                 uint64_t* loc_out, uint32_t* val_out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
     const uint32_t l = uint32_t(g.span >> g.lg_seg);
     uint32_t sshift = 0;
-    while (((l - 1) >> sshift) + 1 > kTileBins / 2) sshift++;
+    while (((l - 1) >> sshift) + 1 > kSegBins) sshift++;
     const uint32_t nb = ((l - 1) >> sshift) + 1;
-    const size_t smem = size_t(kTile) * 12 + size_t(2 * nb) * 4;
-    static std::atomic<uint64_t> attr_set{0};  // one bit per device
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    const uint64_t nbins = uint64_t(S) * nb;
+    cudaError_t e = cudaMemsetAsync(counts, 0, nbins * 8, st);
     if (e != cudaSuccess) return e;
-    const uint64_t bit = uint64_t(1) << (dev & 63);
-    if (!(attr_set.load() & bit)) {
-        e = cudaFuncSetAttribute(k_tile_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(size_t(kTile) * 12 + size_t(kTileBins) * 4));
-        if (e != cudaSuccess) return e;
-        attr_set.fetch_or(bit);
-    }
     uint64_t tiles = (n + kTile - 1) / kTile;
-    const uint64_t cap = uint64_t(num_sms()) * 2;
-    k_tile_order<<<unsigned(tiles < cap ? tiles : cap), kTileThreads, smem, st>>>(loc, val, n, start, S, g, nb,
-                                                                                  sshift);
+    const uint64_t cap = uint64_t(num_sms()) * 4;
+    const unsigned grid = unsigned(tiles < cap ? tiles : cap);
+    k_seg_count<<<grid, kTileThreads, size_t(2 * nb) * 4, st>>>(loc, n, start, S, g, nb, sshift, counts);
+    k_seg_scan<<<1, 1024, 0, st>>>(counts, nbins, start, nb);
+    k_seg_scatter<<<grid, kTileThreads, size_t(2 * nb) * 12, st>>>(loc, val, n, start, S, g, nb, sshift, counts,
+                                                                    loc_out, val_out);
     return cudaGetLastError();
+}
+
+uint64_t segment_order_bins(const Geom& g, uint32_t S) {
+    const uint32_t l = uint32_t(g.span >> g.lg_seg);
+    uint32_t sshift = 0;
+    while (((l - 1) >> sshift) + 1 > kSegBins) sshift++;
+    return uint64_t(S) * (((l - 1) >> sshift) + 1);
 }
 
 cudaError_t launch_find_dups(const uint64_t* loc, const uint32_t* val, uint64_t n, const unsigned long long* start,

@@ -151,10 +151,13 @@ cudaError_t launch_find_dups(const uint64_t* loc, const uint32_t* val, uint64_t 
 cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st);
 uint32_t flow_batches(const FlowArgs& a);
 cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st);
-// Sorts each tile of consecutive edges by (shard, segment of the first vertex)
-// in place (fuse regime; locality of the peeling wave).
-cudaError_t launch_tile_order(uint64_t* loc, uint32_t* val, uint64_t n, const unsigned long long* start,
-                              uint32_t S, const Geom& g, cudaStream_t st);
+// Counting sort of each shard's edges by the segment of their first vertex
+// (fuse regime; locality of the peeling waves): loc/val to loc_out/val_out;
+// counts: segment_order_bins(g, S) words of scratch.
+cudaError_t launch_segment_order(const uint64_t* loc, const uint32_t* val, uint64_t n,
+                                 const unsigned long long* start, uint32_t S, const Geom& g, unsigned long long* counts,
+                                 uint64_t* loc_out, uint32_t* val_out, cudaStream_t st);
+uint64_t segment_order_bins(const Geom& g, uint32_t S);
 
 // Fuse-regime wave solver (csrc/vf_wave.cu): 64-bit vertex words that hold the
 // degree, the other two vertices and the value of the edges' sum; phase I in
