@@ -91,6 +91,45 @@ __device__ void cta_exclusive_scan(uint32_t* arr, uint32_t len, uint32_t* s_part
     __syncthreads();
 }
 
+// Drops the 128-byte L2 lines wholly inside [p, p + words) without writing
+// them back (discard.global.L2: the line's contents become undefined).
+__device__ __forceinline__ void discard_words(const uint32_t* p, uint64_t words) {
+    const uint64_t lo = (reinterpret_cast<uint64_t>(p) + 127u) & ~uint64_t(127);
+    const uint64_t hi = (reinterpret_cast<uint64_t>(p + words)) & ~uint64_t(127);
+    for (uint64_t x = lo + uint64_t(threadIdx.x) * 128u; x < hi; x += uint64_t(blockDim.x) * 128u)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(x) : "memory");
+}
+
+// Everything a shard wrote to the CTA's slab is dead once the shard is done,
+// and every array is written before it is read by the next shard. Without
+// this, the 304 slabs resident at once (more than L2 holds) are written back
+// to DRAM line by line as they are evicted; discarding them instead keeps L2
+// for live lines. `m`, `V`: the finished shard's keys and cells; `lused`:
+// words of coefficient rows (and slab-resident dense system) it wrote.
+__device__ void discard_slab(const uint32_t* scr, const LgeOffsets& o, uint32_t m, uint32_t V, uint64_t lused) {
+    const uint64_t mm = m, vv = V;
+    discard_words(scr + o.cev, 3 * mm);
+    discard_words(scr + o.porder, mm);
+    discard_words(scr + o.proff, vv + 2);
+    discard_words(scr + o.f0, vv);
+    discard_words(scr + o.f1, vv);
+    discard_words(scr + o.cand, vv);
+    discard_words(scr + o.core, mm);
+    discard_words(scr + o.eqst, mm);
+    discard_words(scr + o.inc_off, vv + 1);
+    discard_words(scr + o.inc_cur, vv);
+    discard_words(scr + o.inc_list, 3 * mm);
+    discard_words(scr + o.vstate, vv);
+    discard_words(scr + o.act, vv);
+    discard_words(scr + o.actv, o.a_cap);
+    discard_words(scr + o.solves, mm);
+    discard_words(scr + o.soff, mm + vv + 4);
+    discard_words(scr + o.srec, 4 * mm);
+    discard_words(scr + o.dense, mm);
+    discard_words(scr + o.lc, mm);
+    discard_words(scr + o.L, lused < o.lpool ? lused : o.lpool);
+}
+
 // Hands task s to the spill list (small configuration) and reports whether
 // it did; the large configuration has no spill list and fails the shard.
 __device__ __forceinline__ bool spill_task(const LgeArgs& a, uint32_t s) {
@@ -137,8 +176,16 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
     // spill list (written by the previous launch), otherwise from all tasks.
     const bool from_spill = a.spilled != nullptr;
     const uint32_t ntasks = from_spill ? *a.spilled : a.ntasks;
+    // the previous shard's sizes, for discarding its slab lines (uniform)
+    uint32_t prev_m = 0, prev_v = 0;
+    uint64_t prev_l = 0;
     for (;;) {
         __shared__ uint32_t s_skip;
+        // every path to here ends its shard with a barrier; the barrier below
+        // orders the discards before the next shard's first slab write
+        if (prev_m | prev_v) discard_slab(scr, o, prev_m, prev_v, prev_l);
+        prev_m = prev_v = 0;
+        prev_l = 0;
         if (tid == 0) {
             const uint32_t q = atomicAdd(&a.stats[from_spill ? 4 : a.ctr], 1u);
             s_shard = q < ntasks ? (from_spill ? a.spill_in[q] : a.task_lo + q) : kNone;
@@ -173,6 +220,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
         gg.fpb = task.fpb;
         gg.fps = task.fps;
         if (m > a.m_cap || V > a.v_cap || V > 65535u || m > 65535u) {
+            // (nothing was written to the slab: prev_m, prev_v stay 0)
             if (tid == 0) {
                 atomicOr(a.err, kErrCapacity);
                 atomicOr(a.item_fail + task.item, kErrCapacity);
@@ -195,6 +243,8 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
             continue;
         }
         for (uint32_t i = tid; i < pw; i += T) sm[i] = 0;
+        prev_m = m;  // the slab is written from here on
+        prev_v = V;
         __syncthreads();
         for (uint32_t e = tid; e < m; e += T) {
             uint64_t v[4];
@@ -559,6 +609,7 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 __syncthreads();
                 continue;
             }
+            prev_l = dense_smem ? uint64_t(S) * AW : rows_off + dense_words;
             // One record per solve, gathered for all solves at once: the solved
             // cell x, its equation's edge e, the two other cells and their states
             // (final when x was solved: active, or solved in an earlier round). The
@@ -577,6 +628,17 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
                 if (srs) srs[si] = rec;
             }
             __syncthreads();
+            // the elimination's arrays are dead from here on (their lines are
+            // dropped instead of being written back when evicted)
+            discard_words(fr[0], V);
+            discard_words(fr[1], V);
+            discard_words(cand, V);
+            discard_words(inc_off, V + 1ull);
+            discard_words(inc_cur, V);
+            discard_words(inc_list, 3ull * m);
+            discard_words(act, V);
+            discard_words(eqst, m);
+            discard_words(solves, m);
             // solved variables as affine functions of the active ones, round by round
             for (uint32_t r = 0; r < R; r++) {
                 const uint32_t lo = __ldcg(&soff[r]), hi = __ldcg(&soff[r + 1]);
@@ -629,6 +691,12 @@ __global__ void __launch_bounds__(kLT, kMinBlocks) k_lge(LgeArgs a) {
             }
             for (uint32_t c = tid; c < A; c += T) colrow[c] = kNone;
             __syncthreads();
+            // the affine rows (and what built the dense rows) are dead now
+            discard_words(L, uint64_t(S) * AW);
+            discard_words(lc, S);
+            discard_words(core, m);
+            discard_words(dense, m);
+            discard_words(vstate, V);
             // Gauss-Jordan over GF(2): pivot = lowest unused row with the column bit
             // once every row is a pivot no later column can have one (its active
             // variable stays free, 0): the loop ends there
