@@ -254,6 +254,11 @@ typedef struct {
     uint64_t lge_target;     /* LGE regime: mean keys per shard */
     int lpt;                 /* solve shards largest first */
     int use_graph;           /* scatter + solver as one CUDA graph */
+    uint64_t small_cta_keys; /* CTA configuration of the LGE solver: shards of at most this
+                                many keys run 3 CTAs of 192 threads per SM, larger ones 2
+                                CTAs of 256 threads (7168; 0: every shard in the latter).
+                                It changes no seed, retry count or member's value,
+                                only the speed. */
 } vf_batch_opts;
 
 vf_status vf_batch_opts_default(vf_batch_opts *opts);
@@ -266,7 +271,8 @@ vf_status vf_build_batch(const vf_batch_item *items, uint32_t count, const vf_pa
 
 /* Autotuner: times candidate opts (fuse/LGE threshold at the given one or
  * none, mean LGE shard 8192 or 16384 keys, largest-first or natural task
- * order) on a sample of the batch (every k-th structure, ~5% of the keys)
+ * order, small CTA configuration for shards up to 7168 keys or not) on a
+ * sample of the batch (every k-th structure, ~5% of the keys)
  * and returns the fastest; results are cached per batch shape (count, total
  * keys, largest structure). best_ms: the sample's build time (-1 if cached). */
 vf_status vf_tune_batch(const vf_batch_item *items, uint32_t count, const vf_params *common, void *stream,

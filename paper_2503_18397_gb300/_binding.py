@@ -68,7 +68,7 @@ class VfBatchItem(C.Structure):
 
 class VfBatchOpts(C.Structure):
     _fields_ = [("lge_threshold", C.c_uint64), ("lge_target", C.c_uint64), ("lpt", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("small_cta_keys", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -914,7 +914,7 @@ vf_status build_batch_once(const vf_batch_item* items, const std::vector<uint32_
     if (opts.lpt)
         std::stable_sort(tasks.begin(), tasks.end(),
                          [](const vf::LgeTask& x, const vf::LgeTask& y) { return x.m > y.m; });
-    const uint32_t n_mid = vf::lge_partition(tasks);
+    const uint32_t n_mid = vf::lge_partition(tasks, opts.small_cta_keys);
     uint32_t m_cap = 1, v_cap = 32;
     for (auto& t : tasks) {
         m_cap = std::max(m_cap, t.m);
@@ -1801,6 +1801,7 @@ vf_status vf_batch_opts_default(vf_batch_opts* o) {
     o->lge_target = 16384;
     o->lpt = 1;
     o->use_graph = 1;
+    o->small_cta_keys = vf::kLgeSmallTaskKeys;
     return VF_OK;
 }
 
@@ -1899,14 +1900,16 @@ vf_status vf_tune_batch(const vf_batch_item* items, uint32_t count, const vf_par
     std::vector<vf_batch_opts> cands;
     for (uint64_t thr : {common->lge_threshold, ~uint64_t(0)})
         for (uint64_t tgt : {uint64_t(8192), uint64_t(16384)})
-            for (int lpt : {1, 0}) {
-                vf_batch_opts o;
-                vf_batch_opts_default(&o);
-                o.lge_threshold = thr;
-                o.lge_target = tgt;
-                o.lpt = lpt;
-                cands.push_back(o);
-            }
+            for (int lpt : {1, 0})
+                for (uint64_t small : {uint64_t(vf::kLgeSmallTaskKeys), uint64_t(0)}) {
+                    vf_batch_opts o;
+                    vf_batch_opts_default(&o);
+                    o.lge_threshold = thr;
+                    o.lge_target = tgt;
+                    o.lpt = lpt;
+                    o.small_cta_keys = small;
+                    cands.push_back(o);
+                }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     VF_CK(cudaEventCreate(&e0));

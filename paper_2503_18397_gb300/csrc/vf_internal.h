@@ -248,7 +248,7 @@ struct LgeArgs {
 // per SM); larger ones in the medium one (two per SM).
 constexpr uint32_t kLgeSmallTaskKeys = 7168;
 // Stable partition: tasks above kLgeSmallTaskKeys first; returns their count.
-uint32_t lge_partition(std::vector<LgeTask>& tasks);
+uint32_t lge_partition(std::vector<LgeTask>& tasks, uint64_t small_keys = kLgeSmallTaskKeys);
 // Layout (in 32-bit words) of one CTA's LGE scratch slab for shards of at most
 // m keys and V cells.
 constexpr uint32_t kMaxActive = 4096;  // active variables per shard (up to kLgeBigShard keys)

@@ -819,9 +819,9 @@ static unsigned resident(LgeCfg c) {
 
 unsigned lge_grid() { return std::max(resident(kCfgSmall), std::max(resident(kCfgMid), resident(kCfgBig))); }
 
-uint32_t lge_partition(std::vector<LgeTask>& tasks) {
+uint32_t lge_partition(std::vector<LgeTask>& tasks, uint64_t small_keys) {
     auto mid = std::stable_partition(tasks.begin(), tasks.end(),
-                                     [](const LgeTask& t) { return t.m > kLgeSmallTaskKeys; });
+                                     [small_keys](const LgeTask& t) { return t.m > small_keys; });
     return uint32_t(mid - tasks.begin());
 }
 

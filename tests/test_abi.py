@@ -51,6 +51,11 @@ def test_params_default_match_paper(vf, orc):
     assert p.fuse_solver == vf.SOLVER_FLOW
 
 
+def test_batch_opts_default(vf):
+    o = vf.vf_batch_opts_default()
+    assert (o.lge_threshold, o.lge_target, o.lpt, o.use_graph, o.small_cta_keys) == (800000, 16384, 1, 1, 7168)
+
+
 def _plan_pair(vf, orc, n, M, **kw):
     p = vf.vf_params_default(**kw)
     info = vf.vf_plan(n, M, p)

@@ -93,6 +93,17 @@ def test_batch_without_graph_and_natural_order(vf, orc):
     _check_against_single(vf, orc, items, host, structs)
 
 
+@pytest.mark.parametrize("small", [0, 1 << 20])
+def test_batch_cta_configuration(vf, orc, small):
+    # every LGE shard in the two-CTA configuration (0), or every shard offered
+    # to the three-CTA one (those whose peel arrays do not fit its shared
+    # memory pass through the spill list): same seeds, retries and geometry as
+    # single builds, every member decoded, the oracle's query equal
+    items, host = _make([700, 6000, 9000, 30_000, 150_000], 15)
+    structs = vf.vf_build_batch(items, opts=vf.vf_batch_opts_default(small_cta_keys=small))
+    _check_against_single(vf, orc, items, host, structs)
+
+
 def test_batch_mixed_regimes(vf, orc):
     # one structure above the fuse threshold among small LGE ones
     items, host = _make([900_000, 3_000, 60_000], 11)
@@ -105,7 +116,7 @@ def test_batch_all_lge_threshold_and_tuner(vf, orc):
     sizes = synth.log_uniform_sizes(48, 1e3, 3e5, 5)
     items, host = _make(sizes, 13)
     best, ms = vf.vf_tune_batch(items)
-    assert best.lge_target in (8192, 16384) and best.lpt in (0, 1)
+    assert best.lge_target in (8192, 16384) and best.lpt in (0, 1) and best.small_cta_keys in (0, 7168)
     structs = vf.vf_build_batch(items, opts=best)
     _check_against_single(vf, orc, items, host, structs, opts_like_default=False)
     best2, ms2 = vf.vf_tune_batch(items)
