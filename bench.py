@@ -338,7 +338,7 @@ def run_gpu(args):
         vf.vf_query(s, kh, offsets=oh, out=outh)
         vf.vf_query(s, xh, offsets=xoh, out=outh)
         s.free()
-    e2e_b, e2e_q = [], []
+    e2e_b, e2e_q, e2e_calls = [], [], []
     # one build per timed step with that step's seed, so retries (a property
     # of the seed) weigh the same as in the device-timed steps
     for seed in timed_seeds:
@@ -348,10 +348,12 @@ def run_gpu(args):
         s = vf.vf_build(kh, vh, offsets=oh, params=p)
         t1 = time.perf_counter()
         vf.vf_query(s, kh, offsets=oh, out=outh)
+        tq = time.perf_counter()
         vf.vf_query(s, xh, offsets=xoh, out=outh)
         t2 = time.perf_counter()
         e2e_b.append((t1 - t0) * 1e3)
         e2e_q.append((t2 - t1) * 1e3)
+        e2e_calls.extend([(tq - t1) * 1e3, (t2 - tq) * 1e3])
         s.free()
     key_bytes = keys.nbytes + (offs.nbytes if offs is not None else 0)
     other_bytes = other.nbytes + (ooffs.nbytes if ooffs is not None else 0)
@@ -394,7 +396,11 @@ def run_gpu(args):
                                      "gqps": round(h2d_gbs / (key_bytes / n), 3),
                                      "frac": round(e2e_qgps / (h2d_gbs / (key_bytes / n)), 4),
                                      "what": "pinned host-to-device copy rate measured in this run, divided by "
-                                             "the bytes of one key: queries from host memory cannot go faster"}},
+                                             "the bytes of one key: queries from host memory cannot go faster"},
+                "query_call_ms": {"min": round(min(e2e_calls), 3), "median": round(statistics.median(e2e_calls), 3),
+                                  "max": round(max(e2e_calls), 3), "calls": len(e2e_calls)},
+                "build_call_ms": {"min": round(min(e2e_b), 3), "median": round(statistics.median(e2e_b), 3),
+                                  "max": round(max(e2e_b), 3)}},
         "gpu_launches": int(launches),
         "phases": per_phase,
         "roofline": roof,
