@@ -412,6 +412,9 @@ def run_gpu(args):
     qps = 2 * n * world / (q_ms * 1e-3)
     q_hbm = random_sector_roofline(qps / world, b, kind, hbm, peak_kind, int(info.k))
     out["query"]["roofline"] = {"hbm": q_hbm}
+    out["build_roofline"] = build_roofline(b_ms, n, b, kind, float(info.c), hbm, peak_kind,
+                                           info.regime != vf.REGIME_LGE,
+                                           max(1, phases.get("hash_hist", (0, 0))[1]) / args.steps)
     out["query"]["roofline"]["sectors"] = sector_roofline(
         qps / world, int(info.data_bytes), "l2" if info.data_bytes <= L2_BYTES else "hbm", int(info.k))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -655,6 +658,29 @@ def measure_c4(steps: int, warmup: int, count: int = 4096) -> dict:
         "gpu_launches": int(sum(v[1] for v in phases.values())),
         "clocks": clk, "check": {"members_ok": ok},
     }
+
+
+def build_roofline(build_ms: float, n: int, b: int, kind: str, c: float, hbm: float, peak_kind: str,
+                   peeled: bool, attempts: float) -> dict:
+    """The whole build against two algorithmic HBM models: streams only (the key
+    read twice, the value once, the bucketed local signature and value written
+    and read once, the data array written: shard state on chip), and streams
+    plus the random 32-byte sector read-modify-writes of a peeled shard whose
+    state is in HBM (incidence 3, peel 3, assignment 3 + 1, 64 B each).
+    Retries count against the build (attempts per build given)."""
+    vb = _vb(b, kind)
+    stream = 16.0 + vb + 2 * (8.0 + vb) + c * b / 8
+    models = {"streaming": stream}
+    if peeled:
+        models["streaming_plus_random_sectors"] = stream + 10 * 64.0
+    out = {"attempts_per_build": round(attempts, 3), "unit": "GB/s", "peak": hbm,
+           "peak_source": f"{peak_kind} hbm_gbs"}
+    for name, bpk in models.items():
+        bound_ns = bpk / hbm  # bytes per key / (GB/s) = ns per key
+        achieved = bpk * n / (build_ms * 1e-3) / 1e9
+        out[name] = {"bytes_per_key": round(bpk, 2), "bound_ns_per_key": round(bound_ns, 5),
+                     "achieved": round(achieved, 2), "frac": round(achieved / hbm, 4)}
+    return out
 
 
 def random_sector_roofline(qps: float, b: int, kind: str, hbm: float, peak_kind: str, k: int = 3) -> dict:
