@@ -248,6 +248,39 @@ def test_retries_match_oracle(vf, orc, solver):
     assert retried > 0
 
 
+@SOLVERS
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 31, 1000, 20_000])
+def test_fuse_forced_tiny_and_empty(vf, orc, n, solver):
+    # fuse graphs of a few segments (eq. (ln) segments of 4 cells and up), far
+    # below the sizes the fuse regime is meant for: whether every attempt fails
+    # (ℓ of a few segments does not peel at c = 1.12) or one succeeds, and with
+    # which seed, must be the oracle's; functions and filters, both arities
+    keys = synth.u64_keys(0, n, 40 + n)
+    vals = synth.values(n, 8, 40 + n)
+    outcomes = set()
+    for arity in (3, 4):
+        for v in (vals, None):
+            kind = orc.FUNC if v is not None else orc.FILTER
+            st, oi, _ = orc.build(orc.default_params(kind=kind, b=8, mode=orc.MODE_FUSE, seed=n, max_retries=30,
+                                                     arity=arity), keys, v)
+            outcomes.add(st)
+            if st == orc.OK:
+                s, info, _ = check_build(vf, orc, keys, v, mode=vf.MODE_FUSE, seed=n, max_retries=30, n_other=500,
+                                         fuse_solver=solver, arity=arity)
+                if n:
+                    assert info.regime == vf.REGIME_FUSE and info.k == arity
+                s.free()
+            else:
+                assert st == orc.EBUILD
+                with pytest.raises(vf.VFError) as e:
+                    vf.vf_build(dev(keys), None if v is None else dev(v),
+                                params=vf.vf_params_default(kind=kind, b=8, mode=vf.MODE_FUSE, seed=n, max_retries=30,
+                                                            fuse_solver=solver, arity=arity))
+                assert e.value.status == 3  # VF_EBUILD, like the oracle
+    if n <= 3:
+        assert outcomes == {orc.OK}
+
+
 # ---------------------------------------------------------------- MWHC (Sec. 4.1)
 
 @SOLVERS
