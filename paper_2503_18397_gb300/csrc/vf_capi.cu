@@ -433,6 +433,9 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     VF_CK(rec.alloc(std::max<uint64_t>(V, 1) * 16, st));  // one slot per item, at most one item per vertex
     VF_CK(ctr.alloc(vf::kFlowWords * 4, st));
     VF_CK(cudaMemsetAsync(ctr.p, 0, vf::kFlowWords * 4, st));
+    DevBuf rc;  // record slots per shard, one 128-byte line each
+    VF_CK(rc.alloc(std::max<uint64_t>(in.shards, 1) * vf::kRcStride * 4, st));
+    VF_CK(cudaMemsetAsync(rc.p, 0, std::max<uint64_t>(in.shards, 1) * vf::kRcStride * 4, st));
     vf::FlowArgs a;
     std::memset(&a, 0, sizeof a);
     a.loc = loc;
@@ -448,6 +451,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.claimed_bits = n;
     a.pv = pv.as<uint32_t>();
     a.rec = rec.as<uint4>();
+    a.rc = rc.as<uint32_t>();
     a.ctr = ctr.as<uint32_t>();
     a.err = a.ctr + vf::kFlowErr;
     a.data = data;
@@ -464,12 +468,16 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
         VF_CK(vf::launch_flow_peel(a, st));
     }
     std::vector<uint32_t> h(vf::kFlowWords);
+    std::vector<uint32_t> hrc(std::max<uint64_t>(in.shards, 1) * vf::kRcStride);
     VF_CK(cudaMemcpyAsync(h.data(), a.ctr, vf::kFlowWords * 4, cudaMemcpyDeviceToHost, st));
+    VF_CK(cudaMemcpyAsync(hrc.data(), rc.p, hrc.size() * 4, cudaMemcpyDeviceToHost, st));
     VF_CK(cudaStreamSynchronize(st));
     const uint32_t count = h[vf::kFlowPeeled], err = h[vf::kFlowErr];
-    uint64_t slots = 0;
-    std::memcpy(&slots, &h[vf::kFlowSlots], 8);
-    slots &= 0xFFFFFFFFull;  // record slots: low half
+    uint64_t slots = 0, rmax = 0;
+    for (uint64_t s = 0; s < in.shards; s++) {
+        slots += hrc[s * vf::kRcStride];
+        rmax = std::max<uint64_t>(rmax, hrc[s * vf::kRcStride]);
+    }
     *peeled = count - ndrop;  // claim bits include the dropped duplicates
     if (err & vf::kErrTimeout) return fail(VF_ETIMEOUT, "asynchronous peeling wait timed out");
     if (err & (vf::kErrDegOverflow | vf::kErrFrontier)) return VF_EBUILD;
@@ -477,8 +485,9 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
         if (claimed_out) claimed_out->adopt(claimed);
         return VF_EBUILD;
     }
-    if (slots > V) return fail(VF_ECUDA, "asynchronous peeling took more record slots than items");
+    if (rmax > in.cells) return fail(VF_ECUDA, "asynchronous peeling took more record slots than items");
     a.nrec = slots;
+    a.rmax = rmax;
     {
         PhaseTimer t(kPhAssign, st, slots ? 2 : 1);  // final flags, dataflow assignment
         VF_CK(vf::launch_flow_assign(a, st));

@@ -14,25 +14,29 @@
 // of a warp with no work at all reserve queue slots and take the item once it
 // is written.
 //
-// Order: every item takes a record slot from one global counter together with
-// its claim, before it removes the edge from the other two vertices. A vertex
-// that an edge f still touches can only be peeled (by some edge g) after f's
-// removal from it, hence after f's slot was taken: g's slot is larger. So the
-// records in decreasing slot order are a reverse peeling order, the order in
-// which assignment must run (each peeled vertex is assigned after the vertices
-// its value depends on). Items whose claim failed leave an empty slot.
+// Order: every item takes a record slot from its shard's counter together
+// with its claim, before it removes the edge from the other two vertices. A
+// vertex that an edge f still touches can only be peeled (by some edge g of
+// the same shard) after f's removal from it, hence after f's slot was taken:
+// g's slot is larger. So each shard's records in decreasing slot order are a
+// reverse peeling order, the order in which assignment must run (each peeled
+// vertex is assigned after the vertices its value depends on). Items whose
+// claim failed leave an empty slot. One counter per shard (each on its own
+// line) instead of one for all: the counter is taken by every warp step, and
+// doubling the traffic on a single shared one cost 12% of the peel.
 // Why "before" holds on the hardware and not only in program order: the slot
-// fetch-and-add is issued by one lane, and the whole warp then executes a
-// warp-synchronous shuffle of its returned value (every lane's slot comes from
-// it) before reaching the removals. The shuffle cannot execute before that
-// value has returned, a warp issues its instructions in order, and a
-// fetch-and-add returns only once it has been performed at L2; so the slot is
-// taken, at L2, before either removal of the step is even issued, and a later
-// peel of a vertex the removal freed takes its slot from the same counter
-// afterwards. The compiler barrier keeps the compiler from moving the
-// removals above the shuffle.
+// fetch-and-add is issued by one lane of each group of the warp's lanes with
+// the same shard, and the whole warp then executes a warp-synchronous shuffle
+// of the returned values (every lane's slot comes from its group's) before
+// reaching the removals. The shuffle cannot execute before those values have
+// returned, a warp issues its instructions in order, and a fetch-and-add
+// returns only once it has been performed at L2; so the slot is taken, at L2,
+// before either removal of the step is even issued, and a later peel of a
+// vertex the removal freed takes its slot from the same counter afterwards.
+// The compiler barrier keeps the compiler from moving the removals above the
+// shuffle.
 //
-// Assignment is a dataflow in decreasing slot order: once final, a vertex's
+// Assignment is a dataflow in decreasing slot order per shard: once final, a vertex's
 // value word (64 bits, in the queue's memory) holds its value with bit 32 set (vertices no edge was peeled from are
 // final from the start, value 0); an edge waits (bounded) until its two other
 // vertices are final. An edge only waits on edges of larger slots, which were
@@ -222,10 +226,15 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
         const unsigned mneed = __ballot_sync(0xFFFFFFFFu, need);
         const unsigned mpend = __ballot_sync(0xFFFFFFFFu, pend);
         // ---- phase 1: independent requests, all in flight together
-        unsigned long long hb = 0, rt = 0;  // rt: record slots (low half), queue slots (high half)
+        unsigned long long hb = 0, rt = 0;  // rt: queue slots (high half)
+        uint32_t rbase = 0, rgrp = 0, rsh = 0;  // record slots: a counter per shard
         if (mneed && int(lane) == __ffs(mneed) - 1) hb = atomicAdd(head, (unsigned long long)__popc(mneed));
-        if (mhave && int(lane) == __ffs(mhave) - 1)  // pend implies have
-            rt = atomicAdd(slots, ((unsigned long long)__popc(mpend) << 32) | (unsigned long long)__popc(mhave));
+        if (mpend && int(lane) == __ffs(mpend) - 1) rt = atomicAdd(slots, (unsigned long long)__popc(mpend) << 32);
+        if (have) {  // one fetch-and-add per shard among the warp's items
+            rsh = v / cells;
+            rgrp = __match_any_sync(mhave, rsh);
+            if (int(lane) == __ffs(rgrp) - 1) rbase = atomicAdd(a.rc + rsh * kRcStride, uint32_t(__popc(rgrp)));
+        }
         unsigned long long it = kEmpty;
         if (!have && slot < a.queue_cap) it = dev_atomic64(a.queue[slot]).load(cuda::memory_order_relaxed);
         uint64_t local = 0;
@@ -240,7 +249,11 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
             hb = __shfl_sync(0xFFFFFFFFu, hb, __ffs(mneed) - 1);
             if (need) slot = hb + __popc(mneed & lanes_below());
         }
-        if (mhave) rt = __shfl_sync(0xFFFFFFFFu, rt, __ffs(mhave) - 1);
+        if (mpend) rt = __shfl_sync(0xFFFFFFFFu, rt, __ffs(mpend) - 1);
+        if (mhave) {
+            const uint32_t b0 = __shfl_sync(0xFFFFFFFFu, rbase, have ? __ffs(rgrp) - 1 : int(lane));
+            if (have) rbase = b0 + __popc(rgrp & lanes_below());
+        }
         if (mpend) {
             if (pend) {
                 const unsigned long long qs = (rt >> 32) + __popc(mpend & lanes_below());
@@ -264,7 +277,7 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
             bool next = false;
             uint32_t nv = 0, ne = 0;
             if (have) {
-                const unsigned long long rs = (rt & 0xFFFFFFFFull) + __popc(mhave & lanes_below());
+                const uint64_t rs = uint64_t(rsh) * cells + rbase;
                 if (peeled) {
                     atomicOr(a.pv + (v >> 5), 1u << (v & 31u));
                     const uint32_t s = v / cells;
@@ -305,9 +318,13 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
                             pe = uint32_t(st0 + (w1 >> 5));
                         }
                     }
-                    a.rec[rs] = make_uint4(v, o0, o1, a.val ? value : fingerprint_slice(local, a.g.b, a.g.fpb, a.g.fps));
+                    if (rbase < cells)  // a shard has at most one item per vertex
+                        a.rec[rs] = make_uint4(v, o0, o1, a.val ? value : fingerprint_slice(local, a.g.b, a.g.fpb, a.g.fps));
+                    else
+                        atomicOr(a.err, kErrFrontier);
                 } else {
-                    a.rec[rs].x = kHole;
+                    if (rbase < cells) a.rec[rs].x = kHole;
+                    else atomicOr(a.err, kErrFrontier);
                 }
                 if (next) {
                     v = nv;
@@ -380,10 +397,15 @@ __global__ void __launch_bounds__(kFT) k_final_init(FlowArgs a) {
         a.fv[v] = (a.stall || ((__ldg(a.pv + (v >> 5)) >> (v & 31u)) & 1u)) ? 0ull : kFinal;
 }
 
-// Dataflow assignment over the record slots, largest slot first.
+// Dataflow assignment over the record slots, largest slot first within each
+// shard. Positions go round robin over the shards (position k: shard k mod S,
+// the (k div S)-th slot from the shard's last), so every shard's dataflow
+// advances at once; a record waits only on larger slots of its own shard,
+// which come at smaller positions.
 __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
     const int b = a.g.b;
-    const uint64_t count = a.nrec;
+    const uint64_t count = a.rmax * a.S;
+    const uint64_t cells = a.g.cells;
     const unsigned lane = lane32();
     const uint32_t vmask = b == 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
     const uint32_t limit = a.assign_limit ? a.assign_limit : kIdleLimit;
@@ -394,7 +416,12 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
         if (base >= count) break;
         const uint64_t k = base + lane;
         uint4 r = make_uint4(kHole, 0, 0, 0);
-        if (k < count) r = __ldg(a.rec + (count - 1 - k));
+        if (k < count) {
+            const uint32_t s = uint32_t(k % a.S);
+            const uint64_t j = k / a.S;
+            const uint32_t taken = __ldg(a.rc + s * kRcStride);
+            if (j < taken) r = __ldg(a.rec + s * cells + (taken - 1 - j));
+        }
         bool done = r.x == kHole;
         uint32_t polls = 0;
         unsigned nap = kAssignNapMin;
@@ -700,7 +727,7 @@ cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st) {
 cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st) {
     k_final_init<<<grid_for(uint64_t(a.S) * a.g.cells), kFT, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || a.nrec == 0) return e;
+    if (e != cudaSuccess || a.nrec == 0 || a.rmax == 0) return e;
     k_flow_assign<<<assign_grid(a.g), kFT, 0, st>>>(a);
     return cudaGetLastError();
 }

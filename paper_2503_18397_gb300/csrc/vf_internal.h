@@ -105,13 +105,14 @@ cudaError_t launch_assign(FuseSolveArgs a, cudaStream_t st);
 // Counter words (u32 index into ctr), one 128-byte line each.
 enum : uint32_t {
     kFlowHead = 0,      // u64: queue slots taken by consumers
-    kFlowSlots = 32,    // u64: record slots taken (low half), queue slots filled (high half)
+    kFlowSlots = 32,    // u64: queue slots filled (high half; the low half is unused)
     kFlowDone = 96,     // u64: queue items whose chain has ended
     kFlowNext = 128,    // u64: assignment: next record position to take
     kFlowPeeled = 160,  // edges peeled
     kFlowErr = 192,     // error bits
     kFlowWords = 224
 };
+constexpr uint32_t kRcStride = 32;  // per-shard record counters, one 128-byte line each
 struct FlowArgs {
     const uint64_t* loc;              // bucketed local signatures
     const uint32_t* val;              // bucketed values, NULL for a filter
@@ -126,8 +127,11 @@ struct FlowArgs {
     uint32_t* claimed;                // one bit per edge
     uint64_t claimed_bits;            // edges
     uint32_t* pv;                     // one bit per vertex: an edge was peeled from it
-    uint4* rec;                       // per slot {peeled vertex, other, other, value}; x = ~0: empty
-    uint64_t nrec;                    // assignment: record slots taken by the peel
+    uint4* rec;                       // per slot {peeled vertex, other, other, value}; x = ~0: empty;
+                                      // shard s owns slots [s*cells, (s+1)*cells)
+    uint32_t* rc;                     // record slots taken per shard, one counter per kRcStride words
+    uint64_t nrec;                    // assignment: record slots taken by the peel, all shards
+    uint64_t rmax;                    // assignment: the most slots any shard took
     uint32_t* ctr;                    // kFlowWords counter words
     uint32_t* err;                    // == ctr + kFlowErr
     uint8_t* data;                    // assignment target
