@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
     bool pend = false;                   // produced item (pu, pe) waiting for a queue slot
     uint32_t v = 0, e = 0, pu = 0, pe = 0;
     uint32_t idle = 0;
+    uint32_t dacc = 0;  // lane 0: ended chains not yet added to done
     unsigned nap = 32;
     for (;;) {
         const unsigned mhave = __ballot_sync(0xFFFFFFFFu, have);
@@ -352,10 +353,21 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
             if (pend && uint32_t(__popc(mp & lanes_below())) < forks) pend = false;
         }
         // done += ended chains - forks (a chain that ended had its produced items
-        // counted in earlier iterations)
+        // counted in earlier iterations). Forks are added at once; ended chains
+        // wait in lane 0's count until it would go negative or the warp idles, so
+        // done never runs ahead of the true count and the exit test below stays
+        // exact, while the shared word is taken far less often (each taking costs
+        // the whole peel: twice the traffic on it was 4.6% slower).
         const unsigned mret = __ballot_sync(0xFFFFFFFFu, retire);
-        if (lane == 0 && uint32_t(__popc(mret)) != forks)
-            atomicAdd(done, (unsigned long long)__popc(mret) - (unsigned long long)forks);
+        if (lane == 0) {
+            const long long net = (long long)dacc + (long long)__popc(mret) - (long long)forks;
+            if (net < 0) {
+                atomicAdd(done, (unsigned long long)net);
+                dacc = 0;
+            } else {
+                dacc = uint32_t(net);
+            }
+        }
         if (got) {
             v = uint32_t(it >> 32);
             e = uint32_t(it);
@@ -366,8 +378,13 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
             nap = 32;
             continue;
         }
-        // nothing in flight in this warp: leave once every queue item's chain has
-        // ended (checked every 8th idle pass: the counters' lines are shared by all)
+        // nothing in flight in this warp: hand in its ended chains, then leave once
+        // every queue item's chain has ended (checked every 8th idle pass: the
+        // counters' lines are shared by all)
+        if (lane == 0 && dacc) {
+            atomicAdd(done, (unsigned long long)dacc);
+            dacc = 0;
+        }
         unsigned long long f = 0, t = 1;
         uint32_t er = 0;
         if (lane == 0 && (idle & 7u) == 0) {
