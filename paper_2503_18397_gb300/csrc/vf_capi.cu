@@ -414,7 +414,8 @@ vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc
 // (peel failed: retry), or an error.
 vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
                      const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
-                     uint64_t cell_base, const uint32_t* drop, uint64_t ndrop, DevBuf* claimed_out) {
+                     uint64_t cell_base, const uint32_t* drop, uint64_t ndrop, DevBuf* claimed_out,
+                     const unsigned long long* seg_ends = nullptr) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
     DevBuf W, queue, claimed, pv, rec, ctr;
@@ -460,7 +461,10 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.stall = g_debug_stall_assign.load() ? 1u : 0u;
     {
         PhaseTimer t(kPhAccum, st);
-        VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, drop, st));
+        if (seg_ends && vf::incidence_seg_fits(g))
+            VF_CK(vf::launch_incidence_seg(loc, n, start, a.S, g, seg_ends, a.W, a.err, drop, st));
+        else
+            VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, drop, st));
     }
     {
         // per batch: (head rebase), initial items, worklist peel; then the peeled count
@@ -664,7 +668,8 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc_i
         if (use == VF_SOLVER_FLOW || fallback) {
             *rounds_out = 0;
             rs = solve_flow(in, g, loc, val, start, data, st, peeled, cell_base,
-                            drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
+                            drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr,
+                            bins.p ? bins.as<unsigned long long>() : nullptr);
         } else if (use == VF_SOLVER_ROUNDS) {
             rs = solve_rounds(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base,
                               drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);

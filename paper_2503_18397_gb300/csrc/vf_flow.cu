@@ -130,6 +130,95 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
     }
 }
 
+// The same incidence over segment-ordered edges, a block per (shard, segment
+// of the first vertex) bin: the bin's first vertices all lie in that segment,
+// so they accumulate in shared memory and reach the vertex words in one
+// coalesced pass of fetch-and-adds; the second and third vertices go to the
+// vertex words directly. seg_ends[i]: one past the last edge of bin i (bins in
+// (shard, segment) order, one segment each). A degree that wraps shows as the
+// five-bit degree fields of the two parts summing past 31.
+constexpr int kIncSegThreads = 1024;
+constexpr uint32_t kSegBins = 2048;  // segment groups per shard in the segment order (below)
+
+__global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t* __restrict__ loc,
+                                                                  const unsigned long long* __restrict__ start,
+                                                                  uint32_t S, uint32_t nb, Geom g,
+                                                                  const unsigned long long* __restrict__ seg_ends,
+                                                                  uint32_t* __restrict__ W, uint32_t* err,
+                                                                  const uint32_t* __restrict__ drop) {
+    extern __shared__ uint32_t sw[];
+    const uint32_t seg = 1u << g.lg_seg;
+    const uint64_t tasks = uint64_t(S) * nb;
+    for (uint64_t task = blockIdx.x; task < tasks; task += gridDim.x) {
+        const uint64_t lo = task ? __ldg(seg_ends + task - 1) : 0ull, hi = __ldg(seg_ends + task);
+        if (lo == hi) continue;  // uniform over the block
+        const uint32_t sh = uint32_t(task / nb);
+        const uint32_t sg = uint32_t(task % nb);
+        const uint64_t st0 = __ldg(start + sh);
+        const uint64_t base = uint64_t(sh) * g.cells;
+        const uint64_t seg0 = uint64_t(sg) << g.lg_seg;  // shard-local cell of the segment's first vertex
+        for (uint32_t i = threadIdx.x; i < seg; i += blockDim.x) sw[i] = 0;
+        __syncthreads();
+        for (uint64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
+            const uint32_t inc = 1u + (uint32_t(e - st0) << 5);
+            uint64_t v[4];
+            edge_of(g, __ldg(loc + e), v);
+            const uint64_t r0 = v[0] - seg0;
+            uint32_t old[3];
+            if (r0 < seg) {
+                atomicAdd(sw + r0, inc);
+                old[0] = 0;
+            } else {  // not this bin's segment (cannot happen for segment-ordered edges)
+                old[0] = atomicAdd(W + base + v[0], inc);
+            }
+            old[1] = atomicAdd(W + base + v[1], inc);
+            old[2] = atomicAdd(W + base + v[2], inc);
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                if ((old[k] & 31u) == 31u) atomicOr(err, kErrDegOverflow);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < seg; i += blockDim.x) {
+            const uint32_t w = sw[i];
+            if (w) {
+                const uint32_t o = atomicAdd(W + base + seg0 + i, w);
+                if ((o & 31u) + (w & 31u) > 31u) atomicOr(err, kErrDegOverflow);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+bool incidence_seg_fits(const Geom& g) {
+    if (g.regime != kRegimeFuse || g.k != 3 || g.lg_seg > 15 || g.lg_seg < 5) return false;
+    const uint32_t l = uint32_t(g.span >> g.lg_seg);
+    return l >= 1 && l <= kSegBins;  // one segment per bin of the segment order
+}
+
+cudaError_t launch_incidence_seg(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
+                                 const Geom& g, const unsigned long long* seg_ends, uint32_t* W, uint32_t* err,
+                                 const uint32_t* drop, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (!incidence_seg_fits(g)) return cudaErrorInvalidValue;
+    const uint32_t nb = uint32_t(g.span >> g.lg_seg);
+    const size_t smem = (size_t(1) << g.lg_seg) * 4;
+    static std::atomic<uint64_t> attr_done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (!(attr_done.load() & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(k_incidence_seg, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(size_t(1) << 17));
+        if (e != cudaSuccess) return e;
+        attr_done.fetch_or(bit);
+    }
+    const uint64_t tasks = uint64_t(S) * nb;
+    const unsigned grid = unsigned(std::min<uint64_t>(tasks, uint64_t(num_sms())));
+    k_incidence_seg<<<grid, kIncSegThreads, smem, st>>>(loc, start, S, nb, g, seg_ends, W, err, drop);
+    return cudaGetLastError();
+}
+
 // Initial items: every vertex of degree one with its edge, for the shards
 // [s_lo, s_hi) of one peeling batch. A block takes chunks of kSeedPer * kFT
 // vertices and reserves the chunk's queue slots with one atomic.
@@ -486,7 +575,6 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
 // atomic.
 constexpr int kTile = 4096;
 constexpr int kTileThreads = 256;
-constexpr uint32_t kSegBins = 2048;  // segment groups per shard
 
 __device__ __forceinline__ uint32_t seg_bin(uint64_t x, const Geom& g, uint32_t sshift) {
     return uint32_t(mulhi(x, g.span) >> g.lg_seg) >> sshift;
