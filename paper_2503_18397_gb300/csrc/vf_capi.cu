@@ -419,8 +419,9 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
     DevBuf W, queue, claimed, pv, rec, ctr;
+    const bool own_incidence = seg_ends && vf::incidence_seg_fits(g);  // writes every vertex word
     VF_CK(W.alloc(V * 4, st));
-    VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
+    if (!own_incidence) VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
     VF_CK(queue.alloc(V * 8, st));
     VF_CK(cudaMemsetAsync(queue.p, 0xFF, V * 8, st));
     const uint64_t ewords = std::max<uint64_t>((n + 31) / 32, 1), vwords = std::max<uint64_t>((V + 31) / 32, 1);
@@ -461,7 +462,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.stall = g_debug_stall_assign.load() ? 1u : 0u;
     {
         PhaseTimer t(kPhAccum, st);
-        if (seg_ends && vf::incidence_seg_fits(g))
+        if (own_incidence)
             VF_CK(vf::launch_incidence_seg(loc, n, start, a.S, g, seg_ends, a.W, a.err, drop, st));
         else
             VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, drop, st));

@@ -130,13 +130,14 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
     }
 }
 
-// The same incidence over segment-ordered edges, a block per (shard, segment
-// of the first vertex) bin: the bin's first vertices all lie in that segment,
-// so they accumulate in shared memory and reach the vertex words in one
-// coalesced pass of fetch-and-adds; the second and third vertices go to the
-// vertex words directly. seg_ends[i]: one past the last edge of bin i (bins in
-// (shard, segment) order, one segment each). A degree that wraps shows as the
-// five-bit degree fields of the two parts summing past 31.
+// The same incidence over segment-ordered edges, owner-computes: a block owns
+// one segment t of one shard at a time and accumulates, in shared memory, every
+// contribution that lands in it: the first vertices of the edges of bin t, the
+// second vertices of bin t - 1 and the third vertices of bin t - 2 (edges start
+// in a segment and reach the next two). It then stores the segment's vertex
+// words, so no global atomic is needed and the words need no zeroing before.
+// An edge is read by three blocks. seg_ends[i]: one past the last edge of bin i
+// (bins in (shard, segment) order, one segment each, l = T - 2 bins a shard).
 constexpr int kIncSegThreads = 1024;
 constexpr uint32_t kSegBins = 2048;  // segment groups per shard in the segment order (below)
 
@@ -148,44 +149,36 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
                                                                   const uint32_t* __restrict__ drop) {
     extern __shared__ uint32_t sw[];
     const uint32_t seg = 1u << g.lg_seg;
-    const uint64_t tasks = uint64_t(S) * nb;
+    const uint32_t T = nb + 2;  // segments of a shard
+    const uint64_t tasks = uint64_t(S) * T;
     for (uint64_t task = blockIdx.x; task < tasks; task += gridDim.x) {
-        const uint64_t lo = task ? __ldg(seg_ends + task - 1) : 0ull, hi = __ldg(seg_ends + task);
-        if (lo == hi) continue;  // uniform over the block
-        const uint32_t sh = uint32_t(task / nb);
-        const uint32_t sg = uint32_t(task % nb);
+        const uint32_t sh = uint32_t(task / T);
+        const uint32_t t = uint32_t(task % T);
         const uint64_t st0 = __ldg(start + sh);
-        const uint64_t base = uint64_t(sh) * g.cells;
-        const uint64_t seg0 = uint64_t(sg) << g.lg_seg;  // shard-local cell of the segment's first vertex
         for (uint32_t i = threadIdx.x; i < seg; i += blockDim.x) sw[i] = 0;
         __syncthreads();
-        for (uint64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-            if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
-            const uint32_t inc = 1u + (uint32_t(e - st0) << 5);
-            uint64_t v[4];
-            edge_of(g, __ldg(loc + e), v);
-            const uint64_t r0 = v[0] - seg0;
-            uint32_t old[3];
-            if (r0 < seg) {
-                atomicAdd(sw + r0, inc);
-                old[0] = 0;
-            } else {  // not this bin's segment (cannot happen for segment-ordered edges)
-                old[0] = atomicAdd(W + base + v[0], inc);
+        bool wrap = false;
+#pragma unroll 1
+        for (uint32_t k = 0; k < 3; k++) {  // vertex k of the edges of bin t - k
+            if (t < k || t - k >= nb) continue;
+            const uint64_t bin = uint64_t(sh) * nb + (t - k);
+            const uint64_t lo = bin ? __ldg(seg_ends + bin - 1) : 0ull, hi = __ldg(seg_ends + bin);
+            const uint64_t seg0 = uint64_t(t) << g.lg_seg;
+            for (uint64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+                if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
+                const uint32_t inc = 1u + (uint32_t(e - st0) << 5);
+                uint64_t v[4];
+                edge_of(g, __ldg(loc + e), v);
+                const uint64_t vk = k == 0 ? v[0] : k == 1 ? v[1] : v[2];
+                const uint64_t r = vk - seg0;  // < seg: vertex k of a bin t - k edge lies in segment t
+                if (r < seg) wrap |= (atomicAdd(sw + r, inc) & 31u) == 31u;
+                else wrap = true;  // cannot happen for segment-ordered edges
             }
-            old[1] = atomicAdd(W + base + v[1], inc);
-            old[2] = atomicAdd(W + base + v[2], inc);
-#pragma unroll
-            for (int k = 0; k < 3; k++)
-                if ((old[k] & 31u) == 31u) atomicOr(err, kErrDegOverflow);
         }
+        if (wrap) atomicOr(err, kErrDegOverflow);
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < seg; i += blockDim.x) {
-            const uint32_t w = sw[i];
-            if (w) {
-                const uint32_t o = atomicAdd(W + base + seg0 + i, w);
-                if ((o & 31u) + (w & 31u) > 31u) atomicOr(err, kErrDegOverflow);
-            }
-        }
+        uint32_t* out = W + uint64_t(sh) * g.cells + (uint64_t(t) << g.lg_seg);
+        for (uint32_t i = threadIdx.x; i < seg; i += blockDim.x) out[i] = sw[i];
         __syncthreads();
     }
 }
@@ -213,7 +206,7 @@ cudaError_t launch_incidence_seg(const uint64_t* loc, uint64_t n, const unsigned
         if (e != cudaSuccess) return e;
         attr_done.fetch_or(bit);
     }
-    const uint64_t tasks = uint64_t(S) * nb;
+    const uint64_t tasks = uint64_t(S) * (nb + 2);
     const unsigned grid = unsigned(std::min<uint64_t>(tasks, uint64_t(num_sms())));
     k_incidence_seg<<<grid, kIncSegThreads, smem, st>>>(loc, start, S, nb, g, seg_ends, W, err, drop);
     return cudaGetLastError();
