@@ -460,6 +460,8 @@ def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse, k=3):
         kb = KERNEL_BYTES[ph](b, kind)
         if ph == "scatter" and fuse:  # segment sort: signatures read twice, written once (values once more)
             kb += _seg_sort_bytes(kind)
+        if ph == "incidence" and fuse:  # owner-computes: three signature reads, one vertex-word store
+            kb = 3 * 8.0 + 4.0 * 1.105
         per_phase[ph] = {"ms_total": round(ms, 3), "kernels": cnt, "passes": passes[ph],
                          "ms_per_pass": round(ms / passes[ph], 4), "share": round(ms / total, 4),
                          "achieved_gbs": round(_algo(ph, b, kind, k) * units[ph] / (ms * 1e-3) / 1e9, 2),
@@ -469,6 +471,8 @@ def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse, k=3):
     if dom:
         d = per_phase[dom]
         kb = KERNEL_BYTES[dom](b, kind) + (_seg_sort_bytes(kind) if dom == "scatter" and fuse else 0)
+        if dom == "incidence" and fuse:
+            kb = 3 * 8.0 + 4.0 * 1.105
         roof = {"bound": "hbm", "kernel": dom, "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": round(d["achieved_gbs"] / hbm, 4), "traffic": TRAFFIC.get((workload, dom)),
                 "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_unit": _algo(dom, b, kind, k),
