@@ -454,6 +454,10 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.pv = pv.as<uint32_t>();
     a.rec = rec.as<uint4>();
     a.rc = rc.as<uint32_t>();
+    if (g.regime == VF_REGIME_FUSE && in.shards > 0) {
+        const uint64_t l = g.span >> g.lg_seg;  // start segments of a shard
+        a.epsg = l ? uint32_t(std::min<uint64_t>(n / in.shards / l, 0xFFFFFFFFull)) : 0u;
+    }
     a.ctr = ctr.as<uint32_t>();
     a.err = a.ctr + vf::kFlowErr;
     a.data = data;

@@ -132,6 +132,7 @@ struct FlowArgs {
     uint32_t* rc;                     // record slots taken per shard, one counter per kRcStride words
     uint64_t nrec;                    // assignment: record slots taken by the peel, all shards
     uint64_t rmax;                    // assignment: the most slots any shard took
+    uint32_t epsg;                    // fuse regime: edges per start segment (signature prefetch), 0: none
     uint32_t* ctr;                    // kFlowWords counter words
     uint32_t* err;                    // == ctr + kFlowErr
     uint8_t* data;                    // assignment target
