@@ -36,11 +36,12 @@
 // The compiler barrier keeps the compiler from moving the removals above the
 // shuffle.
 //
-// Assignment is a dataflow in decreasing slot order per shard: once final, a vertex's
-// value word (64 bits, in the queue's memory) holds its value with bit 32 set (vertices no edge was peeled from are
-// final from the start, value 0); an edge waits (bounded) until its two other
-// vertices are final. An edge only waits on edges of larger slots, which were
-// taken before it, so the earliest unfinished edge can always proceed.
+// Assignment is a dataflow in decreasing slot order per shard: once final, a
+// vertex's value word (64 bits, in the queue's memory) holds its value with bit
+// 32 set (vertices no edge was peeled from are final from the start, value 0);
+// an edge waits (bounded) until its two other vertices are final. An edge only
+// waits on edges of its shard with larger slots, which were handed out before
+// it, so the earliest unfinished edge can always proceed.
 #include <atomic>
 
 #include <cuda/atomic>
