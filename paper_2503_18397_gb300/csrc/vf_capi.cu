@@ -333,12 +333,13 @@ vf_status h2d(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
 vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc, const uint32_t* val,
                        const unsigned long long* start, uint8_t* data, cudaStream_t st, uint64_t* peeled,
                        uint64_t* rounds_out, uint64_t cell_base, const uint32_t* drop, uint64_t ndrop,
-                       DevBuf* claimed_out) {
+                       DevBuf* claimed_out, const unsigned long long* seg_ends = nullptr) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
+    const bool own_incidence = seg_ends && vf::incidence_seg_fits(g);  // writes every vertex word
     DevBuf W, claimed, f0, f1, rec, rec3, roff, ctr;
     VF_CK(W.alloc(V * 4, st));
-    VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
+    if (!own_incidence) VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
     VF_CK(claimed.alloc(((n + 31) / 32) * 4, st));
     if (drop)  // dropped duplicates count as claimed: they are never peeled
         VF_CK(cudaMemcpyAsync(claimed.p, drop, ((n + 31) / 32) * 4, cudaMemcpyDeviceToDevice, st));
@@ -379,7 +380,10 @@ vf_status solve_rounds(const vf_info& in, const vf::Geom& g, const uint64_t* loc
     a.cell_base = cell_base;
     {
         PhaseTimer t(kPhAccum, st);
-        VF_CK(vf::launch_accumulate(loc, n, start, a.S, g, a.W, a.err, drop, st));
+        if (own_incidence)
+            VF_CK(vf::launch_incidence_seg(loc, n, start, a.S, g, seg_ends, a.W, a.err, drop, true, st));
+        else
+            VF_CK(vf::launch_accumulate(loc, n, start, a.S, g, a.W, a.err, drop, st));
     }
     {
         PhaseTimer t(kPhPeel, st);
@@ -467,7 +471,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     {
         PhaseTimer t(kPhAccum, st);
         if (own_incidence)
-            VF_CK(vf::launch_incidence_seg(loc, n, start, a.S, g, seg_ends, a.W, a.err, drop, st));
+            VF_CK(vf::launch_incidence_seg(loc, n, start, a.S, g, seg_ends, a.W, a.err, drop, false, st));
         else
             VF_CK(vf::launch_incidence32(loc, n, start, a.S, g, a.W, a.err, drop, st));
     }
@@ -677,7 +681,8 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc_i
                             bins.p ? bins.as<unsigned long long>() : nullptr);
         } else if (use == VF_SOLVER_ROUNDS) {
             rs = solve_rounds(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base,
-                              drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr);
+                              drop.as<uint32_t>(), ndrop, dedup ? &claimed : nullptr,
+                              bins.p ? bins.as<unsigned long long>() : nullptr);
         }
         if (rs != VF_EBUILD || !claimed.p) return rs;
         // unpeeled edges of a failed attempt: any duplicates?

@@ -134,15 +134,17 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
 
 // The same incidence over segment-ordered edges, owner-computes: a block owns
 // one segment t of one shard at a time and accumulates, in shared memory, every
-// contribution that lands in it: the first vertices of the edges of bin t, the
-// second vertices of bin t - 1 and the third vertices of bin t - 2 (edges start
-// in a segment and reach the next two). It then stores the segment's vertex
-// words, so no global atomic is needed and the words need no zeroing before.
-// An edge is read by three blocks. seg_ends[i]: one past the last edge of bin i
-// (bins in (shard, segment) order, one segment each, l = T - 2 bins a shard).
+// contribution that lands in it: vertex j of the edges of bin t - j for j < k
+// (edges start in a segment and reach the next k - 1). It then stores the
+// segment's vertex words, so no global atomic is needed and the words need no
+// zeroing before. An edge is read by k blocks. seg_ends[i]: one past the last
+// edge of bin i (bins in (shard, segment) order, one segment each, l = T - k + 1
+// bins a shard). XOR: the round solver's words (degree, XOR of the indices)
+// instead of the worklist solver's (degree, sum of the indices).
 constexpr int kIncSegThreads = 1024;
 constexpr uint32_t kSegBins = 2048;  // segment groups per shard in the segment order (below)
 
+template <bool XOR>
 __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t* __restrict__ loc,
                                                                   const unsigned long long* __restrict__ start,
                                                                   uint32_t S, uint32_t nb, Geom g,
@@ -151,7 +153,8 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
                                                                   const uint32_t* __restrict__ drop) {
     extern __shared__ uint32_t sw[];
     const uint32_t seg = 1u << g.lg_seg;
-    const uint32_t T = nb + 2;  // segments of a shard
+    const uint32_t K = g.k == 4 ? 4u : 3u;
+    const uint32_t T = nb + K - 1;  // segments of a shard
     const uint64_t tasks = uint64_t(S) * T;
     for (uint64_t task = blockIdx.x; task < tasks; task += gridDim.x) {
         const uint32_t sh = uint32_t(task / T);
@@ -161,20 +164,26 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
         __syncthreads();
         bool wrap = false;
 #pragma unroll 1
-        for (uint32_t k = 0; k < 3; k++) {  // vertex k of the edges of bin t - k
+        for (uint32_t k = 0; k < K; k++) {  // vertex k of the edges of bin t - k
             if (t < k || t - k >= nb) continue;
             const uint64_t bin = uint64_t(sh) * nb + (t - k);
             const uint64_t lo = bin ? __ldg(seg_ends + bin - 1) : 0ull, hi = __ldg(seg_ends + bin);
             const uint64_t seg0 = uint64_t(t) << g.lg_seg;
             for (uint64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
                 if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
-                const uint32_t inc = 1u + (uint32_t(e - st0) << 5);
+                const uint32_t el = uint32_t(e - st0);
                 uint64_t v[4];
                 edge_of(g, __ldg(loc + e), v);
-                const uint64_t vk = k == 0 ? v[0] : k == 1 ? v[1] : v[2];
+                const uint64_t vk = k == 0 ? v[0] : k == 1 ? v[1] : k == 2 ? v[2] : v[3];
                 const uint64_t r = vk - seg0;  // < seg: vertex k of a bin t - k edge lies in segment t
-                if (r < seg) wrap |= (atomicAdd(sw + r, inc) & 31u) == 31u;
-                else wrap = true;  // cannot happen for segment-ordered edges
+                if (r >= seg) {
+                    wrap = true;  // cannot happen for segment-ordered edges
+                } else if (XOR) {
+                    wrap |= (atomicAdd(sw + r, 1u) & 31u) == 31u;
+                    atomicXor(sw + r, el << 5);
+                } else {
+                    wrap |= (atomicAdd(sw + r, 1u + (el << 5)) & 31u) == 31u;
+                }
             }
         }
         if (wrap) atomicOr(err, kErrDegOverflow);
@@ -186,14 +195,14 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
 }
 
 bool incidence_seg_fits(const Geom& g) {
-    if (g.regime != kRegimeFuse || g.k != 3 || g.lg_seg > 15 || g.lg_seg < 5) return false;
+    if (g.regime != kRegimeFuse || (g.k != 3 && g.k != 4) || g.lg_seg > 15 || g.lg_seg < 5) return false;
     const uint32_t l = uint32_t(g.span >> g.lg_seg);
     return l >= 1 && l <= kSegBins;  // one segment per bin of the segment order
 }
 
 cudaError_t launch_incidence_seg(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
                                  const Geom& g, const unsigned long long* seg_ends, uint32_t* W, uint32_t* err,
-                                 const uint32_t* drop, cudaStream_t st) {
+                                 const uint32_t* drop, bool xor_words, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     if (!incidence_seg_fits(g)) return cudaErrorInvalidValue;
     const uint32_t nb = uint32_t(g.span >> g.lg_seg);
@@ -203,14 +212,20 @@ cudaError_t launch_incidence_seg(const uint64_t* loc, uint64_t n, const unsigned
     cudaGetDevice(&dev);
     const uint64_t bit = uint64_t(1) << (dev & 63);
     if (!(attr_done.load() & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(k_incidence_seg, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_incidence_seg<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(size_t(1) << 17));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_incidence_seg<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(size_t(1) << 17));
         if (e != cudaSuccess) return e;
         attr_done.fetch_or(bit);
     }
-    const uint64_t tasks = uint64_t(S) * (nb + 2);
+    const uint64_t tasks = uint64_t(S) * (nb + (g.k == 4 ? 3 : 2));
     const unsigned grid = unsigned(std::min<uint64_t>(tasks, uint64_t(num_sms())));
-    k_incidence_seg<<<grid, kIncSegThreads, smem, st>>>(loc, start, S, nb, g, seg_ends, W, err, drop);
+    if (xor_words)
+        k_incidence_seg<true><<<grid, kIncSegThreads, smem, st>>>(loc, start, S, nb, g, seg_ends, W, err, drop);
+    else
+        k_incidence_seg<false><<<grid, kIncSegThreads, smem, st>>>(loc, start, S, nb, g, seg_ends, W, err, drop);
     return cudaGetLastError();
 }
 

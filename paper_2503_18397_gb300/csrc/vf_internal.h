@@ -145,13 +145,14 @@ cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned l
 // The same over segment-ordered edges (launch_segment_order): a block per
 // (shard, segment) accumulates every contribution to that segment in shared
 // memory and stores its vertex words (W needs no zeroing); seg_ends: the
-// segment order's bin ends. Fuse graphs with k = 3, segments of 2^5..2^15
+// segment order's bin ends. Fuse graphs (k = 3 or 4), segments of 2^5..2^15
 // cells, one segment per bin (incidence_seg_fits); cudaErrorInvalidValue
 // otherwise.
 bool incidence_seg_fits(const Geom& g);
+// xor_words: the round solver's words (degree, XOR of the edge indices).
 cudaError_t launch_incidence_seg(const uint64_t* loc, uint64_t n, const unsigned long long* start, uint32_t S,
                                  const Geom& g, const unsigned long long* seg_ends, uint32_t* W, uint32_t* err,
-                                 const uint32_t* drop, cudaStream_t st);
+                                 const uint32_t* drop, bool xor_words, cudaStream_t st);
 // Marks in `drop` (if given) every edge not set in `claimed` (if given) whose
 // (shard, local signature) an earlier such edge already has; table: cap (a
 // power of two, >= 2x the edges inserted) zeroed words; *ndrop counts the
