@@ -61,7 +61,7 @@ enum { VF_REGIME_FUSE = 1, VF_REGIME_LGE = 2, VF_REGIME_MWHC = 3 };
  * edges, so a peeling step is one fetch-and-add per vertex; grid-wide rounds
  * for the initial cascades, then one CTA per shard for the waves that sweep
  * its segments (Sec. 4.5); assignment in reverse rounds. It needs fuse graphs
- * with b <= 57 - 2 lg_seg and at most 1024 shards; other structures, and
+ * with k = 3, b <= 57 - 2 lg_seg and at most 1024 shards; other structures, and
  * shards whose waves outgrow its per-round capacity, are solved by
  * VF_SOLVER_FLOW. */
 enum { VF_SOLVER_FLOW = 0, VF_SOLVER_ROUNDS = 1, VF_SOLVER_WAVE = 2 };
@@ -97,7 +97,8 @@ typedef struct {
     int fuse_solver;         /* VF_SOLVER_FLOW (default), VF_SOLVER_ROUNDS or VF_SOLVER_WAVE */
     int arity;               /* vertices per edge of a fuse-regime structure: 3 (default) or 4
                                 (4-uniform fuse graphs, Sec. 4.2 with k = 4: one more probe per
-                                query for less space; solved by VF_SOLVER_ROUNDS). The LGE and
+                                query for less space; VF_SOLVER_FLOW and VF_SOLVER_ROUNDS peel
+                                it, VF_SOLVER_WAVE hands it to VF_SOLVER_FLOW). The LGE and
                                 MWHC regimes are 3-uniform whatever this says. */
 } vf_params;
 

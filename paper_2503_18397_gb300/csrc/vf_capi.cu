@@ -422,7 +422,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
                      const unsigned long long* seg_ends = nullptr) {
     const uint64_t n = in.n_eff;
     const uint64_t V = in.total_cells;
-    DevBuf W, queue, claimed, pv, rec, ctr;
+    DevBuf W, queue, claimed, pv, rec, rec3, ctr;
     const bool own_incidence = seg_ends && vf::incidence_seg_fits(g);  // writes every vertex word
     VF_CK(W.alloc(V * 4, st));
     if (!own_incidence) VF_CK(cudaMemsetAsync(W.p, 0, V * 4, st));
@@ -437,6 +437,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     VF_CK(pv.alloc(vwords * 4, st));
     VF_CK(cudaMemsetAsync(pv.p, 0, vwords * 4, st));
     VF_CK(rec.alloc(std::max<uint64_t>(V, 1) * 16, st));  // one slot per item, at most one item per vertex
+    if (g.k == 4) VF_CK(rec3.alloc(std::max<uint64_t>(V, 1) * 4, st));  // the third other vertex
     VF_CK(ctr.alloc(vf::kFlowWords * 4, st));
     VF_CK(cudaMemsetAsync(ctr.p, 0, vf::kFlowWords * 4, st));
     DevBuf rc;  // record slots per shard, one 128-byte line each
@@ -457,6 +458,7 @@ vf_status solve_flow(const vf_info& in, const vf::Geom& g, const uint64_t* loc, 
     a.claimed_bits = n;
     a.pv = pv.as<uint32_t>();
     a.rec = rec.as<uint4>();
+    a.rec3 = g.k == 4 ? rec3.as<uint32_t>() : nullptr;
     a.rc = rc.as<uint32_t>();
     if (g.regime == VF_REGIME_FUSE && in.shards > 0) {
         const uint64_t l = g.span >> g.lg_seg;  // start segments of a shard
@@ -666,8 +668,7 @@ vf_status solve_fuse(const vf_info& in, const vf::Geom& g, const uint64_t* loc_i
         DevBuf claimed;
         const bool dedup = pass == 0;
         vf_status rs = VF_EINVAL;
-        // 4-uniform fuse graphs are peeled by the round solver
-        const int use = g.k == 4 ? VF_SOLVER_ROUNDS : solver;
+        const int use = solver;  // the wave solver takes k = 3 only (wave_eligible), else the worklist solver
         bool fallback = use == VF_SOLVER_WAVE && !vf::wave_eligible(g, uint32_t(in.shards));
         if (use == VF_SOLVER_WAVE && !fallback) {
             rs = solve_wave(in, g, loc, val, start, data, st, peeled, rounds_out, cell_base, drop.as<uint32_t>(),

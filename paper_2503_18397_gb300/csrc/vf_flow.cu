@@ -123,11 +123,13 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
         uint64_t v[4];
         edge_of(g, __ldg(loc + e), v);
         const uint64_t base = uint64_t(s) * g.cells;
-        uint32_t old[3];
+        const int kk = g.k == 4 ? 4 : 3;
+        uint32_t old[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int k = 0; k < 3; k++) old[k] = atomicAdd(W + base + v[k], inc);
+        for (int k = 0; k < 4; k++)
+            if (k < kk) old[k] = atomicAdd(W + base + v[k], inc);
 #pragma unroll
-        for (int k = 0; k < 3; k++)
+        for (int k = 0; k < 4; k++)
             if ((old[k] & 31u) == 31u) atomicOr(err, kErrDegOverflow);
     }
 }
@@ -387,12 +389,17 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
                     uint64_t vv[4];
                     edge_of(a.g, local, vv);
                     const uint32_t lv = v - base;
+                    const bool four = a.g.k == 4;
+                    // the vertices other than v, in edge order (two, or three for k = 4)
                     const uint32_t c0 = uint32_t(vv[0]), c1 = uint32_t(vv[1]), c2 = uint32_t(vv[2]);
-                    const uint32_t o0 = base + (c0 == lv ? c1 : c0);             // the two vertices other
-                    const uint32_t o1 = base + (c0 != lv && c1 != lv ? c1 : c2);  // than v, in edge order
+                    const uint32_t c3 = four ? uint32_t(vv[3]) : 0u;
+                    const uint32_t o0 = base + (c0 == lv ? c1 : c0);
+                    const uint32_t o1 = base + (c0 == lv || c1 == lv ? c2 : c1);
+                    const uint32_t o2 = base + (c0 == lv || c1 == lv || c2 == lv ? c3 : c2);
                     // the removals first; the prefetches below go out while they are in flight
                     const uint32_t a0 = atomicAdd(a.W + o0, 0u - dec);
                     const uint32_t a1 = atomicAdd(a.W + o1, 0u - dec);
+                    const uint32_t a2 = four ? atomicAdd(a.W + o2, 0u - dec) : 0u;
                     if (a.g.regime == kRegimeFuse) {
                         // the waves sweep the segments: warm L2 with a line of vertex
                         // words kWavePrefetch segments ahead, in either direction
@@ -434,10 +441,31 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
                             pe = uint32_t(st0 + (w1 >> 5));
                         }
                     }
-                    if (rbase < cells)  // a shard has at most one item per vertex
+                    if (four && ((a2 - dec) & 31u) == 1u) {
+                        const uint32_t e2 = uint32_t(st0 + ((a2 - dec) >> 5));
+                        if (!next) {
+                            next = true;
+                            nv = o2;
+                            ne = e2;
+                        } else if (!pend) {
+                            pend = true;
+                            pu = o2;
+                            pe = e2;
+                        } else {  // a third vertex freed at once (rare): to the queue now
+                            const unsigned long long qs = atomicAdd(slots, 1ull << 32) >> 32;
+                            if (qs < a.queue_cap)
+                                dev_atomic64(a.queue[qs]).store((unsigned long long)o2 << 32 | e2,
+                                                                cuda::memory_order_relaxed);
+                            else
+                                atomicOr(a.err, kErrFrontier);
+                        }
+                    }
+                    if (rbase < cells) {  // a shard has at most one item per vertex
                         a.rec[rs] = make_uint4(v, o0, o1, a.val ? value : fingerprint_slice(local, a.g.b, a.g.fpb, a.g.fps));
-                    else
+                        if (four) a.rec3[rs] = o2;
+                    } else {
                         atomicOr(a.err, kErrFrontier);
+                    }
                 } else {
                     if (rbase < cells) a.rec[rs].x = kHole;
                     else atomicOr(a.err, kErrFrontier);
@@ -549,12 +577,17 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
         if (base >= count) break;
         const uint64_t k = base + lane;
         uint4 r = make_uint4(kHole, 0, 0, 0);
+        uint32_t r3 = kHole;
         if (k < count) {
             const uint64_t c = k >> 5;  // a warp's 32 positions: consecutive records of one shard
             const uint32_t s = uint32_t(c % a.S);
             const uint64_t j = ((c / a.S) << 5) + (k & 31u);
             const uint32_t taken = __ldg(a.rc + s * kRcStride);
-            if (j < taken) r = __ldg(a.rec + s * cells + (taken - 1 - j));
+            if (j < taken) {
+                const uint64_t rs = s * cells + (taken - 1 - j);
+                r = __ldg(a.rec + rs);
+                if (a.rec3 && r.x != kHole) r3 = __ldg(a.rec3 + rs);  // third other vertex (k = 4)
+            }
         }
         bool done = r.x == kHole;
         uint32_t polls = 0;
@@ -564,8 +597,10 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
             if (!done) {
                 const unsigned long long wy = dev_atomic64(a.fv[r.y]).load(cuda::memory_order_relaxed);
                 const unsigned long long wz = dev_atomic64(a.fv[r.z]).load(cuda::memory_order_relaxed);
-                if (wy & wz & kFinal) {
-                    const uint32_t x = (r.w ^ uint32_t(wy) ^ uint32_t(wz)) & vmask;
+                const unsigned long long w3 =
+                    r3 != kHole ? dev_atomic64(a.fv[r3]).load(cuda::memory_order_relaxed) : kFinal;
+                if (wy & wz & w3 & kFinal) {
+                    const uint32_t x = (r.w ^ uint32_t(wy) ^ uint32_t(wz) ^ uint32_t(w3)) & vmask;
                     dev_atomic64(a.fv[r.x]).store(kFinal | x, cuda::memory_order_relaxed);
                     cell_put_zero(a.data, b, a.cell_base + r.x, x);
                     done = true;

@@ -129,6 +129,7 @@ struct FlowArgs {
     uint32_t* pv;                     // one bit per vertex: an edge was peeled from it
     uint4* rec;                       // per slot {peeled vertex, other, other, value}; x = ~0: empty;
                                       // shard s owns slots [s*cells, (s+1)*cells)
+    uint32_t* rec3;                   // k = 4: per slot the third other vertex (else NULL)
     uint32_t* rc;                     // record slots taken per shard, one counter per kRcStride words
     uint64_t nrec;                    // assignment: record slots taken by the peel, all shards
     uint64_t rmax;                    // assignment: the most slots any shard took
