@@ -309,6 +309,8 @@ __global__ void __launch_bounds__(kFT) k_count_claims(FlowArgs a, uint64_t words
 // a fork is subtracted before its chain's end is added); done == tail means no
 // chain is running. Reading done, then tail, and finding them equal means none
 // ran when done was read, so none can start again.
+// K: vertices per edge (3, or 4 for a 4-uniform fuse graph), fixed at compile time.
+template <int K>
 __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
     const unsigned lane = lane32();
     const uint32_t cells = uint32_t(a.g.cells);
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(kFT) k_flow_peel(FlowArgs a) {
                     uint64_t vv[4];
                     edge_of(a.g, local, vv);
                     const uint32_t lv = v - base;
-                    const bool four = a.g.k == 4;
+                    constexpr bool four = K == 4;
                     // the vertices other than v, in edge order (two, or three for k = 4)
                     const uint32_t c0 = uint32_t(vv[0]), c1 = uint32_t(vv[1]), c2 = uint32_t(vv[2]);
                     const uint32_t c3 = four ? uint32_t(vv[3]) : 0u;
@@ -563,6 +565,7 @@ __global__ void __launch_bounds__(kFT) k_final_init(FlowArgs a) {
 // together; 2.5% faster than interleaving single records), so every shard's
 // dataflow advances at once; a record waits only on larger slots of its own
 // shard, which come at smaller positions.
+template <int K>
 __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
     const int b = a.g.b;
     const uint64_t count = ((a.rmax + 31) & ~uint64_t(31)) * a.S;
@@ -586,7 +589,7 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
             if (j < taken) {
                 const uint64_t rs = s * cells + (taken - 1 - j);
                 r = __ldg(a.rec + rs);
-                if (a.rec3 && r.x != kHole) r3 = __ldg(a.rec3 + rs);  // third other vertex (k = 4)
+                if (K == 4 && r.x != kHole) r3 = __ldg(a.rec3 + rs);  // third other vertex
             }
         }
         bool done = r.x == kHole;
@@ -598,7 +601,7 @@ __global__ void __launch_bounds__(kFT) k_flow_assign(FlowArgs a) {
                 const unsigned long long wy = dev_atomic64(a.fv[r.y]).load(cuda::memory_order_relaxed);
                 const unsigned long long wz = dev_atomic64(a.fv[r.z]).load(cuda::memory_order_relaxed);
                 const unsigned long long w3 =
-                    r3 != kHole ? dev_atomic64(a.fv[r3]).load(cuda::memory_order_relaxed) : kFinal;
+                    K == 4 && r3 != kHole ? dev_atomic64(a.fv[r3]).load(cuda::memory_order_relaxed) : kFinal;
                 if (wy & wz & w3 & kFinal) {
                     const uint32_t x = (r.w ^ uint32_t(wy) ^ uint32_t(wz) ^ uint32_t(w3)) & vmask;
                     dev_atomic64(a.fv[r.x]).store(kFinal | x, cuda::memory_order_relaxed);
@@ -883,7 +886,8 @@ cudaError_t launch_flow_peel(const FlowArgs& a, cudaStream_t st) {
         const uint32_t s1 = s0 + per < a.S ? s0 + per : a.S;
         if (s0 > 0) k_rebase_head<<<1, 1, 0, st>>>(a);
         k_flow_seed<<<grid_for((uint64_t(s1 - s0) * a.g.cells + kSeedPer - 1) / kSeedPer), kFT, 0, st>>>(a, s0, s1);
-        k_flow_peel<<<worker_grid(), kFT, 0, st>>>(a);
+        if (a.g.k == 4) k_flow_peel<4><<<worker_grid(), kFT, 0, st>>>(a);
+        else k_flow_peel<3><<<worker_grid(), kFT, 0, st>>>(a);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -896,7 +900,8 @@ cudaError_t launch_flow_assign(const FlowArgs& a, cudaStream_t st) {
     k_final_init<<<grid_for(uint64_t(a.S) * a.g.cells), kFT, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.nrec == 0 || a.rmax == 0) return e;
-    k_flow_assign<<<assign_grid(a.g), kFT, 0, st>>>(a);
+    if (a.g.k == 4) k_flow_assign<4><<<assign_grid(a.g), kFT, 0, st>>>(a);
+    else k_flow_assign<3><<<assign_grid(a.g), kFT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
