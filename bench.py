@@ -484,7 +484,7 @@ def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse, k=3):
 # Per-launch DRAM traffic (bytes) from ncu captures of the same kernels, scaled
 # from the captured case by units processed; absent until a capture of the
 # current kernel exists (profiles/ holds the summaries).
-TRAFFIC = {("c2", "peel"): round(1118.92e6 / 2e7 * 1e8),   # k_flow_peel, one launch per attempt at 1e8
+TRAFFIC = {("c2", "peel"): round(1120.07e6 / 2e7 * 1e8),   # k_flow_peel, one launch per attempt at 1e8
            ("c2", "query"): round(189.42e6 / 2e7 * 1e8),  # k_query, one launch per 1e8 queries
            ("c3", "lge"): round(788.86e6 + 806.24e6)}     # k_lge medium configuration, full-size capture
 
