@@ -443,7 +443,13 @@ def run_gpu(args):
 # through scatter, incidence and peel (or the LGE solver); a successful one also
 # through assignment; every step queries 2n keys.
 def _algo(ph, b, kind, k):
-    return ALGO_BYTES[ph](b, kind, k) if ph == "query" else ALGO_BYTES[ph](b, kind)
+    """Algorithmic bytes per unit of a phase; a k-uniform graph has k vertex
+    updates per edge in incidence and peel, and k - 1 other values to read in
+    the assignment (the models above are written for k = 3)."""
+    if ph == "query":
+        return ALGO_BYTES[ph](b, kind, k)
+    extra = (k - 3) * 64.0 if ph in ("incidence", "peel", "assign") else 0.0
+    return ALGO_BYTES[ph](b, kind) + extra
 
 
 def phase_table(phases, n, steps, b, kind, hbm, peak_kind, workload, fuse, k=3):
