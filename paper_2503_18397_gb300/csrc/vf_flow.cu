@@ -141,9 +141,15 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
 // segment's vertex words, so no global atomic is needed and the words need no
 // zeroing before. An edge is read by k blocks. seg_ends[i]: one past the last
 // edge of bin i (bins in (shard, segment) order, one segment each, l = T - k + 1
-// bins a shard). XOR: the round solver's words (degree, XOR of the indices)
-// instead of the worklist solver's (degree, sum of the indices).
+// bins a shard). A segment larger than shared memory holds (2^15 words) is owned
+// in chunks of 2^15 cells by as many blocks, each reading the segment's bins and
+// keeping the contributions that land in its chunk (the neighbouring chunks'
+// blocks read the same bins at about the same time, so L2 serves the repeats).
+// XOR: the round solver's words (degree, XOR of the indices) instead of the
+// worklist solver's (degree, sum of the indices).
 constexpr int kIncSegThreads = 1024;
+constexpr uint32_t kIncSegLgChunk = 15;  // cells a block owns at once: 128 KB of shared memory
+constexpr uint32_t kIncSegLgMax = 18;    // larger segments: at most 8 chunks, each reading the bins
 constexpr uint32_t kSegBins = 2048;  // segment groups per shard in the segment order (below)
 
 template <bool XOR>
@@ -154,15 +160,17 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
                                                                   uint32_t* __restrict__ W, uint32_t* err,
                                                                   const uint32_t* __restrict__ drop) {
     extern __shared__ uint32_t sw[];
-    const uint32_t seg = 1u << g.lg_seg;
+    const uint32_t lgc = g.lg_seg < kIncSegLgChunk ? g.lg_seg : kIncSegLgChunk;
+    const uint32_t chunk = 1u << lgc, nch = 1u << (g.lg_seg - lgc);
     const uint32_t K = g.k == 4 ? 4u : 3u;
     const uint32_t T = nb + K - 1;  // segments of a shard
-    const uint64_t tasks = uint64_t(S) * T;
+    const uint64_t tasks = uint64_t(S) * T * nch;
     for (uint64_t task = blockIdx.x; task < tasks; task += gridDim.x) {
-        const uint32_t sh = uint32_t(task / T);
-        const uint32_t t = uint32_t(task % T);
+        const uint32_t ch = uint32_t(task % nch);
+        const uint32_t sh = uint32_t(task / nch / T);
+        const uint32_t t = uint32_t(task / nch % T);
         const uint64_t st0 = __ldg(start + sh);
-        for (uint32_t i = threadIdx.x; i < seg; i += blockDim.x) sw[i] = 0;
+        for (uint32_t i = threadIdx.x; i < chunk; i += blockDim.x) sw[i] = 0;
         __syncthreads();
         bool wrap = false;
 #pragma unroll 1
@@ -170,16 +178,18 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
             if (t < k || t - k >= nb) continue;
             const uint64_t bin = uint64_t(sh) * nb + (t - k);
             const uint64_t lo = bin ? __ldg(seg_ends + bin - 1) : 0ull, hi = __ldg(seg_ends + bin);
-            const uint64_t seg0 = uint64_t(t) << g.lg_seg;
+            const uint64_t seg0 = (uint64_t(t) << g.lg_seg) + (uint64_t(ch) << lgc);  // the chunk's first cell
             for (uint64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
                 if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
                 const uint32_t el = uint32_t(e - st0);
                 uint64_t v[4];
                 edge_of(g, __ldg(loc + e), v);
                 const uint64_t vk = k == 0 ? v[0] : k == 1 ? v[1] : k == 2 ? v[2] : v[3];
-                const uint64_t r = vk - seg0;  // < seg: vertex k of a bin t - k edge lies in segment t
-                if (r >= seg) {
-                    wrap = true;  // cannot happen for segment-ordered edges
+                const uint64_t r = vk - seg0;  // vertex k of a bin t - k edge lies in segment t
+                if (r >= chunk) {
+                    // another chunk of the segment (or, if the segment has one chunk,
+                    // impossible for segment-ordered edges)
+                    if (nch == 1) wrap = true;
                 } else if (XOR) {
                     wrap |= (atomicAdd(sw + r, 1u) & 31u) == 31u;
                     atomicXor(sw + r, el << 5);
@@ -190,14 +200,14 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
         }
         if (wrap) atomicOr(err, kErrDegOverflow);
         __syncthreads();
-        uint32_t* out = W + uint64_t(sh) * g.cells + (uint64_t(t) << g.lg_seg);
-        for (uint32_t i = threadIdx.x; i < seg; i += blockDim.x) out[i] = sw[i];
+        uint32_t* out = W + uint64_t(sh) * g.cells + (uint64_t(t) << g.lg_seg) + (uint64_t(ch) << lgc);
+        for (uint32_t i = threadIdx.x; i < chunk; i += blockDim.x) out[i] = sw[i];
         __syncthreads();
     }
 }
 
 bool incidence_seg_fits(const Geom& g) {
-    if (g.regime != kRegimeFuse || (g.k != 3 && g.k != 4) || g.lg_seg > 15 || g.lg_seg < 5) return false;
+    if (g.regime != kRegimeFuse || (g.k != 3 && g.k != 4) || g.lg_seg > kIncSegLgMax || g.lg_seg < 5) return false;
     const uint32_t l = uint32_t(g.span >> g.lg_seg);
     return l >= 1 && l <= kSegBins;  // one segment per bin of the segment order
 }
@@ -208,7 +218,8 @@ cudaError_t launch_incidence_seg(const uint64_t* loc, uint64_t n, const unsigned
     if (n == 0) return cudaSuccess;
     if (!incidence_seg_fits(g)) return cudaErrorInvalidValue;
     const uint32_t nb = uint32_t(g.span >> g.lg_seg);
-    const size_t smem = (size_t(1) << g.lg_seg) * 4;
+    const uint32_t lgc = g.lg_seg < kIncSegLgChunk ? g.lg_seg : kIncSegLgChunk;
+    const size_t smem = (size_t(1) << lgc) * 4;
     static std::atomic<uint64_t> attr_done{0};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -222,7 +233,7 @@ cudaError_t launch_incidence_seg(const uint64_t* loc, uint64_t n, const unsigned
         if (e != cudaSuccess) return e;
         attr_done.fetch_or(bit);
     }
-    const uint64_t tasks = uint64_t(S) * (nb + (g.k == 4 ? 3 : 2));
+    const uint64_t tasks = uint64_t(S) * (nb + (g.k == 4 ? 3 : 2)) << (g.lg_seg - lgc);
     const unsigned grid = unsigned(std::min<uint64_t>(tasks, uint64_t(num_sms())));
     if (xor_words)
         k_incidence_seg<true><<<grid, kIncSegThreads, smem, st>>>(loc, start, S, nb, g, seg_ends, W, err, drop);

@@ -146,7 +146,7 @@ cudaError_t launch_incidence32(const uint64_t* loc, uint64_t n, const unsigned l
 // The same over segment-ordered edges (launch_segment_order): a block per
 // (shard, segment) accumulates every contribution to that segment in shared
 // memory and stores its vertex words (W needs no zeroing); seg_ends: the
-// segment order's bin ends. Fuse graphs (k = 3 or 4), segments of 2^5..2^15
+// segment order's bin ends. Fuse graphs (k = 3 or 4), segments of 2^5..2^18
 // cells, one segment per bin (incidence_seg_fits); cudaErrorInvalidValue
 // otherwise.
 bool incidence_seg_fits(const Geom& g);
