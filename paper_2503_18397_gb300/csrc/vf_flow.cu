@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kFT) k_incidence32(const uint64_t* __restrict_
 constexpr int kIncSegThreads = 1024;
 constexpr uint32_t kIncSegLgChunk = 15;  // cells a block owns at once: 128 KB of shared memory
 constexpr uint32_t kIncSegLgMax = 18;    // larger segments: at most 8 chunks, each reading the bins
+constexpr uint32_t kIncSegUnroll = 8;    // edges a thread loads before using any
 constexpr uint32_t kSegBins = 2048;  // segment groups per shard in the segment order (below)
 
 template <bool XOR>
@@ -179,22 +180,38 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
             const uint64_t bin = uint64_t(sh) * nb + (t - k);
             const uint64_t lo = bin ? __ldg(seg_ends + bin - 1) : 0ull, hi = __ldg(seg_ends + bin);
             const uint64_t seg0 = (uint64_t(t) << g.lg_seg) + (uint64_t(ch) << lgc);  // the chunk's first cell
-            for (uint64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-                if (drop && ((__ldg(drop + (e >> 5)) >> (e & 31u)) & 1u)) continue;
-                const uint32_t el = uint32_t(e - st0);
-                uint64_t v[4];
-                edge_of(g, __ldg(loc + e), v);
-                const uint64_t vk = k == 0 ? v[0] : k == 1 ? v[1] : k == 2 ? v[2] : v[3];
-                const uint64_t r = vk - seg0;  // vertex k of a bin t - k edge lies in segment t
-                if (r >= chunk) {
-                    // another chunk of the segment (or, if the segment has one chunk,
-                    // impossible for segment-ordered edges)
-                    if (nch == 1) wrap = true;
-                } else if (XOR) {
-                    wrap |= (atomicAdd(sw + r, 1u) & 31u) == 31u;
-                    atomicXor(sw + r, el << 5);
-                } else {
-                    wrap |= (atomicAdd(sw + r, 1u + (el << 5)) & 31u) == 31u;
+            const uint64_t step = uint64_t(kIncSegUnroll) * blockDim.x;
+            for (uint64_t e0 = lo + threadIdx.x; e0 < hi; e0 += step) {
+                // all of a thread's signature (and drop-word) loads are issued
+                // before any is used: one load in flight per thread left the
+                // block bound by the load latency, not by bandwidth
+                uint64_t sg[kIncSegUnroll];
+                uint32_t dw[kIncSegUnroll];
+#pragma unroll
+                for (uint32_t u = 0; u < kIncSegUnroll; u++) {
+                    const uint64_t e = e0 + uint64_t(u) * blockDim.x;
+                    sg[u] = e < hi ? __ldg(loc + e) : 0ull;
+                    dw[u] = (drop && e < hi) ? __ldg(drop + (e >> 5)) : 0u;
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < kIncSegUnroll; u++) {
+                    const uint64_t e = e0 + uint64_t(u) * blockDim.x;
+                    if (e >= hi || ((dw[u] >> (e & 31u)) & 1u)) continue;
+                    const uint32_t el = uint32_t(e - st0);
+                    uint64_t v[4];
+                    edge_of(g, sg[u], v);
+                    const uint64_t vk = k == 0 ? v[0] : k == 1 ? v[1] : k == 2 ? v[2] : v[3];
+                    const uint64_t r = vk - seg0;  // vertex k of a bin t - k edge lies in segment t
+                    if (r >= chunk) {
+                        // another chunk of the segment (or, if the segment has one chunk,
+                        // impossible for segment-ordered edges)
+                        if (nch == 1) wrap = true;
+                    } else if (XOR) {
+                        wrap |= (atomicAdd(sw + r, 1u) & 31u) == 31u;
+                        atomicXor(sw + r, el << 5);
+                    } else {
+                        wrap |= (atomicAdd(sw + r, 1u + (el << 5)) & 31u) == 31u;
+                    }
                 }
             }
         }
@@ -687,13 +704,22 @@ __global__ void __launch_bounds__(kTileThreads) k_seg_count(const uint64_t* __re
         for (uint32_t i = threadIdx.x; i < 2 * nb; i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
         const uint32_t f = s_f, split = s_split;
-        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-            const uint64_t x = __ldg(loc + t0 + i);
+        constexpr int kPer = kTile / kTileThreads;
+        uint64_t xs[kPer];  // every load of the tile issued before the first count
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            const uint32_t i = threadIdx.x + uint32_t(j) * kTileThreads;
+            xs[j] = i < m ? __ldg(loc + t0 + i) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; j++) {
+            const uint32_t i = threadIdx.x + uint32_t(j) * kTileThreads;
+            if (i >= m) continue;
             if (s_many) {
                 const uint32_t s = flow_shard_of_edge(start, S, t0 + i);
-                atomicAdd(counts + uint64_t(s) * nb + seg_bin(x, g, sshift), 1ull);
+                atomicAdd(counts + uint64_t(s) * nb + seg_bin(xs[j], g, sshift), 1ull);
             } else {
-                atomicAdd(&s_cnt[(i >= split ? nb : 0u) + seg_bin(x, g, sshift)], 1u);
+                atomicAdd(&s_cnt[(i >= split ? nb : 0u) + seg_bin(xs[j], g, sshift)], 1u);
             }
         }
         __syncthreads();
