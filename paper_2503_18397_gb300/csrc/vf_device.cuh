@@ -150,6 +150,19 @@ __device__ __forceinline__ void edge_of(const Geom& g, uint64_t local, uint64_t 
     }
 }
 
+// Vertex k of a fuse edge whose first vertex lies in segment t - k, as an
+// offset from the first cell of segment t: the cell edge_of gives, less
+// (t << lg_seg). For k >= 1 the segment is already known, so only the remix
+// that places the vertex inside it is computed; for k = 0 the offset is
+// v0 - (t << lg_seg), which wraps to a huge value if v0 lies outside segment t.
+__device__ __forceinline__ uint64_t fuse_vertex_in_segment(const Geom& g, uint64_t local, uint32_t k, uint64_t t) {
+    const uint64_t mask = (uint64_t(1) << g.lg_seg) - 1;
+    if (k == 0) return mulhi(local, g.span) - (t << g.lg_seg);
+    if (k == 3) return mix64(local ^ kEdgeSalt2) & mask;
+    const uint64_t r = mix64(local ^ kEdgeSalt);
+    return (k == 1 ? r : r >> 32) & mask;
+}
+
 // Filter fingerprint: top b bits of a remix of the local signature (Sec. 4.5).
 __device__ __forceinline__ uint64_t fingerprint64(uint64_t local, int b) { return mix64(local ^ kFpSalt) >> (64 - b); }
 

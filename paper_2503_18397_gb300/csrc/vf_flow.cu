@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
             if (t < k || t - k >= nb) continue;
             const uint64_t bin = uint64_t(sh) * nb + (t - k);
             const uint64_t lo = bin ? __ldg(seg_ends + bin - 1) : 0ull, hi = __ldg(seg_ends + bin);
-            const uint64_t seg0 = (uint64_t(t) << g.lg_seg) + (uint64_t(ch) << lgc);  // the chunk's first cell
+            const uint64_t choff = uint64_t(ch) << lgc;  // the chunk's first cell within the segment
             const uint64_t step = uint64_t(kIncSegUnroll) * blockDim.x;
             for (uint64_t e0 = lo + threadIdx.x; e0 < hi; e0 += step) {
                 // all of a thread's signature (and drop-word) loads are issued
@@ -198,10 +198,9 @@ __global__ void __launch_bounds__(kIncSegThreads) k_incidence_seg(const uint64_t
                     const uint64_t e = e0 + uint64_t(u) * blockDim.x;
                     if (e >= hi || ((dw[u] >> (e & 31u)) & 1u)) continue;
                     const uint32_t el = uint32_t(e - st0);
-                    uint64_t v[4];
-                    edge_of(g, sg[u], v);
-                    const uint64_t vk = k == 0 ? v[0] : k == 1 ? v[1] : k == 2 ? v[2] : v[3];
-                    const uint64_t r = vk - seg0;  // vertex k of a bin t - k edge lies in segment t
+                    // vertex k of a bin t - k edge lies in segment t (for k = 0 this is
+                    // checked: a misplaced edge gives an offset beyond the segment)
+                    const uint64_t r = fuse_vertex_in_segment(g, sg[u], k, t) - choff;
                     if (r >= chunk) {
                         // another chunk of the segment (or, if the segment has one chunk,
                         // impossible for segment-ordered edges)
