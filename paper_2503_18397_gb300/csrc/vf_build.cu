@@ -69,9 +69,14 @@ __device__ __forceinline__ uint32_t load_value(const void* values, int b, uint64
 // Each block takes tiles of kThreads*kItems keys, counts the tile's keys per
 // shard in shared memory, reserves one contiguous range per (tile, shard) with
 // a single global atomic, and writes each key into its range.
-// cursor[s] starts at shard_start[s]. sig_in (byte keys) replaces hashing.
+// cursor[s] starts at shard_start[s]. SIG: signatures given (byte keys, sig_in)
+// instead of hashing the keys. A tile's steps form a dependent chain (loads,
+// shared ranks, the global reservation, the writes), so each block loads the
+// keys of its next tile before working on the current one: their latency
+// overlaps this tile's reservation instead of adding to it.
 constexpr int kItems = 4;
 
+template <bool SIG>
 __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict__ keys,
                                                       const Sig* __restrict__ sig_in, const void* __restrict__ values,
                                                       uint64_t n, Geom g, unsigned long long* __restrict__ cursor,
@@ -82,7 +87,32 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict
     const uint32_t S = 1u << g.h;
     const bool has_val = values != nullptr;
     const uint64_t tile = uint64_t(kThreads) * kItems;
-    for (uint64_t t0 = blockIdx.x * tile; t0 < n; t0 += uint64_t(gridDim.x) * tile) {
+    const uint64_t stride = uint64_t(gridDim.x) * tile;
+    uint64_t nk[kItems];  // the next tile's keys (SIG: its signatures)
+    Sig ns[kItems];
+    auto fetch = [&](uint64_t t) {
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            const uint64_t i = t + uint64_t(k) * kThreads + threadIdx.x;
+            if (i < n) {
+                if constexpr (SIG) ns[k] = sig_in[i];
+                else nk[k] = __ldg(keys + i);
+            }
+        }
+    };
+    uint64_t t0 = blockIdx.x * tile;
+    if (t0 < n) fetch(t0);
+    for (; t0 < n; t0 += stride) {
+        Sig cur[kItems];
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            const uint64_t i = t0 + uint64_t(k) * kThreads + threadIdx.x;
+            if (i < n) {
+                if constexpr (SIG) cur[k] = ns[k];
+                else cur[k] = sig_u64(nk[k], g.kh, g.kl);
+            }
+        }
+        if (t0 + stride < n) fetch(t0 + stride);
         for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) cnt[i] = 0;
         __syncthreads();
         uint64_t loc[kItems];
@@ -92,11 +122,10 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict
             uint64_t i = t0 + uint64_t(k) * kThreads + threadIdx.x;
             sh[k] = 0xFFFFFFFFu;
             if (i < n) {
-                Sig s = sig_in ? sig_in[i] : sig_u64(__ldg(keys + i), g.kh, g.kl);
-                const uint32_t shard = uint32_t(shard_of(s, g.h));
+                const uint32_t shard = uint32_t(shard_of(cur[k], g.h));
                 if (shard >= s_lo && shard < s_hi) {  // only the shard group being built
                     sh[k] = shard;
-                    loc[k] = local_of(s, g.h);
+                    loc[k] = local_of(cur[k], g.h);
                     val[k] = has_val ? load_value(values, g.b, i) : 0u;
                     rank[k] = atomicAdd(&cnt[shard], 1u);
                 }
@@ -230,8 +259,12 @@ cudaError_t launch_scatter(const uint64_t* keys_u64, const Sig* sig_in, const vo
                            uint32_t s_lo, uint32_t s_hi, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     if ((1u << g.h) <= uint32_t(kSmemBinsMax))
-        k_scatter<<<stream_grid(n, kItems), kThreads, 0, st>>>(keys_u64, sig_in, values, n, g, cursor, loc_out,
-                                                               val_out, s_lo, s_hi);
+        if (sig_in)
+            k_scatter<true><<<stream_grid(n, kItems), kThreads, 0, st>>>(keys_u64, sig_in, values, n, g, cursor,
+                                                                         loc_out, val_out, s_lo, s_hi);
+        else
+            k_scatter<false><<<stream_grid(n, kItems), kThreads, 0, st>>>(keys_u64, sig_in, values, n, g, cursor,
+                                                                          loc_out, val_out, s_lo, s_hi);
     else
         k_scatter_wide<<<stream_grid(n), kThreads, 0, st>>>(keys_u64, sig_in, values, n, g, cursor, loc_out,
                                                             val_out, s_lo, s_hi);
