@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(1024) k_seg_scan(unsigned long long* __restric
 }
 
 // Scatter every edge (signature and value) to its bin's next slot.
-__global__ void __launch_bounds__(kTileThreads) k_seg_scatter(const uint64_t* __restrict__ loc,
+__global__ void __launch_bounds__(kTileThreads, 3) k_seg_scatter(const uint64_t* __restrict__ loc,
                                                                const uint32_t* __restrict__ val, uint64_t n,
                                                                const unsigned long long* __restrict__ start,
                                                                uint32_t S, Geom g, uint32_t nb, uint32_t sshift,
@@ -789,11 +789,15 @@ __global__ void __launch_bounds__(kTileThreads) k_seg_scatter(const uint64_t* __
         uint64_t xs[kPer];
         uint32_t rk[kPer], bn[kPer];
 #pragma unroll
+        for (int j = 0; j < kPer; j++) {  // every load of the tile issued before the first rank
+            const uint32_t i = threadIdx.x + uint32_t(j) * kTileThreads;
+            xs[j] = i < m ? __ldg(loc + t0 + i) : 0ull;
+        }
+#pragma unroll
         for (int j = 0; j < kPer; j++) {
             const uint32_t i = threadIdx.x + uint32_t(j) * kTileThreads;
             bn[j] = 0xFFFFFFFFu;
             if (i < m) {
-                xs[j] = __ldg(loc + t0 + i);
                 if (s_many) {
                     const uint32_t s = flow_shard_of_edge(start, S, t0 + i);
                     const unsigned long long pos = atomicAdd(cursor + uint64_t(s) * nb + seg_bin(xs[j], g, sshift), 1ull);
