@@ -80,7 +80,7 @@ def query_need(m: int) -> int:
 @dataclass
 class Server:
     device: int = 0
-    budget: int = 8 << 30          # device bytes the loop may hold for in-flight work
+    budget: int = 8 << 30          # device bytes the loop may hold: in-flight work and resident arrays
     batch_below: int = 1 << 20     # builds smaller than this are batched together
     batch_keys: int = 1 << 26      # at most this many keys per batched build launch
     params: B.VfParams | None = None
@@ -95,7 +95,8 @@ class Server:
         self._lock = threading.Condition()
         self._builds = collections.deque()     # admitted, not started
         self._queries = collections.deque()    # resident structure, not started
-        self._in_use = 0
+        self._in_use = 0       # accounted device bytes: admitted work plus resident data arrays
+        self._inflight = 0     # admitted requests not yet finished
         self._stop = False
         self._errors = []
 
@@ -153,6 +154,7 @@ class Server:
                 self.resident[r.sid] = s
                 info = s.info
                 self._in_use -= build_need(len(r.keys), r.b, info.regime == B.REGIME_FUSE) - int(info.data_bytes)
+                self._inflight -= 1
             self._lock.notify_all()
 
     def _query_worker(self):
@@ -190,6 +192,7 @@ class Server:
                 rec.done = done
                 rec.result = h
                 self._in_use -= query_need(len(r.keys))
+                self._inflight -= 1
             self._lock.notify_all()
 
     # ------------------------------------------------------------------ scheduler
@@ -215,21 +218,25 @@ class Server:
                 with self._lock:
                     if self._errors:
                         break
-                    # builds: in arrival order while memory allows (one oversized build runs alone)
+                    # builds: in arrival order while memory allows; one that does not fit
+                    # (beyond the budget, or with resident arrays filling it) runs once
+                    # nothing else is in flight
                     while waiting_b:
                         r = waiting_b[0]
                         need = build_need(len(r.keys), r.b, len(r.keys) >= self.params.lge_threshold)
-                        if self._in_use + need > self.budget and self._in_use > 0:
+                        if self._in_use + need > self.budget and self._inflight > 0:
                             break
                         self._in_use += need
+                        self._inflight += 1
                         self._builds.append(waiting_b.popleft())
                     # queries: once their structure is resident and memory allows
                     keep = collections.deque()
                     while waiting_q:
                         r = waiting_q.popleft()
                         need = query_need(len(r.keys))
-                        if r.sid in self.resident and (self._in_use + need <= self.budget or self._in_use == 0):
+                        if r.sid in self.resident and (self._in_use + need <= self.budget or self._inflight == 0):
                             self._in_use += need
+                            self._inflight += 1
                             self._queries.append(r)
                         else:
                             keep.append(r)
